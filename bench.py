@@ -1,0 +1,309 @@
+"""Benchmark: FP64 tiled SPD inversion (POTRI) on one GB300, n = 16384, tile 64.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                [--n 16384] [--tile 64] [--cond 1e4] [--no-e2e] [--no-cpu-baseline]
+
+One step = restore A from a pristine device copy (0.6 ms) + one full
+inversion through the C-ABI (spdinv_potri_ex).  The metric counts n^3 flops
+per inversion (the leading term of Steps 1-3, n^3/3 each).  A (2 GiB) is
+larger than L2, so no flush is needed between steps.
+
+--impl reference times the FP64 CPU oracle (the reference arm of this
+project: a plain unblocked FP64 implementation) on a bounded sample of the
+same workload.  With torchrun (N > 1) each rank inverts its own matrix
+(replicas: the single-matrix inversion does not shard), value = all ranks'
+flops / the slowest rank's time.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "POTRI Gflop/s (n^3/inv) & % tensor peak; mixed vs FP64 speedup at 1e-10 err"
+BF16_NOMINAL_TFLOPS = 2250.0
+FP64_NOMINAL_TFLOPS = 1.25
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=4)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=16384)
+    ap.add_argument("--tile", type=int, default=64)
+    ap.add_argument("--ctas-per-sm", type=int, default=0)
+    ap.add_argument("--cond", type=float, default=1e4)
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"bf16_tflops": 1900.0, "hbm_gbs": 6800.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.out = tempfile.NamedTemporaryFile(prefix="clk", suffix=".csv", delete=False)
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.out, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.out.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.out.name):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.out.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(n_full, cond, budget_s=15.0):
+    """The FP64 oracle (unblocked potf2/trti2/lauu2, OpenMP) on one matrix of
+    the same generator, with n chosen so that the run takes about budget_s."""
+    import oracle
+    import spd_inputs as si
+    n = 768
+    A, _, _ = si.spectral_spd(n, cond, seed=si.SEED_BASE + 1)
+    t0 = time.perf_counter()
+    _, info = oracle.potri(A)
+    dt = time.perf_counter() - t0
+    assert info == 0
+    # unblocked cost grows like n^3; pick a sample size for ~budget_s
+    n2 = int(n * (budget_s / max(dt, 1e-3)) ** (1.0 / 3.0))
+    n2 = max(512, min(n2, 4096, n_full))
+    n2 -= n2 % 64
+    A, _, _ = si.spectral_spd(n2, cond, seed=si.SEED_BASE + 1)
+    t0 = time.perf_counter()
+    _, info = oracle.potri(A)
+    dt = time.perf_counter() - t0
+    assert info == 0
+    return {"value": round(n2 ** 3 / dt / 1e9, 3), "unit": "Gflop/s", "cores": oracle.num_threads(),
+            "kind": "oracle",
+            "sample": "one full oracle inversion of an n=%d matrix of the same generator (cond %.0e); "
+                      "%.1f s; Gflop/s = n^3/t" % (n2, cond, dt)}
+
+
+def run_reference(args, rank, world):
+    """The reference arm: the FP64 CPU oracle, each step a bounded sample."""
+    if rank != 0:
+        return
+    import oracle
+    import spd_inputs as si
+    n = 1024
+    A0, _, _ = si.spectral_spd(n, args.cond, seed=si.SEED_BASE + 1)
+    for _ in range(args.warmup):
+        oracle.potri(A0)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        _, info = oracle.potri(A0)
+        assert info == 0
+    dt = (time.perf_counter() - t0) / args.steps
+    val = n ** 3 / dt / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(val, 3), "unit": "Gflop/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt * 1e3, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "fp64_potri_n%d_b%d" % (args.n, args.tile), "sample_n": n, "cond": args.cond},
+        "cpu_baseline": {"value": round(val, 3), "unit": "Gflop/s", "cores": oracle.num_threads(), "kind": "oracle",
+                         "sample": "each step: one full oracle inversion of an n=%d matrix of the same "
+                                   "generator (the n=%d workload is hours of unblocked CPU work)" % (n, args.n)},
+        "e2e": {"value": round(val, 3), "unit": "Gflop/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    # CPU baseline first (threads only; before any GPU work)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args.n, args.cond)
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import spd_inputs as si
+    from paper_1002_4057_gb300 import _lib as L
+    from paper_1002_4057_gb300 import torch_api as T
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    n, b = args.n, args.tile
+    A0, _, _ = si.spectral_spd(n, args.cond, seed=si.SEED_BASE + 1 + rank, device=dev)
+    A = torch.empty_like(A0)
+    info = torch.zeros(1, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        A.copy_(A0)
+        T.potri_(A, info=info, tile=b, ctas_per_sm=args.ctas_per_sm)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    assert int(info.item()) == 0, "info %d" % int(info.item())
+
+    # ---- timed region: K steps, events on the launching stream
+    clk = ClockSampler(local)
+    clk.start()
+    time.sleep(0.3)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    launches0 = L.spdinv_kernel_launches()
+    barrier()
+    torch.cuda.synchronize()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for k in range(args.steps):
+        A.copy_(A0)
+        ev[k][0].record(stream)
+        T.potri_(A, info=info, tile=b, ctas_per_sm=args.ctas_per_sm)
+        ev[k][1].record(stream)
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    launches = L.spdinv_kernel_launches() - launches0
+    clocks = clk.stop()
+    total_ms = t_start.elapsed_time(t_end)
+    kern_ms = [s.elapsed_time(e) for s, e in ev]
+    assert int(info.item()) == 0
+    if world > 1:
+        tt = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    ms_per_step = total_ms / args.steps
+    flops = float(n) ** 3
+    value = world * flops / (ms_per_step * 1e-3) / 1e9  # Gflop/s, all ranks
+
+    # ---- end to end through the public API, host buffers (pinned)
+    e2e = None
+    if not args.no_e2e:
+        hA = torch.empty((n * n,), dtype=torch.float64, pin_memory=True)
+        hA.copy_(A0.t().contiguous().reshape(-1))  # column-major flattening of A0
+        hOut = torch.empty_like(hA)
+        dA = torch.empty((n * n,), dtype=torch.float64, device=dev)
+        dview = dA.as_strided((n, n), (1, n))
+
+        def e2e_step():
+            dA.copy_(hA, non_blocking=True)
+            T.potri_(dview, info=info, tile=b, ctas_per_sm=args.ctas_per_sm)
+            hOut.copy_(dA, non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        barrier()
+        s0 = torch.cuda.Event(enable_timing=True)
+        s1 = torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        for _ in range(args.e2e_steps):
+            e2e_step()
+        s1.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms = s0.elapsed_time(s1) / args.e2e_steps
+        if world > 1:
+            tt = torch.tensor([e2e_ms], device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            e2e_ms = float(tt.item())
+        assert int(info.item()) == 0
+        e2e = {"value": round(world * flops / (e2e_ms * 1e-3) / 1e9, 3), "unit": "Gflop/s",
+               "h2d_bytes_per_step": n * n * 8, "d2h_bytes_per_step": n * n * 8,
+               "ms_per_step": round(e2e_ms, 3), "steps": args.e2e_steps}
+        del hA, hOut, dA
+
+    peaks, src = measured_peaks()
+    peak_tf = peaks["bf16_tflops"] * FP64_NOMINAL_TFLOPS / BF16_NOMINAL_TFLOPS
+    kern_avg_s = statistics.mean(kern_ms) * 1e-3
+    achieved_tf = flops / kern_avg_s / 1e12
+    roofline = {
+        "bound": "tensor", "achieved": round(achieved_tf, 4), "peak": round(peak_tf, 4), "unit": "TFLOP/s",
+        "frac": round(achieved_tf / peak_tf, 4), "traffic": None,
+        "kernel": "potri_fp64_persistent<64> (FP64 DMMA m8n8k4)",
+        "peak_note": "FP64 peak = bf16_tflops (%s) x nominal FP64/bf16 ratio 1.25/2250; "
+                     "DMMA microbenchmark on this GPU: 1.04 TFLOP/s" % src,
+    }
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 3), "unit": "Gflop/s", "n_gpus": world, "steps": args.steps,
+            "warmup": max(args.warmup, 3), "ms_per_step": round(ms_per_step, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "fp64_potri_n%d_b%d" % (n, b), "n": n, "tile": b, "cond": args.cond,
+                       "generator": "A = Q diag(lam) Q^T, Q from QR of seeded N(0,1), lam log-uniform [1, cond]",
+                       "l2": "inputs larger than L2 (A is %.1f GiB)" % (n * n * 8 / 2 ** 30),
+                       "step": "restore A from a device copy + spdinv_potri_ex",
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": int(launches),
+            "kernel_ms": [round(x, 3) for x in kern_ms],
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,230 @@
+/*
+ * spdinv -- inversion of symmetric positive definite matrices on GB300
+ * (sm_103a) as the three tiled steps of Agullo, Bouwmeester, Dongarra,
+ * Kurzak, Langou and Rosenberg, "Towards an Efficient Tile Matrix Inversion
+ * of Symmetric Positive Definite Matrices on Multicore Architectures"
+ * (Sec. 2, Algorithm 1):
+ *
+ *   Step 1  tile Cholesky factorisation       A = L L^T      (POTRF, TRSM, SYRK, GEMM)
+ *   Step 2  tile triangular inversion         X = L^{-1}     (TRTRI, TRMM, GEMM)
+ *   Step 3  tile product of lower triangles   A^{-1} = X^T X (TRMM, LAUUM, GEMM, SYRK)
+ *
+ * The tile DAG runs as one persistent kernel: tile readiness is tracked by
+ * device-side dependency counters, the write-after-read hazards of Sec. 3
+ * ("array renaming") are removed by renamed temporaries, and the three steps
+ * are overlapped ("pipelining", Sec. 3).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Matrices are column-major with leading dimension lda >= max(1, n);
+ *    element (i, j) is at A[i + j*lda].  Only the lower triangle (i >= j) is
+ *    read or written; the strictly upper part is never touched.
+ *  - Device pointers must point to device memory of the current CUDA device.
+ *    The caller owns every pointer it passes; the library keeps none after
+ *    the call returns except inside the work queued on `stream`.
+ *  - Every call is asynchronous on `stream` (0 = legacy default stream).
+ *    Argument errors are returned synchronously and nothing is launched.
+ *  - d_info (nullable) is a device int written when the queued work ends:
+ *      0   success;
+ *      k>0 the leading minor of order k is not positive definite (POTRF,
+ *          POTRI: the pivot of global column k-1 was <= 0 or NaN), or the
+ *          diagonal entry k-1 of the triangular factor is exactly zero
+ *          (TRTRI);
+ *      <0  a device-side failure with the value of an spdinv_status below
+ *          (SPDINV_ERR_TIMEOUT: a dependency wait ran past its limit; all
+ *          CTAs stopped and the kernel returned).
+ *    After k>0 or k<0 the contents of the lower triangle are unspecified,
+ *    except for TRTRI with k>0, which leaves A unchanged (LAPACK dtrtri).
+ *  - n == 0 returns SPDINV_OK at once and writes 0 to d_info.
+ *  - The library keeps a per-device workspace (the renamed temporaries and
+ *    the dependency counters, about n*n + n*b elements) and a plan cache;
+ *    both grow on demand with cudaMalloc.  A call made for the first time
+ *    with a given size may therefore allocate and must come before any CUDA
+ *    graph capture that later replays the same size.
+ *  - Calls on different streams of the same device share that workspace and
+ *    must not overlap in time; calls on one stream are ordered by the stream.
+ */
+#ifndef SPDINV_H
+#define SPDINV_H
+
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#if defined(__GNUC__)
+#define SPDINV_API __attribute__((visibility("default")))
+#else
+#define SPDINV_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SPDINV_OK = 0,
+    SPDINV_ERR_N = -1,            /* n < 0, or n beyond the supported maximum */
+    SPDINV_ERR_LDA = -2,          /* lda < max(1, n) */
+    SPDINV_ERR_NULL = -3,         /* a required pointer is NULL */
+    SPDINV_ERR_CUDA = -4,         /* a CUDA runtime call failed (see spdinv_last_cuda_error) */
+    SPDINV_ERR_TIMEOUT = -5,      /* device-side: a dependency wait exceeded its limit */
+    SPDINV_ERR_UNSUPPORTED = -6,  /* an option value this build does not implement */
+    SPDINV_ERR_WORKSPACE = -7     /* a caller-provided buffer is too small */
+} spdinv_status;
+
+/* Precision of the bulk tile updates (GEMM/SYRK/TRMM). */
+typedef enum {
+    SPDINV_PREC_FP64 = 0,         /* every operation in native FP64 (DMMA tensor cores) */
+    SPDINV_PREC_MIXED_FP32 = 1,   /* bulk updates FP32; diagonal POTRF/TRTRI and the residual FP64 */
+    SPDINV_PREC_MIXED_BF16X3 = 2  /* bulk updates as three BF16 products with FP32 accumulation
+                                     (tcgen05 tensor cores); diagonal tiles and residual FP64 */
+} spdinv_precision;
+
+/* Options for spdinv_potri_ex.  Zero-initialise and set what you need. */
+typedef struct {
+    int tile;            /* tile order b; 0 = automatic (64 for FP64) */
+    int ctas_per_sm;     /* resident CTAs per SM of the persistent kernel; 0 = automatic */
+    int precision;       /* spdinv_precision */
+    int refine_steps;    /* mixed precision only: residual corrections X <- X + X(I - A X); 0 = none */
+    double wait_timeout_s; /* limit for one dependency wait; 0 = default (60 s) */
+    int fault_drop_task; /* failure-detection test hook: when >= 0, the task with this ticket
+                            never signals completion, so its consumers hit the wait limit and
+                            the call ends with d_info = SPDINV_ERR_TIMEOUT; -1 (or any value
+                            below 0) = off.  Only honoured when wait_timeout_s > 0. */
+} spdinv_opts;
+
+/* ------------------------------------------------------------------------
+ * The three steps, separately (LAPACK lower-triangle semantics)
+ * ------------------------------------------------------------------------ */
+
+/* Step 1 (Algorithm 1, Step 1; Sec. 2): tile Cholesky factorisation.
+ * On entry the lower triangle of A holds the SPD matrix; on exit it holds L
+ * with A = L L^T (LAPACK dpotrf, uplo = 'L'). */
+SPDINV_API spdinv_status spdinv_potrf(int64_t n, double* dA, int64_t lda, int* d_info, cudaStream_t stream);
+
+/* Step 2 (Algorithm 1, Step 2; Sec. 2): inversion of a lower triangular,
+ * non-unit matrix in place, X = L^{-1} (LAPACK dtrtri, uplo 'L', diag 'N').
+ * d_info = k > 0 if L(k-1, k-1) == 0; A is then left unchanged. */
+SPDINV_API spdinv_status spdinv_trtri(int64_t n, double* dA, int64_t lda, int* d_info, cudaStream_t stream);
+
+/* Step 3 (Algorithm 1, Step 3; Sec. 2): lower triangle of X^T X for a lower
+ * triangular X, in place (LAPACK dlauum, uplo 'L'). */
+SPDINV_API spdinv_status spdinv_lauum(int64_t n, double* dA, int64_t lda, cudaStream_t stream);
+
+/* ------------------------------------------------------------------------
+ * The whole inversion
+ * ------------------------------------------------------------------------ */
+
+/* Steps 1-3 pipelined in one persistent launch (Algorithm 1 with the
+ * renaming and pipelining of Sec. 3): the lower triangle of A is replaced by
+ * the lower triangle of A^{-1}.  Note: unlike LAPACK dpotri, which takes the
+ * Cholesky factor, this takes A itself; spdinv_trtri followed by
+ * spdinv_lauum gives dpotri's semantics on a factor. */
+SPDINV_API spdinv_status spdinv_potri(int64_t n, double* dA, int64_t lda, int* d_info, cudaStream_t stream);
+
+/* spdinv_potri with options (tile size, residency, precision, correction
+ * steps, wait limit).  opts may be NULL (= all defaults).
+ * Mixed precision (opts->precision != SPDINV_PREC_FP64): the lower triangle
+ * of A still holds A^{-1} in FP64 on exit; with refine_steps > 0 the library
+ * also keeps an FP64 copy of A for the residual. */
+SPDINV_API spdinv_status spdinv_potri_ex(int64_t n, double* dA, int64_t lda, const spdinv_opts* opts,
+                              int* d_info, cudaStream_t stream);
+
+/* ------------------------------------------------------------------------
+ * Many independent matrices of uneven sizes in one persistent launch
+ * ------------------------------------------------------------------------ */
+
+/* Inverts batch matrices A_k (k < batch) in place, each with Algorithm 1's
+ * three steps, in ONE kernel launch: CTAs take matrices from a device queue
+ * ordered by decreasing n (largest first), and each matrix runs the tile
+ * algorithm with the tile shape the autotuner chose for its size class.
+ *   h_n[k], h_lda[k]  host arrays: order and leading dimension of A_k
+ *                     (0 <= h_n[k] <= 4096, h_lda[k] >= max(1, h_n[k]));
+ *   d_Aptrs           device array of batch device pointers;
+ *   d_info            device int[batch] (nullable): per-matrix info as above.
+ * The per-size plan (queue order, tile choice) is cached by the exact size
+ * list: the first call with a size list uploads it (and may allocate); a
+ * later call with the same list queues only the kernel launch and can be
+ * captured in a CUDA graph. */
+SPDINV_API spdinv_status spdinv_potri_batched(int batch, const int* h_n, double* const* d_Aptrs,
+                                   const int* h_lda, int* d_info, cudaStream_t stream);
+
+/* FP32 twin of spdinv_potri_batched (float data, FP32 arithmetic). */
+SPDINV_API spdinv_status spdinv_spotri_batched(int batch, const int* h_n, float* const* d_Aptrs,
+                                    const int* h_lda, int* d_info, cudaStream_t stream);
+
+/* ------------------------------------------------------------------------
+ * Differentiation (added form: backward of X = A^{-1})
+ * ------------------------------------------------------------------------ */
+
+/* grad_A = -sym(X G X) = -(X G X + (X G X)^T) / 2 for `batch` matrices of
+ * order n, from the saved inverse X (full symmetric, column-major, ldx) and
+ * the incoming gradient G (full, ldg).  Writes the full symmetric grad_A
+ * (ldgrad).  Matrix k starts at element offset k*stride_* of each pointer.
+ * X, G and grad_A must not overlap. */
+SPDINV_API spdinv_status spdinv_potri_backward(int batch, int64_t n, const double* dX, int64_t ldx, int64_t stride_x,
+                                    const double* dG, int64_t ldg, int64_t stride_g,
+                                    double* dGrad, int64_t ldgrad, int64_t stride_grad,
+                                    cudaStream_t stream);
+
+/* FP32 twin of spdinv_potri_backward. */
+SPDINV_API spdinv_status spdinv_spotri_backward(int batch, int64_t n, const float* dX, int64_t ldx, int64_t stride_x,
+                                     const float* dG, int64_t ldg, int64_t stride_g,
+                                     float* dGrad, int64_t ldgrad, int64_t stride_grad,
+                                     cudaStream_t stream);
+
+/* ------------------------------------------------------------------------
+ * Host-side planner queries (no GPU needed)
+ * ------------------------------------------------------------------------ */
+
+/* Flags describing a variant of the paper's task DAG (Sec. 3). */
+#define SPDINV_DAG_OUT_OF_PLACE 1  /* renaming: Step 2 reads B (copy of L), Step 3 reads C (copy of L^{-1}) */
+#define SPDINV_DAG_RENAME_DIAG  2  /* also keep the inverted diagonal tiles in their own store D */
+#define SPDINV_DAG_UUU          4  /* all innermost GEMM loops increasing (default: U, D, U) */
+#define SPDINV_DAG_PIPELINE     8  /* one DAG across the three steps (else a barrier between steps) */
+
+/* Critical path, in tasks of unit weight (tile copies weigh 0), of the
+ * fine-grained task DAG of Algorithm 1 (Sec. 2) or its variants (Sec. 3)
+ * for t x t tiles: out[0..2] = each step's own DAG, out[3] = the whole
+ * inversion (pipelined or with barriers, per SPDINV_DAG_PIPELINE).
+ * Table 1 of the paper gives out[0..2] for the in-place and out-of-place
+ * cases.  1 <= t <= 256. */
+SPDINV_API spdinv_status spdinv_dag_critical_path(int t, int flags, int64_t out[4]);
+
+/* Number of tasks of each kind in Algorithm 1 for t x t tiles, in the order
+ * POTRF, TRSM, SYRK(step 1), GEMM(step 1), TRTRI, TRMM(step 2, left),
+ * GEMM(step 2), TRMM(step 2, right), TRMM(step 3), LAUUM, GEMM(step 3),
+ * SYRK(step 3): out[0..11]. */
+SPDINV_API spdinv_status spdinv_dag_task_counts(int t, int64_t out[12]);
+
+/* The execution plan the persistent kernel runs for an order-n matrix with
+ * tile b: the chain tasks (one per output tile and step; each holds its
+ * whole commutative update chain, Sec. 3 "loop reversal") in the order CTAs
+ * take them.  Each task is encoded as (kind << 28) | (i << 14) | j with kind
+ * 0 = Step-1 diagonal, 1 = Step-1 off-diagonal, 2 = Step-2 diagonal,
+ * 3 = Step-2 off-diagonal, 4 = Step-3 diagonal, 5 = Step-3 off-diagonal.
+ * steps: 1 = potrf, 2 = trtri, 3 = lauum, 0 = potri (all three).
+ * Writes at most cap tasks to out (NULL allowed when cap == 0), the task
+ * count to *ntasks and the weighted critical path (in units of one b^3
+ * multiply-add tile product) to *crit (nullable). */
+SPDINV_API spdinv_status spdinv_plan_tasks(int64_t n, int b, int steps, uint32_t* out, int64_t cap,
+                                int64_t* ntasks, double* crit);
+
+/* ------------------------------------------------------------------------
+ * Library information
+ * ------------------------------------------------------------------------ */
+
+/* Text of the last CUDA runtime error seen by this thread's calls (or ""). */
+SPDINV_API const char* spdinv_last_cuda_error(void);
+
+/* Number of kernels this library has queued since it was loaded (all
+ * devices, all threads): a host-side counter, incremented per launch. */
+SPDINV_API uint64_t spdinv_kernel_launches(void);
+
+/* Version as major*10000 + minor*100 + patch. */
+SPDINV_API int spdinv_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPDINV_H */

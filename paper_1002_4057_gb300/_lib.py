@@ -1,0 +1,160 @@
+"""ctypes binding of libspdinv.so: the C-ABI functions under the same names.
+
+Argument marshalling only.  The library is loaded from this package's lib/
+folder (built by paper_1002_4057_gb300.build); there is no fallback: a
+missing library raises.
+"""
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "lib", "libspdinv.so")
+
+c_int64 = ctypes.c_int64
+c_int = ctypes.c_int
+c_double = ctypes.c_double
+c_void_p = ctypes.c_void_p
+P = ctypes.c_void_p  # device/host pointers and cudaStream_t are passed as integers
+
+SPDINV_OK = 0
+SPDINV_ERR_N = -1
+SPDINV_ERR_LDA = -2
+SPDINV_ERR_NULL = -3
+SPDINV_ERR_CUDA = -4
+SPDINV_ERR_TIMEOUT = -5
+SPDINV_ERR_UNSUPPORTED = -6
+SPDINV_ERR_WORKSPACE = -7
+
+SPDINV_PREC_FP64 = 0
+SPDINV_PREC_MIXED_FP32 = 1
+SPDINV_PREC_MIXED_BF16X3 = 2
+
+SPDINV_DAG_OUT_OF_PLACE = 1
+SPDINV_DAG_RENAME_DIAG = 2
+SPDINV_DAG_UUU = 4
+SPDINV_DAG_PIPELINE = 8
+
+STATUS_NAMES = {0: "SPDINV_OK", -1: "SPDINV_ERR_N", -2: "SPDINV_ERR_LDA", -3: "SPDINV_ERR_NULL",
+                -4: "SPDINV_ERR_CUDA", -5: "SPDINV_ERR_TIMEOUT", -6: "SPDINV_ERR_UNSUPPORTED",
+                -7: "SPDINV_ERR_WORKSPACE"}
+
+
+class spdinv_opts(ctypes.Structure):
+    _fields_ = [("tile", c_int), ("ctas_per_sm", c_int), ("precision", c_int), ("refine_steps", c_int),
+                ("wait_timeout_s", c_double), ("fault_drop_task", c_int)]
+
+
+# name -> (restype, argtypes); every symbol declared in include/spdinv.h
+SIGNATURES = {
+    "spdinv_potrf": (c_int, [c_int64, P, c_int64, P, P]),
+    "spdinv_trtri": (c_int, [c_int64, P, c_int64, P, P]),
+    "spdinv_lauum": (c_int, [c_int64, P, c_int64, P]),
+    "spdinv_potri": (c_int, [c_int64, P, c_int64, P, P]),
+    "spdinv_potri_ex": (c_int, [c_int64, P, c_int64, ctypes.POINTER(spdinv_opts), P, P]),
+    "spdinv_potri_batched": (c_int, [c_int, P, P, P, P, P]),
+    "spdinv_spotri_batched": (c_int, [c_int, P, P, P, P, P]),
+    "spdinv_potri_backward": (c_int, [c_int, c_int64, P, c_int64, c_int64, P, c_int64, c_int64,
+                                      P, c_int64, c_int64, P]),
+    "spdinv_spotri_backward": (c_int, [c_int, c_int64, P, c_int64, c_int64, P, c_int64, c_int64,
+                                       P, c_int64, c_int64, P]),
+    "spdinv_dag_critical_path": (c_int, [c_int, c_int, P]),
+    "spdinv_dag_task_counts": (c_int, [c_int, P]),
+    "spdinv_plan_tasks": (c_int, [c_int64, c_int, c_int, P, c_int64, P, P]),
+    "spdinv_last_cuda_error": (ctypes.c_char_p, []),
+    "spdinv_kernel_launches": (ctypes.c_uint64, []),
+    "spdinv_version": (c_int, []),
+}
+
+_lib = None
+
+
+def lib():
+    """The loaded library (raises if it was not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libspdinv.so is missing (%s): run paper_1002_4057_gb300.build.build() "
+                               "or __graft_entry__.build() first" % LIB_PATH)
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _call(name, *args):
+    return getattr(lib(), name)(*args)
+
+
+def spdinv_potrf(n, dA, lda, d_info, stream):
+    return _call("spdinv_potrf", n, dA, lda, d_info, stream)
+
+
+def spdinv_trtri(n, dA, lda, d_info, stream):
+    return _call("spdinv_trtri", n, dA, lda, d_info, stream)
+
+
+def spdinv_lauum(n, dA, lda, stream):
+    return _call("spdinv_lauum", n, dA, lda, stream)
+
+
+def spdinv_potri(n, dA, lda, d_info, stream):
+    return _call("spdinv_potri", n, dA, lda, d_info, stream)
+
+
+def spdinv_potri_ex(n, dA, lda, opts, d_info, stream):
+    return _call("spdinv_potri_ex", n, dA, lda, ctypes.byref(opts) if opts is not None else None, d_info, stream)
+
+
+def spdinv_potri_batched(batch, h_n, d_Aptrs, h_lda, d_info, stream):
+    return _call("spdinv_potri_batched", batch, h_n, d_Aptrs, h_lda, d_info, stream)
+
+
+def spdinv_spotri_batched(batch, h_n, d_Aptrs, h_lda, d_info, stream):
+    return _call("spdinv_spotri_batched", batch, h_n, d_Aptrs, h_lda, d_info, stream)
+
+
+def spdinv_potri_backward(batch, n, dX, ldx, sx, dG, ldg, sg, dGrad, ldgr, sgr, stream):
+    return _call("spdinv_potri_backward", batch, n, dX, ldx, sx, dG, ldg, sg, dGrad, ldgr, sgr, stream)
+
+
+def spdinv_spotri_backward(batch, n, dX, ldx, sx, dG, ldg, sg, dGrad, ldgr, sgr, stream):
+    return _call("spdinv_spotri_backward", batch, n, dX, ldx, sx, dG, ldg, sg, dGrad, ldgr, sgr, stream)
+
+
+def spdinv_dag_critical_path(t, flags):
+    out = (ctypes.c_int64 * 4)()
+    st = _call("spdinv_dag_critical_path", t, flags, ctypes.addressof(out))
+    return st, list(out)
+
+
+def spdinv_dag_task_counts(t):
+    out = (ctypes.c_int64 * 12)()
+    st = _call("spdinv_dag_task_counts", t, ctypes.addressof(out))
+    return st, list(out)
+
+
+def spdinv_plan_tasks(n, b, steps):
+    cnt = ctypes.c_int64(0)
+    crit = ctypes.c_double(0)
+    st = _call("spdinv_plan_tasks", n, b, steps, None, 0, ctypes.addressof(cnt), ctypes.addressof(crit))
+    if st != 0:
+        return st, [], 0.0
+    buf = (ctypes.c_uint32 * max(cnt.value, 1))()
+    st = _call("spdinv_plan_tasks", n, b, steps, ctypes.addressof(buf), cnt.value, ctypes.addressof(cnt),
+               ctypes.addressof(crit))
+    return st, list(buf)[:cnt.value], crit.value
+
+
+def spdinv_last_cuda_error():
+    return _call("spdinv_last_cuda_error").decode()
+
+
+def spdinv_kernel_launches():
+    return _call("spdinv_kernel_launches")
+
+
+def spdinv_version():
+    return _call("spdinv_version")

@@ -1,0 +1,222 @@
+// C-ABI of the library (declared in include/spdinv.h): argument checks, the
+// per-device plan cache and workspace, and the launch of the persistent
+// kernel.  No compute happens here.
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <climits>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/spdinv.h"
+#include "api_internal.h"
+#include "kernels.h"
+#include "plan.h"
+
+namespace spdinv {
+
+namespace {
+thread_local std::string g_last_cuda_error;
+std::atomic<uint64_t> g_launches{0};
+}  // namespace
+
+void count_launches(int k) { g_launches.fetch_add((uint64_t)k, std::memory_order_relaxed); }
+
+spdinv_status cuda_fail(cudaError_t e) {
+    g_last_cuda_error = cudaGetErrorString(e);
+    return SPDINV_ERR_CUDA;
+}
+
+DeviceState& device_state(int dev) {
+    static std::mutex mu;
+    static std::map<int, std::unique_ptr<DeviceState>> states;
+    std::lock_guard<std::mutex> lk(mu);
+    auto& s = states[dev];
+    if (!s) {
+        s.reset(new DeviceState());
+        cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, dev);
+    }
+    return *s;
+}
+
+cudaError_t DeviceState::ensure_workspace(size_t bytes) {
+    if (bytes <= ws_bytes) return cudaSuccess;
+    if (ws) {
+        cudaError_t e = cudaDeviceSynchronize();  // earlier work may still use the old buffer
+        if (e != cudaSuccess) return e;
+        cudaFree(ws);
+        ws = nullptr;
+        ws_bytes = 0;
+    }
+    cudaError_t e = cudaMalloc(&ws, bytes);
+    if (e == cudaSuccess) ws_bytes = bytes;
+    return e;
+}
+
+cudaError_t DeviceState::exec_plan(int t, int steps, const uint32_t** d_tasks, int* ntasks) {
+    const auto key = std::make_pair(t, steps);
+    auto it = plans.find(key);
+    if (it == plans.end()) {
+        ExecPlan p = build_exec_plan(t, steps);
+        DevicePlan dp;
+        dp.ntasks = (int)p.order.size();
+        cudaError_t e = cudaMalloc(&dp.d_tasks, sizeof(uint32_t) * (p.order.size() + 1));
+        if (e != cudaSuccess) return e;
+        e = cudaMemcpy(dp.d_tasks, p.order.data(), sizeof(uint32_t) * p.order.size(), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            cudaFree(dp.d_tasks);
+            return e;
+        }
+        it = plans.emplace(key, dp).first;
+    }
+    *d_tasks = it->second.d_tasks;
+    *ntasks = it->second.ntasks;
+    return cudaSuccess;
+}
+
+static size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+static double wait_timeout_s(const spdinv_opts* o) {
+    if (o && o->wait_timeout_s > 0) return o->wait_timeout_s;
+    if (const char* env = std::getenv("SPDINV_WAIT_TIMEOUT_S")) {
+        const double v = std::atof(env);
+        if (v > 0) return v;
+    }
+    return 60.0;
+}
+
+static int default_tile(int64_t n) { return n >= 8192 ? 64 : 32; }
+
+// Shared body of potrf / trtri / lauum / potri (FP64).
+spdinv_status run_fp64(int64_t n, double* dA, int64_t lda, int steps, const spdinv_opts* o, int* d_info,
+                       cudaStream_t stream) {
+    if (n < 0) return SPDINV_ERR_N;
+    if (lda < (n > 1 ? n : 1)) return SPDINV_ERR_LDA;
+    if (n > 0 && dA == nullptr) return SPDINV_ERR_NULL;
+    int b = (o && o->tile > 0) ? o->tile : default_tile(n);
+    if (b != 32 && b != 64) return SPDINV_ERR_UNSUPPORTED;
+    if (o && o->precision != SPDINV_PREC_FP64) return SPDINV_ERR_UNSUPPORTED;
+    const int64_t t64 = (n + b - 1) / b;
+    if (t64 > 16383) return SPDINV_ERR_N;
+    if (n == 0) {
+        if (d_info) {
+            cudaError_t e = cudaMemsetAsync(d_info, 0, sizeof(int), stream);
+            if (e != cudaSuccess) return cuda_fail(e);
+        }
+        return SPDINV_OK;
+    }
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e);
+    DeviceState& ds = device_state(dev);
+    std::lock_guard<std::mutex> lk(ds.mu);
+
+    const int t = (int)t64;
+    const size_t tile_bytes = (size_t)b * b * sizeof(double);
+    const size_t ntri = (size_t)t * (t - 1) / 2;
+    const size_t ctrl_bytes = align_up(sizeof(int) * (4 + 2 * (size_t)t * t + t), 256);
+    const bool needB = steps != STEPS_LAUUM, needC = steps != STEPS_POTRF;
+    const size_t bytesB = needB ? ntri * tile_bytes : 0, bytesC = needC ? ntri * tile_bytes : 0;
+    const size_t total = ctrl_bytes + bytesB + bytesC + (size_t)t * tile_bytes;
+    e = ds.ensure_workspace(total);
+    if (e != cudaSuccess) return cuda_fail(e);
+
+    KParamsF64 p{};
+    p.n = n;
+    p.lda = lda;
+    p.t = t;
+    p.b = b;
+    p.steps = steps;
+    p.A = dA;
+    char* base = static_cast<char*>(ds.ws);
+    p.ctrl = reinterpret_cast<int*>(base);
+    p.flags = p.ctrl + 4;
+    p.Bw = needB ? reinterpret_cast<double*>(base + ctrl_bytes) : nullptr;
+    p.Cw = needC ? reinterpret_cast<double*>(base + ctrl_bytes + bytesB) : nullptr;
+    p.Dw = reinterpret_cast<double*>(base + ctrl_bytes + bytesB + bytesC);
+    p.timeout_ns = (long long)(wait_timeout_s(o) * 1e9);
+    p.drop_task = (o && o->wait_timeout_s > 0 && o->fault_drop_task >= 0) ? o->fault_drop_task : -1;
+    e = ds.exec_plan(t, steps, &p.tasks, &p.ntasks);
+    if (e != cudaSuccess) return cuda_fail(e);
+
+    e = cudaMemsetAsync(p.ctrl, 0, ctrl_bytes, stream);
+    if (e != cudaSuccess) return cuda_fail(e);
+    int grid = 0;
+    const int per = (o && o->ctas_per_sm > 0) ? o->ctas_per_sm : 0;
+    e = launch_potri_fp64(p, per, ds.num_sms, d_info, stream, &grid);
+    if (e != cudaSuccess) return cuda_fail(e);
+    count_launches(1 + (d_info ? 1 : 0) + ((steps == STEPS_TRTRI || steps == STEPS_LAUUM) ? 1 : 0));
+    ds.last_grid = grid;
+    return SPDINV_OK;
+}
+
+}  // namespace spdinv
+
+using namespace spdinv;
+
+extern "C" {
+
+spdinv_status spdinv_potrf(int64_t n, double* dA, int64_t lda, int* d_info, cudaStream_t stream) {
+    return run_fp64(n, dA, lda, STEPS_POTRF, nullptr, d_info, stream);
+}
+
+spdinv_status spdinv_trtri(int64_t n, double* dA, int64_t lda, int* d_info, cudaStream_t stream) {
+    return run_fp64(n, dA, lda, STEPS_TRTRI, nullptr, d_info, stream);
+}
+
+spdinv_status spdinv_lauum(int64_t n, double* dA, int64_t lda, cudaStream_t stream) {
+    return run_fp64(n, dA, lda, STEPS_LAUUM, nullptr, nullptr, stream);
+}
+
+spdinv_status spdinv_potri(int64_t n, double* dA, int64_t lda, int* d_info, cudaStream_t stream) {
+    return run_fp64(n, dA, lda, STEPS_ALL, nullptr, d_info, stream);
+}
+
+spdinv_status spdinv_potri_ex(int64_t n, double* dA, int64_t lda, const spdinv_opts* opts, int* d_info,
+                              cudaStream_t stream) {
+    if (opts && opts->precision != SPDINV_PREC_FP64) return run_mixed(n, dA, lda, opts, d_info, stream);
+    return run_fp64(n, dA, lda, STEPS_ALL, opts, d_info, stream);
+}
+
+spdinv_status spdinv_dag_critical_path(int t, int flags, int64_t out[4]) {
+    if (t < 1 || t > 256) return SPDINV_ERR_N;
+    if (!out) return SPDINV_ERR_NULL;
+    dag_critical_path(t, flags, out);
+    return SPDINV_OK;
+}
+
+spdinv_status spdinv_dag_task_counts(int t, int64_t out[12]) {
+    if (t < 1) return SPDINV_ERR_N;
+    if (!out) return SPDINV_ERR_NULL;
+    dag_task_counts(t, out);
+    return SPDINV_OK;
+}
+
+spdinv_status spdinv_plan_tasks(int64_t n, int b, int steps, uint32_t* out, int64_t cap, int64_t* ntasks,
+                                double* crit) {
+    if (n < 1 || b < 1) return SPDINV_ERR_N;
+    if (steps < 0 || steps > 3) return SPDINV_ERR_UNSUPPORTED;
+    if (!ntasks || (cap > 0 && !out)) return SPDINV_ERR_NULL;
+    const int64_t t = (n + b - 1) / b;
+    if (t > 16383) return SPDINV_ERR_N;
+    ExecPlan p = build_exec_plan((int)t, steps);
+    *ntasks = (int64_t)p.order.size();
+    if (crit) *crit = p.crit;
+    const int64_t m = cap < *ntasks ? cap : *ntasks;
+    if (m > 0) std::memcpy(out, p.order.data(), sizeof(uint32_t) * (size_t)m);
+    return SPDINV_OK;
+}
+
+const char* spdinv_last_cuda_error(void) { return g_last_cuda_error.c_str(); }
+
+uint64_t spdinv_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+int spdinv_version(void) { return 10000; }
+
+}  // extern "C"

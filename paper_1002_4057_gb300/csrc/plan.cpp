@@ -1,0 +1,274 @@
+// Host planner.
+//
+// (1) dag_critical_path: the fine-grained task DAG of Algorithm 1 (Sec. 2)
+//     and of its variants studied in Sec. 3 -- array renaming (out-of-place,
+//     Table 1), loop reversal (UDU vs UUU) and pipelining of the three steps.
+//     Tasks are unfolded in their sequential order and the hazards on tiles
+//     (read after write, write after read, write after write) become edges,
+//     which is how the paper's dynamic scheduler builds its DAG (Sec. 1).
+//     Every task weighs one unit; tile copies weigh zero.
+//
+// (2) build_exec_plan: the plan the persistent kernel runs.  Each task owns
+//     one output tile of one step and carries that tile's whole commutative
+//     update chain (Sec. 3, "loop reversal": the innermost GEMMs of each step
+//     commute), in the loop orders U (Step 1), D (Step 2), U (Step 3) that the
+//     paper chose because they shorten the critical path.  Renamed stores
+//     B (L), C (L^{-1}) and D (inverted diagonal tiles) remove every
+//     write-after-read hazard, so a task depends only on the tiles it reads.
+//     Tasks are ordered by decreasing bottom level (longest weighted path to
+//     the end), which is a topological order; a CTA only ever waits for tasks
+//     taken before its own, so the persistent kernel cannot deadlock.
+#include "plan.h"
+
+#include <algorithm>
+#include <cstring>
+#include <numeric>
+
+#include "../../include/spdinv.h"
+
+namespace spdinv {
+
+// --------------------------------------------------------------------------
+// (1) fine-grained DAG
+// --------------------------------------------------------------------------
+namespace {
+
+struct HazardSim {
+    // Per address: finish time of the last writer and the latest finish of
+    // the readers since that write.
+    std::vector<int64_t> last_write, last_reads;
+    int64_t span = 0;
+    explicit HazardSim(size_t naddr) : last_write(naddr, 0), last_reads(naddr, 0) {}
+    void reset() {
+        std::fill(last_write.begin(), last_write.end(), 0);
+        std::fill(last_reads.begin(), last_reads.end(), 0);
+        span = 0;
+    }
+    // One task: start when every RAW/WAW/WAR predecessor has finished.
+    void task(std::initializer_list<int64_t> reads, std::initializer_list<int64_t> writes, int64_t w) {
+        int64_t start = 0;
+        for (int64_t a : reads) start = std::max(start, last_write[a]);
+        for (int64_t a : writes) start = std::max({start, last_write[a], last_reads[a]});
+        const int64_t fin = start + w;
+        for (int64_t a : reads) last_reads[a] = std::max(last_reads[a], fin);
+        for (int64_t a : writes) {
+            last_write[a] = fin;
+            last_reads[a] = 0;
+        }
+        span = std::max(span, fin);
+    }
+};
+
+}  // namespace
+
+void dag_critical_path(int t, int flags, int64_t out[4]) {
+    const bool oop = flags & SPDINV_DAG_OUT_OF_PLACE;
+    const bool rdiag = flags & SPDINV_DAG_RENAME_DIAG;
+    const bool uuu = flags & SPDINV_DAG_UUU;
+    const bool pipe = flags & SPDINV_DAG_PIPELINE;
+    const int64_t T = t;
+    // address spaces: A(i,j), B(i,j), C(i,j), D(j)
+    auto A = [&](int64_t i, int64_t j) { return i * T + j; };
+    auto B = [&](int64_t i, int64_t j) { return T * T + i * T + j; };
+    auto C = [&](int64_t i, int64_t j) { return 2 * T * T + i * T + j; };
+    auto D = [&](int64_t j) { return 3 * T * T + j; };
+    HazardSim sim(3 * T * T + T);
+    HazardSim whole(3 * T * T + T);
+    int64_t step_cp[3] = {0, 0, 0};
+
+    for (int pass = 0; pass < 2; ++pass) {
+        // pass 0: each step's own DAG (state reset between steps);
+        // pass 1: the whole inversion with one continuing state (pipelined).
+        HazardSim& s = pass == 0 ? sim : whole;
+        // ---- Step 1: tile Cholesky (Algorithm 1, Step 1)
+        if (pass == 0) s.reset();
+        for (int64_t j = 0; j < T; ++j) {
+            for (int64_t k = 0; k < j; ++k) s.task({A(j, j), A(j, k)}, {A(j, j)}, 1);  // SYRK
+            s.task({A(j, j)}, {A(j, j)}, 1);                                            // POTRF
+            for (int64_t i = j + 1; i < T; ++i)
+                for (int64_t k = 0; k < j; ++k) s.task({A(i, j), A(i, k), A(j, k)}, {A(i, j)}, 1);  // GEMM
+            for (int64_t i = j + 1; i < T; ++i) s.task({A(i, j), A(j, j)}, {A(i, j)}, 1);           // TRSM
+        }
+        if (pass == 0) step_cp[0] = s.span;
+        // ---- Step 2: tile triangular inversion (Algorithm 1, Step 2)
+        if (pass == 0) s.reset();
+        if (oop)
+            for (int64_t i = 0; i < T; ++i)
+                for (int64_t j = 0; j < i; ++j) s.task({A(i, j)}, {B(i, j)}, 0);  // B <- A
+        for (int64_t j = T - 1; j >= 0; --j) {
+            if (rdiag) s.task({A(j, j)}, {D(j)}, 1);  // TRTRI into D_j
+            else s.task({A(j, j)}, {A(j, j)}, 1);     // TRTRI in place
+            const int64_t Xj = rdiag ? D(j) : A(j, j);
+            for (int64_t i = T - 1; i > j; --i) {
+                const int64_t Xi = rdiag ? D(i) : A(i, i);
+                s.task({Xi, A(i, j)}, {A(i, j)}, 1);  // TRMM: A_ij <- X_ii A_ij
+                for (int64_t m = 0; m < i - j - 1; ++m) {
+                    const int64_t k = uuu ? j + 1 + m : i - 1 - m;  // U or D order
+                    const int64_t Lkj = oop ? B(k, j) : A(k, j);
+                    s.task({A(i, j), A(i, k), Lkj}, {A(i, j)}, 1);  // GEMM
+                }
+                s.task({A(i, j), Xj}, {A(i, j)}, 1);  // TRMM: A_ij <- -A_ij X_jj
+            }
+        }
+        if (pass == 0) step_cp[1] = s.span;
+        // ---- Step 3: product X^T X (Algorithm 1, Step 3)
+        if (pass == 0) s.reset();
+        if (oop)
+            for (int64_t i = 0; i < T; ++i)
+                for (int64_t j = 0; j <= i; ++j)
+                    if (j < i || !rdiag) s.task({A(i, j)}, {C(i, j)}, 0);  // C <- A
+        for (int64_t i = 0; i < T; ++i) {
+            const int64_t Xii = rdiag ? D(i) : (oop ? C(i, i) : A(i, i));
+            for (int64_t j = 0; j < i; ++j) s.task({Xii, A(i, j)}, {A(i, j)}, 1);  // TRMM
+            if (rdiag) s.task({D(i)}, {A(i, i)}, 1);                                 // LAUUM from D_i
+            else s.task({A(i, i)}, {A(i, i)}, 1);                                    // LAUUM in place
+            for (int64_t j = 0; j < i; ++j)
+                for (int64_t k = i + 1; k < T; ++k) {
+                    const int64_t Xki = oop ? C(k, i) : A(k, i), Xkj = oop ? C(k, j) : A(k, j);
+                    s.task({A(i, j), Xki, Xkj}, {A(i, j)}, 1);  // GEMM
+                }
+            for (int64_t k = i + 1; k < T; ++k) {
+                const int64_t Xki = oop ? C(k, i) : A(k, i);
+                s.task({A(i, i), Xki}, {A(i, i)}, 1);  // SYRK
+            }
+        }
+        if (pass == 0) step_cp[2] = s.span;
+    }
+    out[0] = step_cp[0];
+    out[1] = step_cp[1];
+    out[2] = step_cp[2];
+    out[3] = pipe ? whole.span : step_cp[0] + step_cp[1] + step_cp[2];
+}
+
+void dag_task_counts(int t, int64_t out[12]) {
+    const int64_t T = t;
+    const int64_t tri = T * (T - 1) / 2;                // tiles strictly below the diagonal
+    const int64_t tet = T * (T - 1) * (T - 2) / 6;      // triples i > j > k
+    out[0] = T;    // POTRF
+    out[1] = tri;  // TRSM
+    out[2] = tri;  // SYRK (step 1)
+    out[3] = tet;  // GEMM (step 1)
+    out[4] = T;    // TRTRI
+    out[5] = tri;  // TRMM (step 2, left)
+    out[6] = tet;  // GEMM (step 2)
+    out[7] = tri;  // TRMM (step 2, right)
+    out[8] = tri;  // TRMM (step 3)
+    out[9] = T;    // LAUUM
+    out[10] = tet; // GEMM (step 3)
+    out[11] = tri; // SYRK (step 3)
+}
+
+// --------------------------------------------------------------------------
+// (2) execution plan of the persistent kernel
+// --------------------------------------------------------------------------
+namespace {
+
+struct TaskIndex {
+    int t;
+    std::vector<int32_t> id;  // (kind, i, j) -> task id, -1 if absent
+    explicit TaskIndex(int t_) : t(t_), id((size_t)6 * t_ * t_, -1) {}
+    int32_t& at(uint32_t kind, int i, int j) { return id[((size_t)kind * t + i) * t + j]; }
+};
+
+}  // namespace
+
+ExecPlan build_exec_plan(int t, int steps) {
+    ExecPlan p;
+    p.t = t;
+    p.steps = steps;
+    const bool s1 = steps == STEPS_ALL || steps == STEPS_POTRF;
+    const bool s2 = steps == STEPS_ALL || steps == STEPS_TRTRI;
+    const bool s3 = steps == STEPS_ALL || steps == STEPS_LAUUM;
+    const bool s2diag = steps == STEPS_TRTRI;  // in potri the Step-1 diagonal task inverts
+
+    // Sequential (topological) order: Algorithm 1's loop nest.
+    std::vector<uint32_t> seq;
+    if (s1)
+        for (int j = 0; j < t; ++j) {
+            seq.push_back(encode_task(K_S1_DIAG, j, j));
+            for (int i = j + 1; i < t; ++i) seq.push_back(encode_task(K_S1_OFF, i, j));
+        }
+    if (s2)
+        for (int j = t - 1; j >= 0; --j) {
+            if (s2diag) seq.push_back(encode_task(K_S2_DIAG, j, j));
+            for (int i = t - 1; i > j; --i) seq.push_back(encode_task(K_S2_OFF, i, j));
+        }
+    if (s3)
+        for (int i = 0; i < t; ++i) {
+            for (int j = 0; j < i; ++j) seq.push_back(encode_task(K_S3_OFF, i, j));
+            seq.push_back(encode_task(K_S3_DIAG, i, i));
+        }
+    const size_t N = seq.size();
+    TaskIndex ix(t);
+    for (size_t m = 0; m < N; ++m) ix.at(task_kind(seq[m]), task_i(seq[m]), task_j(seq[m])) = (int32_t)m;
+
+    // Producer of each renamed store, or -1 when the data is ready at launch.
+    auto dprod = [&](int j) -> int32_t {  // D_j = X_jj
+        if (s1) return ix.at(K_S1_DIAG, j, j);
+        if (s2diag) return ix.at(K_S2_DIAG, j, j);
+        return -1;
+    };
+    auto lprod = [&](int i, int j) -> int32_t { return s1 ? ix.at(K_S1_OFF, i, j) : -1; };  // B_ij = L_ij
+    auto xprod = [&](int i, int j) -> int32_t { return s2 ? ix.at(K_S2_OFF, i, j) : -1; };  // C_ij = X_ij
+
+    // Cost of each task in units of one b x b x b tile product (b^3 FMA).
+    auto cost = [&](uint32_t e) -> double {
+        const int i = task_i(e), j = task_j(e);
+        switch (task_kind(e)) {
+            case K_S1_DIAG: return j + 0.7;
+            case K_S1_OFF: return j + 1.0;
+            case K_S2_DIAG: return 0.4;
+            case K_S2_OFF: return (i - j - 1) + 2.0;
+            case K_S3_DIAG: return (t - 1 - i) + 1.0;
+            default: return (t - 1 - i) + 1.0;
+        }
+    };
+    // Visits every predecessor (task whose output this task reads).
+    auto for_preds = [&](uint32_t e, auto&& f) {
+        const int i = task_i(e), j = task_j(e);
+        auto g = [&](int32_t p) { if (p >= 0) f(p); };
+        switch (task_kind(e)) {
+            case K_S1_DIAG:
+                for (int k = 0; k < j; ++k) g(lprod(j, k));
+                break;
+            case K_S1_OFF:
+                for (int k = 0; k < j; ++k) { g(lprod(i, k)); g(lprod(j, k)); }
+                g(dprod(j));
+                break;
+            case K_S2_DIAG:
+                break;
+            case K_S2_OFF:
+                g(dprod(i)); g(lprod(i, j));
+                for (int k = i - 1; k > j; --k) { g(xprod(i, k)); g(lprod(k, j)); }
+                g(dprod(j));
+                break;
+            case K_S3_DIAG:
+                g(dprod(i));
+                for (int k = i + 1; k < t; ++k) g(xprod(k, i));
+                break;
+            case K_S3_OFF:
+                g(dprod(i)); g(xprod(i, j));
+                for (int k = i + 1; k < t; ++k) { g(xprod(k, i)); g(xprod(k, j)); }
+                break;
+        }
+    };
+    // Bottom levels, pushed backwards along the sequential order.
+    std::vector<double> succmax(N, 0.0), bl(N, 0.0);
+    double work = 0.0;
+    for (size_t r = N; r-- > 0;) {
+        const double c = cost(seq[r]);
+        work += c;
+        bl[r] = c + succmax[r];
+        for_preds(seq[r], [&](int32_t p) { succmax[p] = std::max(succmax[p], bl[r]); });
+    }
+    std::vector<uint32_t> perm(N);
+    std::iota(perm.begin(), perm.end(), 0u);
+    std::stable_sort(perm.begin(), perm.end(), [&](uint32_t a, uint32_t b) { return bl[a] > bl[b]; });
+    p.order.resize(N);
+    for (size_t m = 0; m < N; ++m) p.order[m] = seq[perm[m]];
+    p.crit = N ? bl[perm[0]] : 0.0;
+    p.work = work;
+    return p;
+}
+
+}  // namespace spdinv

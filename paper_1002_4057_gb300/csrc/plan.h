@@ -1,0 +1,46 @@
+// Host-side planner: the paper's task DAG analysis and the execution plan of
+// the persistent kernel.
+#pragma once
+#include <cstdint>
+#include <vector>
+
+namespace spdinv {
+
+// Chain-task kinds of the execution plan (one task per output tile and step).
+enum TaskKind : uint32_t {
+    K_S1_DIAG = 0,  // Step 1, diagonal tile: SYRK chain, POTRF, then TRTRI of the factor
+    K_S1_OFF = 1,   // Step 1, off-diagonal tile: GEMM chain, then TRSM as TRMM by X_jj^T
+    K_S2_DIAG = 2,  // Step 2, diagonal tile (TRTRI alone: spdinv_trtri only)
+    K_S2_OFF = 3,   // Step 2, off-diagonal tile: TRMM, GEMM chain, TRMM
+    K_S3_DIAG = 4,  // Step 3, diagonal tile: LAUUM, SYRK chain
+    K_S3_OFF = 5,   // Step 3, off-diagonal tile: TRMM, GEMM chain
+};
+
+#if defined(__CUDACC__)
+#define SPDINV_HD __host__ __device__
+#else
+#define SPDINV_HD
+#endif
+SPDINV_HD inline uint32_t encode_task(uint32_t kind, uint32_t i, uint32_t j) { return (kind << 28) | (i << 14) | j; }
+SPDINV_HD inline uint32_t task_kind(uint32_t e) { return e >> 28; }
+SPDINV_HD inline uint32_t task_i(uint32_t e) { return (e >> 14) & 0x3FFFu; }
+SPDINV_HD inline uint32_t task_j(uint32_t e) { return e & 0x3FFFu; }
+
+enum PlanSteps { STEPS_ALL = 0, STEPS_POTRF = 1, STEPS_TRTRI = 2, STEPS_LAUUM = 3 };
+
+struct ExecPlan {
+    int t = 0;
+    int steps = 0;
+    std::vector<uint32_t> order;  // tasks in the order CTAs take them
+    double crit = 0.0;            // weighted critical path (tile-product units)
+    double work = 0.0;            // total weight
+};
+
+// Builds the chain-task plan for t x t tiles (t <= 16383).
+ExecPlan build_exec_plan(int t, int steps);
+
+// Fine-grained DAG of Algorithm 1 / its Sec. 3 variants: critical paths.
+void dag_critical_path(int t, int flags, int64_t out[4]);
+void dag_task_counts(int t, int64_t out[12]);
+
+}  // namespace spdinv

@@ -1,0 +1,427 @@
+// Persistent FP64 kernel for the tiled SPD inversion (Algorithm 1 of Agullo
+// et al., with the array renaming and pipelining of Sec. 3).
+//
+// One launch runs the whole tile DAG.  CTAs take tasks from a global ticket
+// counter in the planner's order (a topological order), so every task a CTA
+// waits for was taken earlier by a running CTA: no deadlock, for any grid.
+// Each task owns one output tile of one step and runs its whole commutative
+// update chain with the accumulator in registers, waiting on the device-side
+// readiness flag of each input tile just before it needs it:
+//
+//   Step 1, diagonal j      A_jj - sum_k L_jk L_jk^T, POTRF -> L_jj, TRTRI -> X_jj (store D_j)
+//   Step 1, tile (i,j)      (A_ij - sum_k L_ik L_jk^T) X_jj^T = L_ij            (store B_ij)
+//   Step 2, tile (i,j)      -(X_ii L_ij + sum_{k=i-1..j+1} X_ik L_kj) X_jj = X_ij (store C_ij)
+//   Step 3, tile (i,j)      X_ii^T X_ij + sum_{k=i+1..t-1} X_ki^T X_kj          (into A)
+//   Step 3, diagonal i      X_ii^T X_ii + sum_{k>i} X_ki^T X_ki  (lower part)   (into A)
+//
+// The renamed stores B (L), C (X = L^{-1}) and D (X_jj) are written once and
+// never overwritten, so no task has a write-after-read hazard and the three
+// steps overlap freely.  A is read once (Step 1) and written once (Step 3).
+// Step 2's right TRMM uses X_jj rather than the A_jj printed in Algorithm 1:
+// X L = I gives X_ij L_jj = -sum_{k=j+1..i} X_ik L_kj.  Step 1's TRSM is done
+// as a product with X_jj^T, the inverse Step 2 needs anyway.
+//
+// Tiles of the stores are b x b, column-major, contiguous ("tile-major") and
+// move between global and shared memory as single bulk (TMA) copies.  Ragged
+// edges (n not a multiple of b) are padded with zeros and, on the diagonal,
+// with the identity, which every step carries through unchanged.
+#include <climits>
+
+#include "kernels.h"
+#include "tile_fp64.cuh"
+
+namespace spdinv {
+
+namespace {
+
+struct WaitCtl {
+    int* ctrl;              // [0] ticket, [1] abort, [2] err, [3] info
+    long long timeout_ns;
+};
+
+__device__ __forceinline__ void raise_error(int* ctrl, int code) {
+    atomicCAS(&ctrl[2], 0, code);
+    atomicExch(&ctrl[1], 1);
+}
+
+// First failing column wins (0 = none).
+__device__ __forceinline__ void record_info(int* ctrl, int v) {
+    int cur = atomicCAS(&ctrl[3], 0, v);
+    while (cur != 0 && v < cur) {
+        const int prev = atomicCAS(&ctrl[3], cur, v);
+        if (prev == cur) break;
+        cur = prev;
+    }
+    atomicExch(&ctrl[1], 1);
+}
+
+// Bounded spin on a readiness flag (thread 0 only).  false = give up
+// (abort raised elsewhere, or this wait hit its limit: error set here).
+__device__ bool wait_flag(const int* flag, const WaitCtl& w) {
+    if (flag == nullptr) return true;
+    if (ld_acquire_gpu(flag) != 0) return true;
+    const uint64_t t0 = globaltimer_ns();
+    unsigned ns = 32;
+    for (;;) {
+        if (ld_acquire_gpu(flag) != 0) return true;
+        if (ld_relaxed_gpu(&w.ctrl[1]) != 0) return false;
+        if ((long long)(globaltimer_ns() - t0) > w.timeout_ns) {
+            raise_error(w.ctrl, SPDINV_ERR_TIMEOUT);
+            return false;
+        }
+        __nanosleep(ns);
+        if (ns < 1024) ns <<= 1;
+    }
+}
+
+template <int B>
+struct Ctx {
+    const KParamsF64* p;
+    double* T0;
+    double* T1;
+    double* tmp;
+    uint64_t* bar;
+    int* s_flag;
+    uint32_t phase;
+    WaitCtl w;
+};
+
+// Bounded wait on the CTA's mbarrier for the current phase.
+template <int B>
+__device__ bool mbar_wait_bounded(Ctx<B>& c) {
+    const uint64_t t0 = globaltimer_ns();
+    while (!mbar_try_wait(c.bar, c.phase)) {
+        if ((long long)(globaltimer_ns() - t0) > 2000000000LL) {
+            if (threadIdx.x == 0) raise_error(c.w.ctrl, SPDINV_ERR_TIMEOUT);
+            return false;
+        }
+    }
+    c.phase ^= 1u;
+    return true;
+}
+
+// Wait for up to two readiness flags, then copy up to two store tiles into
+// T0 / T1.  Called by all threads; false = stop (abort or timeout).
+template <int B>
+__device__ bool fetch(Ctx<B>& c, const int* f0, const int* f1, const double* g0, const double* g1) {
+    constexpr uint32_t kBytes = B * B * sizeof(double);
+    __syncthreads();  // every thread is done with T0 / T1
+    if (threadIdx.x == 0) {
+        const bool ok = wait_flag(f0, c.w) && wait_flag(f1, c.w);
+        *c.s_flag = ok ? 0 : 1;
+        if (ok) {
+            fence_proxy_async_global();
+            fence_proxy_async_shared();
+            mbar_arrive_expect_tx(c.bar, (g0 ? kBytes : 0u) + (g1 ? kBytes : 0u));
+            if (g0) bulk_g2s(c.T0, g0, kBytes, c.bar);
+            if (g1) bulk_g2s(c.T1, g1, kBytes, c.bar);
+        }
+    }
+    // The others wait here while thread 0 waits on the dependency flags (its
+    // own limit); the mbarrier wait below then covers only the copy itself.
+    __syncthreads();
+    if (*c.s_flag != 0) return false;
+    return mbar_wait_bounded(c);
+}
+
+template <int B>
+__device__ __forceinline__ const double* tileB(const KParamsF64& p, int i, int j) {
+    return p.Bw + ((int64_t)i * (i - 1) / 2 + j) * (int64_t)(B * B);
+}
+template <int B>
+__device__ __forceinline__ const double* tileC(const KParamsF64& p, int i, int j) {
+    return p.Cw + ((int64_t)i * (i - 1) / 2 + j) * (int64_t)(B * B);
+}
+template <int B>
+__device__ __forceinline__ const double* tileD(const KParamsF64& p, int j) {
+    return p.Dw + (int64_t)j * (B * B);
+}
+
+// Tile (ti, tj) of the column-major A into T (padded: zeros, identity on the
+// diagonal past n).  lower_only: diagonal tile, strictly upper part of A not read.
+template <int B>
+__device__ void load_A_tile(const KParamsF64& p, int ti, int tj, double* T, bool lower_only) {
+    for (int idx = threadIdx.x; idx < B * B; idx += kThreads) {
+        const int r = idx % B, c = idx / B;
+        const int64_t gr = (int64_t)ti * B + r, gc = (int64_t)tj * B + c;
+        double v;
+        if (gr < p.n && gc < p.n) v = (lower_only && r < c) ? 0.0 : p.A[gr + gc * p.lda];
+        else v = (ti == tj && r == c) ? 1.0 : 0.0;
+        T[idx] = v;
+    }
+}
+
+// T into tile (ti, tj) of A, clipped to n; lower_only keeps the upper part of A.
+template <int B>
+__device__ void store_A_tile(const KParamsF64& p, int ti, int tj, const double* T, bool lower_only) {
+    for (int idx = threadIdx.x; idx < B * B; idx += kThreads) {
+        const int r = idx % B, c = idx / B;
+        const int64_t gr = (int64_t)ti * B + r, gc = (int64_t)tj * B + c;
+        if (gr < p.n && gc < p.n && !(lower_only && r < c)) p.A[gr + gc * p.lda] = T[idx];
+    }
+}
+
+template <int B>
+__device__ void store_ws_tile(double* g, const double* T) {
+    const double2* s = reinterpret_cast<const double2*>(T);
+    double2* d = reinterpret_cast<double2*>(g);
+    for (int idx = threadIdx.x; idx < B * B / 2; idx += kThreads) d[idx] = s[idx];
+}
+
+// All threads: make the CTA's global writes visible, then raise the flag.
+template <int B>
+__device__ void publish(Ctx<B>& c, int* flag, int ticket) {
+    __syncthreads();
+    if (threadIdx.x == 0 && flag != nullptr && ticket != c.p->drop_task) {
+        __threadfence();
+        fence_proxy_async_global();
+        st_release_gpu(flag, 1);
+    }
+}
+
+template <int B>
+__global__ void __launch_bounds__(kThreads) potri_fp64_persistent(const KParamsF64 prm) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ int s_task, s_flag, s_fail;
+    const KParamsF64& p = prm;
+    Ctx<B> c;
+    c.p = &p;
+    c.T0 = reinterpret_cast<double*>(smem_raw);
+    c.T1 = c.T0 + B * B;
+    c.tmp = c.T1 + B * B;
+    c.bar = &bar;
+    c.s_flag = &s_flag;
+    c.phase = 0;
+    c.w.ctrl = p.ctrl;
+    c.w.timeout_ns = p.timeout_ns;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_proxy_async_shared();
+    }
+    __syncthreads();
+    const int t = p.t;
+    int* const fL = p.flags;                  // [t*t]  B_ij holds L_ij
+    int* const fX = p.flags + (int64_t)t * t; // [t*t]  C_ij holds X_ij
+    int* const fD = p.flags + 2 * (int64_t)t * t;  // [t]  D_j holds X_jj
+    const bool from_A = p.steps == STEPS_ALL || p.steps == STEPS_POTRF;
+    // D_i is staged before the launch for spdinv_lauum: nothing to wait for.
+    auto dflag = [&](int q) -> const int* { return p.steps == STEPS_LAUUM ? nullptr : &fD[q]; };
+
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int m = -1;
+            if (ld_relaxed_gpu(&p.ctrl[1]) == 0) {
+                m = atomicAdd(&p.ctrl[0], 1);
+                if (m >= p.ntasks) m = -1;
+            }
+            s_task = m;
+        }
+        __syncthreads();
+        const int ticket = s_task;
+        if (ticket < 0) return;
+        const uint32_t e = p.tasks[ticket];
+        const int kind = (int)task_kind(e), i = (int)task_i(e), j = (int)task_j(e);
+        Acc<B> acc;
+
+        if (kind == K_S1_DIAG) {
+            load_A_tile<B>(p, j, j, c.T0, true);
+            __syncthreads();
+            acc_load<B>(acc, c.T0);
+            for (int k = 0; k < j; ++k) {  // SYRK chain, U order
+                if (!fetch<B>(c, &fL[j * t + k], nullptr, tileB<B>(p, j, k), nullptr)) return;
+                tile_mma<B, false, true, true, FULL, FULL>(acc, c.T0, c.T0);
+            }
+            __syncthreads();
+            acc_store<B>(acc, c.T0);
+            const int fail = tile_potrf<B>(c.T0, &s_fail);
+            if (fail) {
+                if (threadIdx.x == 0) record_info(p.ctrl, j * B + fail);
+                return;
+            }
+            tile_zero_upper<B>(c.T0);
+            __syncthreads();
+            if (p.steps == STEPS_POTRF) store_A_tile<B>(p, j, j, c.T0, true);
+            tile_trtri<B>(c.T0, c.tmp);
+            store_ws_tile<B>(const_cast<double*>(tileD<B>(p, j)), c.T0);
+            publish<B>(c, &fD[j], ticket);
+        } else if (kind == K_S1_OFF) {
+            load_A_tile<B>(p, i, j, c.T0, false);
+            __syncthreads();
+            acc_load<B>(acc, c.T0);
+            for (int k = 0; k < j; ++k) {  // GEMM chain, U order
+                if (!fetch<B>(c, &fL[i * t + k], &fL[j * t + k], tileB<B>(p, i, k), tileB<B>(p, j, k))) return;
+                tile_mma<B, false, true, true, FULL, FULL>(acc, c.T0, c.T1);
+            }
+            // TRSM: L_ij = A'_ij L_jj^{-T} = A'_ij X_jj^T
+            if (!fetch<B>(c, &fD[j], nullptr, nullptr, tileD<B>(p, j))) return;
+            acc_store<B>(acc, c.T0);
+            __syncthreads();
+            acc_zero<B>(acc);
+            tile_mma<B, false, true, false, FULL, LOWER>(acc, c.T0, c.T1);
+            __syncthreads();
+            acc_store<B>(acc, c.T0);
+            __syncthreads();
+            store_ws_tile<B>(const_cast<double*>(tileB<B>(p, i, j)), c.T0);
+            if (p.steps == STEPS_POTRF) store_A_tile<B>(p, i, j, c.T0, false);
+            publish<B>(c, &fL[i * t + j], ticket);
+        } else if (kind == K_S2_DIAG) {  // spdinv_trtri: X_jj = TRTRI(A_jj)
+            load_A_tile<B>(p, j, j, c.T0, true);
+            tile_trtri<B>(c.T0, c.tmp);
+            store_ws_tile<B>(const_cast<double*>(tileD<B>(p, j)), c.T0);
+            store_A_tile<B>(p, j, j, c.T0, true);
+            publish<B>(c, &fD[j], ticket);
+        } else if (kind == K_S2_OFF) {
+            // X_ii L_ij
+            if (!fetch<B>(c, &fD[i], from_A ? &fL[i * t + j] : nullptr, tileD<B>(p, i), tileB<B>(p, i, j))) return;
+            acc_zero<B>(acc);
+            tile_mma<B, false, false, false, LOWER, FULL>(acc, c.T0, c.T1);
+            for (int k = i - 1; k > j; --k) {  // GEMM chain, D order
+                if (!fetch<B>(c, &fX[i * t + k], from_A ? &fL[k * t + j] : nullptr, tileC<B>(p, i, k),
+                              tileB<B>(p, k, j)))
+                    return;
+                tile_mma<B, false, false, false, FULL, FULL>(acc, c.T0, c.T1);
+            }
+            // X_ij = -(...) X_jj
+            if (!fetch<B>(c, &fD[j], nullptr, nullptr, tileD<B>(p, j))) return;
+            acc_store<B>(acc, c.T0);
+            __syncthreads();
+            acc_zero<B>(acc);
+            tile_mma<B, false, false, true, FULL, LOWER>(acc, c.T0, c.T1);
+            __syncthreads();
+            acc_store<B>(acc, c.T0);
+            __syncthreads();
+            store_ws_tile<B>(const_cast<double*>(tileC<B>(p, i, j)), c.T0);
+            if (p.steps == STEPS_TRTRI) store_A_tile<B>(p, i, j, c.T0, false);
+            publish<B>(c, &fX[i * t + j], ticket);
+        } else if (kind == K_S3_OFF) {
+            const bool wait_x = p.steps != STEPS_LAUUM;
+            // X_ii^T X_ij
+            if (!fetch<B>(c, dflag(i), wait_x ? &fX[i * t + j] : nullptr, tileD<B>(p, i), tileC<B>(p, i, j))) return;
+            acc_zero<B>(acc);
+            tile_mma<B, true, false, false, LOWER, FULL>(acc, c.T0, c.T1);
+            for (int k = i + 1; k < t; ++k) {  // GEMM chain, U order
+                if (!fetch<B>(c, wait_x ? &fX[k * t + i] : nullptr, wait_x ? &fX[k * t + j] : nullptr,
+                              tileC<B>(p, k, i), tileC<B>(p, k, j)))
+                    return;
+                tile_mma<B, true, false, false, FULL, FULL>(acc, c.T0, c.T1);
+            }
+            __syncthreads();
+            acc_store<B>(acc, c.T0);
+            __syncthreads();
+            store_A_tile<B>(p, i, j, c.T0, false);
+        } else {  // K_S3_DIAG
+            const bool wait_x = p.steps != STEPS_LAUUM;
+            // LAUUM: X_ii^T X_ii
+            if (!fetch<B>(c, dflag(i), nullptr, tileD<B>(p, i), nullptr)) return;
+            acc_zero<B>(acc);
+            tile_mma<B, true, false, false, LOWER, LOWER>(acc, c.T0, c.T0);
+            for (int k = i + 1; k < t; ++k) {  // SYRK chain, U order
+                if (!fetch<B>(c, wait_x ? &fX[k * t + i] : nullptr, nullptr, tileC<B>(p, k, i), nullptr)) return;
+                tile_mma<B, true, false, false, FULL, FULL>(acc, c.T0, c.T0);
+            }
+            __syncthreads();
+            acc_store<B>(acc, c.T0);
+            __syncthreads();
+            store_A_tile<B>(p, i, i, c.T0, true);
+        }
+    }
+}
+
+// Copies A's tiles into the renamed stores for the standalone steps:
+// lower-triangular tiles below the diagonal into dst (B or C), diagonal tiles
+// (lower part, identity padding) into D when diag != nullptr.  For TRTRI it
+// also records the first exactly-zero diagonal entry (LAPACK dtrtri), which
+// makes the main kernel leave A untouched.
+template <int B>
+__global__ void __launch_bounds__(kThreads) stage_in_fp64(const KParamsF64 p, double* dst, double* diag,
+                                                          int check_zero_diag) {
+    const int t = p.t;
+    const int64_t ntri = (int64_t)t * (t - 1) / 2;
+    for (int64_t tile = blockIdx.x; tile < ntri + t; tile += gridDim.x) {
+        int ti, tj;
+        bool is_diag = tile >= ntri;
+        if (is_diag) {
+            ti = tj = (int)(tile - ntri);
+            if (diag == nullptr && !check_zero_diag) continue;
+        } else {
+            // tile = ti*(ti-1)/2 + tj
+            ti = (int)((1.0 + sqrt(1.0 + 8.0 * (double)tile)) / 2.0);
+            while ((int64_t)ti * (ti - 1) / 2 > tile) --ti;
+            while ((int64_t)(ti + 1) * ti / 2 <= tile) ++ti;
+            tj = (int)(tile - (int64_t)ti * (ti - 1) / 2);
+        }
+        double* out = is_diag ? (diag ? diag + (int64_t)ti * B * B : nullptr) : dst + tile * (int64_t)(B * B);
+        for (int idx = threadIdx.x; idx < B * B; idx += kThreads) {
+            const int r = idx % B, cc = idx / B;
+            const int64_t gr = (int64_t)ti * B + r, gc = (int64_t)tj * B + cc;
+            double v;
+            if (gr < p.n && gc < p.n) v = (is_diag && r < cc) ? 0.0 : p.A[gr + gc * p.lda];
+            else v = (is_diag && r == cc) ? 1.0 : 0.0;
+            if (is_diag && check_zero_diag && r == cc && gr < p.n && v == 0.0) record_info(p.ctrl, (int)gr + 1);
+            if (out) out[idx] = v;
+        }
+    }
+}
+
+__global__ void finalize_info(const int* ctrl, int* d_info) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        const int err = ctrl[2], info = ctrl[3];
+        *d_info = err != 0 ? err : info;
+    }
+}
+
+template <int B>
+int smem_bytes() {
+    return (2 * B * B + kThreads) * (int)sizeof(double);
+}
+
+template <int B>
+cudaError_t launch_impl(const KParamsF64& p, int ctas_per_sm, int num_sms, cudaStream_t s, int* grid_out) {
+    auto kern = potri_fp64_persistent<B>;
+    const int sm = smem_bytes<B>();
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    if (e != cudaSuccess) return e;
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, sm);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) return cudaErrorInvalidConfiguration;
+    int per = ctas_per_sm > 0 ? ctas_per_sm : (B >= 64 ? 3 : 6);
+    per = per < occ ? per : occ;
+    int grid = num_sms * per;
+    if (grid > p.ntasks) grid = p.ntasks > 0 ? p.ntasks : 1;
+    *grid_out = grid;
+    if (p.steps == STEPS_TRTRI || p.steps == STEPS_LAUUM) {
+        const int64_t ntiles = (int64_t)p.t * (p.t + 1) / 2;
+        const int g2 = (int)(ntiles < 4096 ? ntiles : 4096);
+        if (p.steps == STEPS_TRTRI)
+            stage_in_fp64<B><<<g2, kThreads, 0, s>>>(p, p.Bw, nullptr, 1);
+        else
+            stage_in_fp64<B><<<g2, kThreads, 0, s>>>(p, p.Cw, p.Dw, 0);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    kern<<<grid, kThreads, sm, s>>>(p);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_potri_fp64(const KParamsF64& p, int ctas_per_sm, int num_sms, int* d_info, cudaStream_t s,
+                              int* grid_out) {
+    cudaError_t e;
+    switch (p.b) {
+        case 32: e = launch_impl<32>(p, ctas_per_sm, num_sms, s, grid_out); break;
+        case 64: e = launch_impl<64>(p, ctas_per_sm, num_sms, s, grid_out); break;
+        default: return cudaErrorInvalidValue;
+    }
+    if (e != cudaSuccess) return e;
+    if (d_info) {
+        finalize_info<<<1, 32, 0, s>>>(p.ctrl, d_info);
+        e = cudaGetLastError();
+    }
+    return e;
+}
+
+}  // namespace spdinv

@@ -68,7 +68,8 @@ def spectral_spd(n, cond, seed, device=None):
     lt = torch.from_numpy(lam).to(Q.device)
     A = (Q * lt) @ Q.T
     A = 0.5 * (A + A.T)
-    return A, Q, lam
+    # A is exactly symmetric: its transpose is the column-major view of it
+    return A.t(), Q, lam
 
 
 def tridiag(n):

@@ -1,0 +1,167 @@
+"""Host planner: the paper's task DAG (Table 1, Sec. 3) and the execution
+plan of the persistent kernel (a topological order of the chain tasks)."""
+import os
+import re
+
+import pytest
+
+from paper_1002_4057_gb300 import _lib as L
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "table1_critical_path.txt")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    from paper_1002_4057_gb300 import build
+    build.build()
+    return L.lib()
+
+
+def _eval(expr, t):
+    e = re.sub(r"(\d)t", r"\1*t", expr.replace("^", "**"))
+    v = eval(e, {"t": t})
+    assert v == int(v)
+    return int(v)
+
+
+def _golden():
+    rows = {}
+    for line in open(GOLDEN):
+        line = line.strip()
+        if line and not line.startswith("#"):
+            parts = line.split()
+            rows[parts[0]] = parts[1:]
+    return rows
+
+
+TS = list(range(2, 17)) + [24, 32, 48]
+
+
+@pytest.mark.parametrize("t", TS)
+def test_table1(t):
+    g = _golden()
+    _, inplace = L.spdinv_dag_critical_path(t, 0)
+    _, oop = L.spdinv_dag_critical_path(t, L.SPDINV_DAG_OUT_OF_PLACE)
+    for s in range(3):
+        ip_expr, oop_expr = g["step%d" % (s + 1)]
+        assert inplace[s] == _eval(ip_expr, t)
+        assert oop[s] == _eval(oop_expr, t)
+
+
+@pytest.mark.parametrize("t", TS)
+def test_loop_reversal_uuu(t):
+    g = _golden()
+    _, ip = L.spdinv_dag_critical_path(t, L.SPDINV_DAG_UUU)
+    _, oop = L.spdinv_dag_critical_path(t, L.SPDINV_DAG_UUU | L.SPDINV_DAG_OUT_OF_PLACE)
+    assert ip[1] == _eval(g["uuu_step2"][0], t)
+    assert oop[1] == _eval(g["uuu_step2"][1], t)
+    # UUU never beats UDU
+    _, udu = L.spdinv_dag_critical_path(t, 0)
+    assert ip[1] >= udu[1]
+
+
+@pytest.mark.parametrize("t", TS)
+def test_pipelining(t):
+    g = _golden()
+    flags = L.SPDINV_DAG_OUT_OF_PLACE | L.SPDINV_DAG_RENAME_DIAG
+    _, unp = L.spdinv_dag_critical_path(t, flags)
+    _, pip = L.spdinv_dag_critical_path(t, flags | L.SPDINV_DAG_PIPELINE)
+    assert unp[3] == _eval(g["oop_unpipelined"][0], t)
+    assert pip[3] == _eval(g["oop_pipelined"][0], t)
+    _, ipu = L.spdinv_dag_critical_path(t, 0)
+    assert ipu[3] == _eval(g["inplace_unpipelined"][0], t)
+    # pipelining never lengthens the path
+    _, ipp = L.spdinv_dag_critical_path(t, L.SPDINV_DAG_PIPELINE)
+    assert ipp[3] <= ipu[3]
+
+
+def _alg1_counts(t):
+    """Counts the tasks of each kind by walking Algorithm 1's loop nest."""
+    c = [0] * 12
+    for j in range(t):
+        c[2] += j                      # SYRK(j,k), k<j
+        c[0] += 1                      # POTRF(j)
+        c[3] += (t - j - 1) * j        # GEMM(i,j,k)
+        c[1] += t - j - 1              # TRSM(i,j)
+    for j in range(t - 1, -1, -1):
+        c[4] += 1                      # TRTRI(j)
+        for i in range(t - 1, j, -1):
+            c[5] += 1                  # TRMM(i,j) left
+            c[6] += i - j - 1          # GEMM(i,j,k)
+            c[7] += 1                  # TRMM(i,j) right
+    for i in range(t):
+        c[8] += i                      # TRMM(i,j), j<i
+        c[9] += 1                      # LAUUM(i)
+        c[10] += i * (t - i - 1)       # GEMM(i,j,k)
+        c[11] += t - i - 1             # SYRK(i,k)
+    return c
+
+
+@pytest.mark.parametrize("t", [1, 2, 3, 7, 20])
+def test_task_counts(t):
+    st, c = L.spdinv_dag_task_counts(t)
+    assert st == 0
+    assert c == _alg1_counts(t)
+    # every step does n^3/3 flops: leading terms sum to t^3 tile products
+    assert c[3] == t * (t - 1) * (t - 2) // 6
+
+
+def _deps(kind, i, j, t, steps):
+    """Tasks whose output (kind, i, j) reads, written out from the chain
+    definitions of the three steps (independent of the C++ planner)."""
+    s1 = steps in (0, 1)
+    s2 = steps in (0, 2)
+    d = []
+    D = (lambda q: [(0, q, q)]) if s1 else ((lambda q: [(2, q, q)]) if steps == 2 else (lambda q: []))
+    Lt = (lambda a, b: [(1, a, b)]) if s1 else (lambda a, b: [])
+    Xt = (lambda a, b: [(3, a, b)]) if s2 else (lambda a, b: [])
+    if kind == 0:
+        for k in range(j):
+            d += Lt(j, k)
+    elif kind == 1:
+        for k in range(j):
+            d += Lt(i, k) + Lt(j, k)
+        d += D(j)
+    elif kind == 3:
+        d += D(i) + Lt(i, j) + D(j)
+        for k in range(j + 1, i):
+            d += Xt(i, k) + Lt(k, j)
+    elif kind == 4:
+        d += D(i)
+        for k in range(i + 1, t):
+            d += Xt(k, i)
+    elif kind == 5:
+        d += D(i) + Xt(i, j)
+        for k in range(i + 1, t):
+            d += Xt(k, i) + Xt(k, j)
+    return d
+
+
+@pytest.mark.parametrize("n,b,steps", [(512, 64, 0), (1000, 32, 0), (700, 64, 1), (700, 64, 2),
+                                       (700, 64, 3), (33, 32, 0), (1, 32, 0)])
+def test_exec_plan_is_topological_and_complete(n, b, steps):
+    st, tasks, crit = L.spdinv_plan_tasks(n, b, steps)
+    assert st == 0
+    t = (n + b - 1) // b
+    dec = [((e >> 28), (e >> 14) & 0x3FFF, e & 0x3FFF) for e in tasks]
+    pos = {d: m for m, d in enumerate(dec)}
+    assert len(pos) == len(dec)  # no duplicates
+    expect = set()
+    if steps in (0, 1):
+        expect |= {(0, j, j) for j in range(t)} | {(1, i, j) for i in range(t) for j in range(i)}
+    if steps == 2:
+        expect |= {(2, j, j) for j in range(t)}
+    if steps in (0, 2):
+        expect |= {(3, i, j) for i in range(t) for j in range(i)}
+    if steps in (0, 3):
+        expect |= {(4, i, i) for i in range(t)} | {(5, i, j) for i in range(t) for j in range(i)}
+    assert set(dec) == expect
+    for m, (k, i, j) in enumerate(dec):
+        for dep in _deps(k, i, j, t, steps):
+            assert pos[dep] < m, (dec[m], dep)
+    assert crit > 0
+
+
+def test_exec_plan_puts_the_critical_path_first():
+    _, tasks, _ = L.spdinv_plan_tasks(64 * 16, 64, 0)
+    assert tasks[0] >> 28 == 0 and (tasks[0] & 0x3FFF) == 0  # Step-1 diagonal tile 0
