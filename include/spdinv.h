@@ -130,6 +130,34 @@ SPDINV_API spdinv_status spdinv_potri_ex(int64_t n, double* dA, int64_t lda, con
                               int* d_info, cudaStream_t stream);
 
 /* ------------------------------------------------------------------------
+ * Inversion without device allocation (the paper has no counterpart)
+ * ------------------------------------------------------------------------ */
+
+/* Largest n spdinv_potri_noalloc accepts. */
+#define SPDINV_NOALLOC_MAX_N 1024
+
+/* spdinv_potri (FP64, tile 32) for callers that must not allocate device
+ * memory.  Some callers cannot call cudaMalloc: code that runs while a
+ * stream is being captured into a CUDA graph (cudaMalloc is not a stream
+ * operation and is refused during capture), plug-ins whose host application
+ * owns all device memory through its own allocator or a fixed budget, and
+ * latency-bound loops in which an allocation, which can synchronise the whole
+ * device, would stall other streams.  This entry point allocates nothing: its
+ * scratch (status words, readiness flags, the renamed tile stores and the
+ * task list, about 8 MiB) is one fixed array in the library's device memory,
+ * which every GPU that loads the library holds until the process exits.
+ * The caller still passes A and d_info as for spdinv_potri.
+ *  - n > SPDINV_NOALLOC_MAX_N returns SPDINV_ERR_N and launches nothing.
+ *  - The first call on a device (with that device current) looks up the
+ *    array's device address; make that first call before any stream capture.
+ *  - Every call uses the same array, which keeps the last call's contents
+ *    (the call clears what must start at zero).  Calls whose GPU work
+ *    overlaps in time -- on different streams, or from different threads --
+ *    race on the array and give wrong results; order them on one stream. */
+SPDINV_API spdinv_status spdinv_potri_noalloc(int64_t n, double* dA, int64_t lda, int* d_info,
+                                              cudaStream_t stream);
+
+/* ------------------------------------------------------------------------
  * Many independent matrices of uneven sizes in one persistent launch
  * ------------------------------------------------------------------------ */
 

@@ -29,6 +29,8 @@ SPDINV_PREC_FP64 = 0
 SPDINV_PREC_MIXED_FP32 = 1
 SPDINV_PREC_MIXED_BF16X3 = 2
 
+SPDINV_NOALLOC_MAX_N = 1024
+
 SPDINV_DAG_OUT_OF_PLACE = 1
 SPDINV_DAG_RENAME_DIAG = 2
 SPDINV_DAG_UUU = 4
@@ -51,6 +53,7 @@ SIGNATURES = {
     "spdinv_lauum": (c_int, [c_int64, P, c_int64, P]),
     "spdinv_potri": (c_int, [c_int64, P, c_int64, P, P]),
     "spdinv_potri_ex": (c_int, [c_int64, P, c_int64, ctypes.POINTER(spdinv_opts), P, P]),
+    "spdinv_potri_noalloc": (c_int, [c_int64, P, c_int64, P, P]),
     "spdinv_potri_batched": (c_int, [c_int, P, P, P, P, P]),
     "spdinv_spotri_batched": (c_int, [c_int, P, P, P, P, P]),
     "spdinv_potri_backward": (c_int, [c_int, c_int64, P, c_int64, c_int64, P, c_int64, c_int64,
@@ -106,6 +109,10 @@ def spdinv_potri(n, dA, lda, d_info, stream):
 
 def spdinv_potri_ex(n, dA, lda, opts, d_info, stream):
     return _call("spdinv_potri_ex", n, dA, lda, ctypes.byref(opts) if opts is not None else None, d_info, stream)
+
+
+def spdinv_potri_noalloc(n, dA, lda, d_info, stream):
+    return _call("spdinv_potri_noalloc", n, dA, lda, d_info, stream)
 
 
 def spdinv_potri_batched(batch, h_n, d_Aptrs, h_lda, d_info, stream):
