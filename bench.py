@@ -45,6 +45,11 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="fp64",
+                    choices=["fp64", "batched64", "batched32", "backward64", "backward32"],
+                    help="fp64 (default, the headline line): one n x n FP64 inversion per step; "
+                         "batched*: 4096 matrices n ~ U{16..256} per step, one graph-captured launch; "
+                         "backward*: forward + backward of 256 matrices n = 512")
     return ap.parse_args()
 
 
@@ -165,11 +170,118 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def timed_steps(fn, steps, warmup, stream):
+    import torch
+    for _ in range(max(warmup, 3)):
+        fn()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def run_secondary(args):
+    """Measurement lines for the batched and backward workloads (not the
+    headline line): Gflop/s with sum(n^3) per batch, or 3 n^3 per matrix for
+    the backward (two products, the second over the lower half)."""
+    import numpy as np
+    import torch
+
+    import spd_inputs as si
+    from paper_1002_4057_gb300 import _lib as L
+    from paper_1002_4057_gb300 import torch_api as T
+
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    clk = ClockSampler(0)
+    if args.workload.startswith("batched"):
+        dtype = torch.float64 if args.workload == "batched64" else torch.float32
+        sizes = si.batch_sizes(4096, 16, 256, seed=si.SEED_BASE + 3)
+        hs = si.wishart_batch(sizes, 0.1, si.SEED_BASE + 3)
+        total = int(sum(a.shape[0] ** 2 for a in hs))
+        pool = torch.empty(total, dtype=dtype, device=dev)
+        mats, off = [], 0
+        for a in hs:
+            n = a.shape[0]
+            v = pool[off:off + n * n].as_strided((n, n), (1, n))
+            v.copy_(torch.from_numpy(a).to(dtype))
+            mats.append(v)
+            off += n * n
+        pristine = pool.clone()
+        pb = T.PreparedBatch(mats)
+        pb.run()
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            pb.run()
+
+        def step():
+            pool.copy_(pristine)
+            g.replay()
+
+        launches0 = L.spdinv_kernel_launches()
+        clk.start()
+        ms = timed_steps(step, args.steps, args.warmup, stream)
+        clocks = clk.stop()
+        assert int(pb.info.abs().sum().item()) == 0
+        flops = float(sum(int(n) ** 3 for n in sizes))
+        e_inv = timed_steps(lambda: g.replay(), args.steps, 1, stream)
+        st, tiles = L.spdinv_batched_tiles(1 if dtype == torch.float32 else 0)
+        line = {"workload": args.workload, "metric": METRIC, "value": round(flops / (ms * 1e-3) / 1e9, 3),
+                "unit": "Gflop/s", "ms_per_step": round(ms, 4), "ms_per_batch_launch": round(e_inv, 4),
+                "value_launch_only": round(flops / (e_inv * 1e-3) / 1e9, 3),
+                "dtype": "f64" if dtype == torch.float64 else "f32", "flops_per_step": flops,
+                "config": {"matrices": 4096, "n": "U{16..256}", "generator": "B B^T/n + 0.1 I",
+                           "step": "restore the batch (device copy) + one graph replay of spdinv_*potri_batched",
+                           "autotuned_tiles_by_32_class": tiles},
+                "clocks": clocks, "gpu_launches_per_step": (L.spdinv_kernel_launches() - launches0)}
+    else:
+        dtype = torch.float64 if args.workload == "backward64" else torch.float32
+        n, b = 512, 256
+        As = np.stack([si.wishart_spd(n, 1.0, seed=si.SEED_BASE + 4 * 1000 + k) for k in range(b)])
+        Gs = np.stack([si.symmetric_gaussian(n, seed=si.SEED_BASE + 4 * 2000 + k) for k in range(b)])
+        dA = torch.from_numpy(As).to(dev, dtype)
+        dG = torch.from_numpy(Gs).to(dev, dtype)
+        X = T.spd_inverse(dA)
+        grad = torch.empty_like(dA)
+        fn = L.spdinv_potri_backward if dtype == torch.float64 else L.spdinv_spotri_backward
+
+        def bwd():
+            st = fn(b, n, X.data_ptr(), n, n * n, dG.data_ptr(), n, n * n, grad.data_ptr(), n, n * n,
+                    stream.cuda_stream)
+            assert st == 0
+
+        def fwd():
+            T.spd_inverse(dA)
+
+        clk.start()
+        ms_b = timed_steps(bwd, args.steps, args.warmup, stream)
+        ms_f = timed_steps(fwd, args.steps, args.warmup, stream)
+        clocks = clk.stop()
+        line = {"workload": args.workload, "metric": METRIC,
+                "value": round(3.0 * b * n ** 3 / (ms_b * 1e-3) / 1e9, 3), "unit": "Gflop/s (3 n^3 per grad)",
+                "ms_backward": round(ms_b, 4), "ms_forward": round(ms_f, 4),
+                "forward_gflops": round(b * n ** 3 / (ms_f * 1e-3) / 1e9, 3),
+                "dtype": "f64" if dtype == torch.float64 else "f32",
+                "config": {"matrices": b, "n": n, "generator": "B B^T/n + I; G = sym(N(0,1))"},
+                "clocks": clocks}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.workload != "fp64":
+        if rank == 0:
+            run_secondary(args)
         return
 
     # CPU baseline first (threads only; before any GPU work)

@@ -200,6 +200,23 @@ SPDINV_API spdinv_status spdinv_spotri_backward(int batch, int64_t n, const floa
                                      float* dGrad, int64_t ldgrad, int64_t stride_grad,
                                      cudaStream_t stream);
 
+/* The autotuner's tile choice for spdinv_potri_batched (fp32 == 0) or
+ * spdinv_spotri_batched (fp32 != 0): tiles[c] is the tile order used for
+ * matrices with 32c < n <= 32(c+1) (c = 7 also for n > 256).  The first call
+ * per device and precision times every candidate tile on synthetic batches
+ * (this allocates, synchronises, and must come before any graph capture);
+ * SPDINV_BATCHED_TILE=16|32|64 in the environment forces one tile. */
+SPDINV_API spdinv_status spdinv_batched_tiles(int fp32, int tiles[8]);
+
+/* Copies the lower triangle of `batch` column-major n x n matrices onto their
+ * strictly upper triangle (A_ij = A_ji, i < j); matrix k starts at element
+ * k*stride.  Used to form the full symmetric A^{-1} (no counterpart in the
+ * paper, whose result is the lower triangle). */
+SPDINV_API spdinv_status spdinv_mirror_lower(int batch, int64_t n, double* dA, int64_t lda, int64_t stride,
+                                             cudaStream_t stream);
+SPDINV_API spdinv_status spdinv_smirror_lower(int batch, int64_t n, float* dA, int64_t lda, int64_t stride,
+                                              cudaStream_t stream);
+
 /* ------------------------------------------------------------------------
  * Host-side planner queries (no GPU needed)
  * ------------------------------------------------------------------------ */

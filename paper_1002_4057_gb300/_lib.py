@@ -60,6 +60,9 @@ SIGNATURES = {
                                       P, c_int64, c_int64, P]),
     "spdinv_spotri_backward": (c_int, [c_int, c_int64, P, c_int64, c_int64, P, c_int64, c_int64,
                                        P, c_int64, c_int64, P]),
+    "spdinv_batched_tiles": (c_int, [c_int, P]),
+    "spdinv_mirror_lower": (c_int, [c_int, c_int64, P, c_int64, c_int64, P]),
+    "spdinv_smirror_lower": (c_int, [c_int, c_int64, P, c_int64, c_int64, P]),
     "spdinv_dag_critical_path": (c_int, [c_int, c_int, P]),
     "spdinv_dag_task_counts": (c_int, [c_int, P]),
     "spdinv_plan_tasks": (c_int, [c_int64, c_int, c_int, P, c_int64, P, P]),
@@ -129,6 +132,20 @@ def spdinv_potri_backward(batch, n, dX, ldx, sx, dG, ldg, sg, dGrad, ldgr, sgr, 
 
 def spdinv_spotri_backward(batch, n, dX, ldx, sx, dG, ldg, sg, dGrad, ldgr, sgr, stream):
     return _call("spdinv_spotri_backward", batch, n, dX, ldx, sx, dG, ldg, sg, dGrad, ldgr, sgr, stream)
+
+
+def spdinv_batched_tiles(fp32):
+    out = (ctypes.c_int * 8)()
+    st = _call("spdinv_batched_tiles", int(fp32), ctypes.addressof(out))
+    return st, list(out)
+
+
+def spdinv_mirror_lower(batch, n, dA, lda, stride, stream):
+    return _call("spdinv_mirror_lower", batch, n, dA, lda, stride, stream)
+
+
+def spdinv_smirror_lower(batch, n, dA, lda, stride, stream):
+    return _call("spdinv_smirror_lower", batch, n, dA, lda, stride, stream)
 
 
 def spdinv_dag_critical_path(t, flags):

@@ -1,0 +1,216 @@
+// Backward of the inversion (an added form; the paper has only the forward
+// method): for f(A) with X = A^{-1} and incoming gradient G = df/dX,
+//   d(A^{-1}) = -X dA X   =>   grad_A = -X sym(G) X,   sym(G) = (G + G^T)/2,
+// which is -sym(X G X) for symmetric X.  Two tiled products per matrix:
+//   phase 0:  Y = X sym(G)              (sym(G) formed while staging G's tiles)
+//   phase 1:  grad = -Y X, lower tiles only, each written to (i, j) and,
+//             transposed, to (j, i); the diagonal tiles are averaged with
+//             their transpose, so grad is exactly symmetric.
+// FP64 uses the tensor-core MMA tile products, FP32 the CUDA-core ones.
+#include <cuda_runtime.h>
+
+#include <map>
+#include <mutex>
+
+#include "../../include/spdinv.h"
+#include "api_internal.h"
+#include "tile_f32.cuh"
+#include "tile_fp64.cuh"
+
+namespace spdinv {
+namespace {
+
+constexpr int BB = 64;  // output tile
+
+template <typename T>
+struct BwdTile;
+template <>
+struct BwdTile<double> {
+    using Acc = spdinv::Acc<BB>;
+    static constexpr int LD = BB;
+};
+template <>
+struct BwdTile<float> {
+    using Acc = Acc32<BB>;
+    static constexpr int LD = BB + 1;
+};
+
+template <typename T>
+struct BwdParams {
+    int64_t n;
+    int t;
+    const T* X;
+    int64_t ldx, sx;
+    const T* G;
+    int64_t ldg, sg;
+    T* Y;  // workspace, n x n per matrix, ld n
+    T* grad;
+    int64_t ldr, sr;
+};
+
+// Tile (ti, tj) of a column-major matrix, zero-padded past n.
+template <typename T>
+__device__ __forceinline__ void load_tile(const T* M, int64_t n, int64_t ld, int ti, int tj, T* S) {
+    constexpr int LD = BwdTile<T>::LD;
+    for (int idx = threadIdx.x; idx < BB * BB; idx += kThreads) {
+        const int r = idx % BB, c = idx / BB;
+        const int64_t gr = (int64_t)ti * BB + r, gc = (int64_t)tj * BB + c;
+        S[c * LD + r] = (gr < n && gc < n) ? M[gr + gc * ld] : T(0);
+    }
+}
+
+// Tile (ti, tj) of sym(G) = (G + G^T)/2.
+template <typename T>
+__device__ __forceinline__ void load_sym_tile(const T* G, int64_t n, int64_t ld, int ti, int tj, T* S) {
+    constexpr int LD = BwdTile<T>::LD;
+    for (int idx = threadIdx.x; idx < BB * BB; idx += kThreads) {
+        const int r = idx % BB, c = idx / BB;
+        const int64_t gr = (int64_t)ti * BB + r, gc = (int64_t)tj * BB + c;
+        S[c * LD + r] = (gr < n && gc < n) ? T(0.5) * (G[gr + gc * ld] + G[gc + gr * ld]) : T(0);
+    }
+}
+
+template <typename T, int PHASE>
+__global__ void __launch_bounds__(kThreads) backward_kernel(const BwdParams<T> p) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int LD = BwdTile<T>::LD;
+    T* S0 = reinterpret_cast<T*>(smem_raw);
+    T* S1 = S0 + BB * LD;
+    const int64_t mat = blockIdx.y;
+    int ti, tj;
+    if (PHASE == 0) {
+        ti = blockIdx.x % p.t;
+        tj = blockIdx.x / p.t;
+    } else {  // lower tiles: blockIdx.x = ti (ti + 1) / 2 + tj
+        ti = (int)((sqrt(8.0 * blockIdx.x + 1.0) - 1.0) / 2.0);
+        while ((ti + 1) * (ti + 2) / 2 <= (int)blockIdx.x) ++ti;
+        while (ti * (ti + 1) / 2 > (int)blockIdx.x) --ti;
+        tj = blockIdx.x - ti * (ti + 1) / 2;
+    }
+    const T* X = p.X + mat * p.sx;
+    const T* G = p.G + mat * p.sg;
+    T* Y = p.Y + mat * p.n * p.n;
+    typename BwdTile<T>::Acc acc;
+    acc_zero<BB>(acc);
+    for (int kt = 0; kt < p.t; ++kt) {
+        __syncthreads();
+        if (PHASE == 0) {
+            load_tile<T>(X, p.n, p.ldx, ti, kt, S0);
+            load_sym_tile<T>(G, p.n, p.ldg, kt, tj, S1);
+        } else {
+            load_tile<T>(Y, p.n, p.n, ti, kt, S0);
+            load_tile<T>(X, p.n, p.ldx, kt, tj, S1);
+        }
+        __syncthreads();
+        tile_mma<BB, false, false, PHASE == 1, FULL, FULL>(acc, S0, S1);
+    }
+    __syncthreads();
+    acc_store<BB>(acc, S0);
+    __syncthreads();
+    if (PHASE == 0) {
+        for (int idx = threadIdx.x; idx < BB * BB; idx += kThreads) {
+            const int r = idx % BB, c = idx / BB;
+            const int64_t gr = (int64_t)ti * BB + r, gc = (int64_t)tj * BB + c;
+            if (gr < p.n && gc < p.n) Y[gr + gc * p.n] = S0[c * LD + r];
+        }
+    } else {
+        T* R = p.grad + mat * p.sr;
+        for (int idx = threadIdx.x; idx < BB * BB; idx += kThreads) {
+            const int r = idx % BB, c = idx / BB;
+            const int64_t gr = (int64_t)ti * BB + r, gc = (int64_t)tj * BB + c;
+            if (gr >= p.n || gc >= p.n) continue;
+            if (ti == tj) {
+                R[gr + gc * p.ldr] = T(0.5) * (S0[c * LD + r] + S0[r * LD + c]);
+            } else {
+                R[gr + gc * p.ldr] = S0[c * LD + r];
+            }
+        }
+        if (ti != tj) {  // mirror: grad(j, i) = grad(i, j)^T, coalesced along the target's rows
+            for (int idx = threadIdx.x; idx < BB * BB; idx += kThreads) {
+                const int r = idx % BB, c = idx / BB;  // target element (tj*B + r, ti*B + c)
+                const int64_t gr = (int64_t)tj * BB + r, gc = (int64_t)ti * BB + c;
+                if (gr < p.n && gc < p.n) R[gr + gc * p.ldr] = S0[r * LD + c];
+            }
+        }
+    }
+}
+
+struct BwdState {
+    std::mutex mu;
+    void* ws = nullptr;
+    size_t bytes = 0;
+};
+
+BwdState& bwd_state(int dev) {
+    static std::mutex mu;
+    static std::map<int, BwdState*> m;
+    std::lock_guard<std::mutex> lk(mu);
+    auto& s = m[dev];
+    if (!s) s = new BwdState();
+    return *s;
+}
+
+template <typename T>
+spdinv_status run_backward(int batch, int64_t n, const T* dX, int64_t ldx, int64_t sx, const T* dG, int64_t ldg,
+                           int64_t sg, T* dGrad, int64_t ldr, int64_t sr, cudaStream_t stream) {
+    if (batch < 0 || n < 0) return SPDINV_ERR_N;
+    const int64_t mn = n > 1 ? n : 1;
+    if (ldx < mn || ldg < mn || ldr < mn) return SPDINV_ERR_LDA;
+    if (batch == 0 || n == 0) return SPDINV_OK;
+    if (!dX || !dG || !dGrad) return SPDINV_ERR_NULL;
+    if (batch > 65535) return SPDINV_ERR_N;
+    const int64_t t = (n + BB - 1) / BB;
+    if (t * (t + 1) / 2 > 2147483647LL || t * t > 2147483647LL) return SPDINV_ERR_N;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e);
+    BwdState& st = bwd_state(dev);
+    std::lock_guard<std::mutex> lk(st.mu);
+    const size_t need = sizeof(T) * (size_t)n * n * batch;
+    if (need > st.bytes) {
+        if (st.ws) {
+            e = cudaDeviceSynchronize();
+            if (e != cudaSuccess) return cuda_fail(e);
+            cudaFree(st.ws);
+            st.ws = nullptr;
+            st.bytes = 0;
+        }
+        e = cudaMalloc(&st.ws, need);
+        if (e != cudaSuccess) return cuda_fail(e);
+        st.bytes = need;
+    }
+    BwdParams<T> p{n, (int)t, dX, ldx, sx, dG, ldg, sg, static_cast<T*>(st.ws), dGrad, ldr, sr};
+    const int sm = 2 * BB * BwdTile<T>::LD * (int)sizeof(T);
+    auto k0 = backward_kernel<T, 0>;
+    auto k1 = backward_kernel<T, 1>;
+    e = cudaFuncSetAttribute(k0, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    if (e != cudaSuccess) return cuda_fail(e);
+    k0<<<dim3((unsigned)(t * t), (unsigned)batch), kThreads, sm, stream>>>(p);
+    k1<<<dim3((unsigned)(t * (t + 1) / 2), (unsigned)batch), kThreads, sm, stream>>>(p);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e);
+    count_launches(2);
+    return SPDINV_OK;
+}
+
+}  // namespace
+}  // namespace spdinv
+
+using namespace spdinv;
+
+extern "C" {
+
+SPDINV_API spdinv_status spdinv_potri_backward(int batch, int64_t n, const double* dX, int64_t ldx, int64_t sx,
+                                               const double* dG, int64_t ldg, int64_t sg, double* dGrad,
+                                               int64_t ldr, int64_t sr, cudaStream_t stream) {
+    return run_backward<double>(batch, n, dX, ldx, sx, dG, ldg, sg, dGrad, ldr, sr, stream);
+}
+
+SPDINV_API spdinv_status spdinv_spotri_backward(int batch, int64_t n, const float* dX, int64_t ldx, int64_t sx,
+                                                const float* dG, int64_t ldg, int64_t sg, float* dGrad,
+                                                int64_t ldr, int64_t sr, cudaStream_t stream) {
+    return run_backward<float>(batch, n, dX, ldx, sx, dG, ldg, sg, dGrad, ldr, sr, stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,473 @@
+// Many independent SPD matrices of uneven sizes, inverted in ONE persistent
+// launch.  Each CTA takes the next matrix from a device queue ordered by
+// decreasing n (largest first, so the long jobs start early and the short
+// ones fill the tail) and runs the three steps of Algorithm 1 (Sec. 2) on it
+// with b x b tiles, one tile operation after another.  Executed in the
+// algorithm's own sequential order the in-place updates have no hazards
+// (Step 2 walks i downwards, Step 3 walks i upwards, exactly as Algorithm 1
+// prints them), so a matrix needs no workspace, flags or waits: only barriers
+// between tile operations.  The inverted diagonal tile X_jj is kept in place
+// of L_jj from Step 1 on; nothing after Step 1 reads L_jj.
+//
+// The tile size of each matrix comes from the autotuner's table for its size
+// class.  FP64 uses the tensor-core MMA tile products, FP32 the CUDA-core ones.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <numeric>
+#include <vector>
+
+#include "../../include/spdinv.h"
+#include "api_internal.h"
+#include "tile_f32.cuh"
+#include "tile_fp64.cuh"
+
+namespace spdinv {
+namespace {
+
+template <typename T, int B>
+struct Tile;
+template <int B>
+struct Tile<double, B> {
+    using Acc = spdinv::Acc<B>;
+    static constexpr int LD = B;
+};
+template <int B>
+struct Tile<float, B> {
+    using Acc = Acc32<B>;
+    static constexpr int LD = B + 1;
+};
+
+template <typename T>
+struct BatchParams {
+    int batch;
+    const int* order;  // matrix indices, largest n first
+    const int* n;
+    const int* lda;
+    const int* tile;   // tile order chosen for each matrix
+    T* const* A;
+    int* info;         // [batch] or nullptr
+    int* counter;      // queue ticket
+};
+
+// Tile (ti, tj) of a column-major matrix into shared memory (leading
+// dimension LD); padding past n: identity on the diagonal, zeros elsewhere.
+template <typename T, int B>
+__device__ __forceinline__ void gload(const T* A, int n, int64_t lda, int ti, int tj, T* S, bool lower_only) {
+    constexpr int LD = Tile<T, B>::LD;
+    for (int idx = threadIdx.x; idx < B * B; idx += kThreads) {
+        const int r = idx % B, c = idx / B;
+        const int gr = ti * B + r, gc = tj * B + c;
+        T v;
+        if (gr < n && gc < n) v = (lower_only && r < c) ? T(0) : A[gr + (int64_t)gc * lda];
+        else v = (ti == tj && r == c) ? T(1) : T(0);
+        S[c * LD + r] = v;
+    }
+}
+
+template <typename T, int B>
+__device__ __forceinline__ void gstore(T* A, int n, int64_t lda, int ti, int tj, const T* S, bool lower_only) {
+    constexpr int LD = Tile<T, B>::LD;
+    for (int idx = threadIdx.x; idx < B * B; idx += kThreads) {
+        const int r = idx % B, c = idx / B;
+        const int gr = ti * B + r, gc = tj * B + c;
+        if (gr < n && gc < n && !(lower_only && r < c)) A[gr + (int64_t)gc * lda] = S[c * LD + r];
+    }
+}
+
+// Algorithm 1 on one matrix, in place.  Returns LAPACK's info.
+template <typename T, int B>
+__device__ int run_matrix(T* A, int n, int64_t lda, T* S0, T* S1, T* tmp, int* s_fail) {
+    typename Tile<T, B>::Acc acc;
+    const int t = (n + B - 1) / B;
+    // ---- Step 1: tile Cholesky (left-looking, k increasing)
+    for (int j = 0; j < t; ++j) {
+        __syncthreads();
+        gload<T, B>(A, n, lda, j, j, S0, true);
+        __syncthreads();
+        acc_load<B>(acc, S0);
+        for (int k = 0; k < j; ++k) {  // SYRK
+            __syncthreads();
+            gload<T, B>(A, n, lda, j, k, S1, false);
+            __syncthreads();
+            tile_mma<B, false, true, true, FULL, FULL>(acc, S1, S1);
+        }
+        __syncthreads();
+        acc_store<B>(acc, S0);
+        const int fail = tile_potrf<B>(S0, s_fail);  // POTRF
+        if (fail) return j * B + fail;
+        tile_zero_upper<B>(S0);
+        tile_trtri<B>(S0, tmp);  // X_jj = L_jj^{-1}, kept in place of L_jj
+        gstore<T, B>(A, n, lda, j, j, S0, true);
+        for (int i = j + 1; i < t; ++i) {
+            __syncthreads();
+            gload<T, B>(A, n, lda, i, j, S0, false);
+            __syncthreads();
+            acc_load<B>(acc, S0);
+            for (int k = 0; k < j; ++k) {  // GEMM
+                __syncthreads();
+                gload<T, B>(A, n, lda, i, k, S0, false);
+                gload<T, B>(A, n, lda, j, k, S1, false);
+                __syncthreads();
+                tile_mma<B, false, true, true, FULL, FULL>(acc, S0, S1);
+            }
+            __syncthreads();  // TRSM as the product with X_jj^T
+            gload<T, B>(A, n, lda, j, j, S1, true);
+            acc_store<B>(acc, S0);
+            __syncthreads();
+            acc_zero<B>(acc);
+            tile_mma<B, false, true, false, FULL, LOWER>(acc, S0, S1);
+            __syncthreads();
+            acc_store<B>(acc, S0);
+            __syncthreads();
+            gstore<T, B>(A, n, lda, i, j, S0, false);
+        }
+    }
+    // ---- Step 2: X = L^{-1} (j decreasing, i decreasing, k decreasing)
+    for (int j = t - 1; j >= 0; --j) {
+        for (int i = t - 1; i > j; --i) {
+            __syncthreads();
+            gload<T, B>(A, n, lda, i, i, S0, true);   // X_ii
+            gload<T, B>(A, n, lda, i, j, S1, false);  // L_ij
+            __syncthreads();
+            acc_zero<B>(acc);
+            tile_mma<B, false, false, false, LOWER, FULL>(acc, S0, S1);  // TRMM
+            for (int k = i - 1; k > j; --k) {                           // GEMM
+                __syncthreads();
+                gload<T, B>(A, n, lda, i, k, S0, false);  // X_ik
+                gload<T, B>(A, n, lda, k, j, S1, false);  // L_kj
+                __syncthreads();
+                tile_mma<B, false, false, false, FULL, FULL>(acc, S0, S1);
+            }
+            __syncthreads();
+            gload<T, B>(A, n, lda, j, j, S1, true);  // X_jj
+            acc_store<B>(acc, S0);
+            __syncthreads();
+            acc_zero<B>(acc);
+            tile_mma<B, false, false, true, FULL, LOWER>(acc, S0, S1);  // TRMM by -X_jj
+            __syncthreads();
+            acc_store<B>(acc, S0);
+            __syncthreads();
+            gstore<T, B>(A, n, lda, i, j, S0, false);
+        }
+    }
+    // ---- Step 3: A^{-1} = X^T X (i increasing; k increasing)
+    for (int i = 0; i < t; ++i) {
+        for (int j = 0; j < i; ++j) {
+            __syncthreads();
+            gload<T, B>(A, n, lda, i, i, S0, true);   // X_ii
+            gload<T, B>(A, n, lda, i, j, S1, false);  // X_ij
+            __syncthreads();
+            acc_zero<B>(acc);
+            tile_mma<B, true, false, false, LOWER, FULL>(acc, S0, S1);  // TRMM
+            for (int k = i + 1; k < t; ++k) {                          // GEMM
+                __syncthreads();
+                gload<T, B>(A, n, lda, k, i, S0, false);
+                gload<T, B>(A, n, lda, k, j, S1, false);
+                __syncthreads();
+                tile_mma<B, true, false, false, FULL, FULL>(acc, S0, S1);
+            }
+            __syncthreads();
+            acc_store<B>(acc, S0);
+            __syncthreads();
+            gstore<T, B>(A, n, lda, i, j, S0, false);
+        }
+        __syncthreads();
+        gload<T, B>(A, n, lda, i, i, S0, true);
+        __syncthreads();
+        acc_zero<B>(acc);
+        tile_mma<B, true, false, false, LOWER, LOWER>(acc, S0, S0);  // LAUUM
+        for (int k = i + 1; k < t; ++k) {                           // SYRK
+            __syncthreads();
+            gload<T, B>(A, n, lda, k, i, S0, false);
+            __syncthreads();
+            tile_mma<B, true, false, false, FULL, FULL>(acc, S0, S0);
+        }
+        __syncthreads();
+        acc_store<B>(acc, S0);
+        __syncthreads();
+        gstore<T, B>(A, n, lda, i, i, S0, true);
+    }
+    return 0;
+}
+
+template <typename T, int BMAX>
+__global__ void __launch_bounds__(kThreads) potri_batched_kernel(const BatchParams<T> p) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int s_m, s_fail;
+    constexpr int TS = BMAX * (BMAX + 1);
+    T* S0 = reinterpret_cast<T*>(smem_raw);
+    T* S1 = S0 + TS;
+    T* tmp = S1 + TS;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_m = atomicAdd(p.counter, 1);
+        __syncthreads();
+        const int m = s_m;
+        if (m >= p.batch) return;
+        const int idx = p.order[m];
+        const int n = p.n[idx];
+        const int64_t lda = p.lda[idx];
+        T* A = p.A[idx];
+        int info = 0;
+        const int b = p.tile[idx];
+        if (b == 16) info = run_matrix<T, 16>(A, n, lda, S0, S1, tmp, &s_fail);
+        if constexpr (BMAX >= 32) {
+            if (b == 32) info = run_matrix<T, 32>(A, n, lda, S0, S1, tmp, &s_fail);
+        }
+        if constexpr (BMAX >= 64) {
+            if (b == 64) info = run_matrix<T, 64>(A, n, lda, S0, S1, tmp, &s_fail);
+        }
+        if (threadIdx.x == 0 && p.info) p.info[idx] = info;
+    }
+}
+
+template <typename T, int BMAX>
+constexpr int batched_smem() {
+    return (2 * BMAX * (BMAX + 1) + kThreads) * (int)sizeof(T);
+}
+
+template <typename T, int BMAX>
+cudaError_t launch_batched_t(const BatchParams<T>& p, int num_sms, cudaStream_t s) {
+    auto k = potri_batched_kernel<T, BMAX>;
+    constexpr int sm = batched_smem<T, BMAX>();
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    if (e != cudaSuccess) return e;
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, kThreads, sm);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) occ = 1;
+    int grid = num_sms * occ;
+    if (grid > p.batch) grid = p.batch;
+    k<<<grid, kThreads, sm, s>>>(p);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_batched(const BatchParams<T>& p, int bmax, int num_sms, cudaStream_t s) {
+    if (bmax <= 16) return launch_batched_t<T, 16>(p, num_sms, s);
+    if (bmax <= 32) return launch_batched_t<T, 32>(p, num_sms, s);
+    if constexpr (sizeof(T) == 4) return launch_batched_t<T, 64>(p, num_sms, s);
+    return cudaErrorInvalidValue;
+}
+
+// A diagonally dominant (hence SPD) test matrix per slot, for the autotuner.
+template <typename T>
+__global__ void fill_tuning_batch(T* base, int n, int count) {
+    const int64_t per = (int64_t)n * n;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < per * count;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t q = e % per;
+        const int r = (int)(q % n), c = (int)(q / n);
+        uint32_t h = (uint32_t)(min(r, c) * 73856093u) ^ (uint32_t)(max(r, c) * 19349663u) ^ (uint32_t)(e / per);
+        h ^= h >> 13;
+        h *= 0x5bd1e995u;
+        h ^= h >> 15;
+        const T off = (T)((h & 0xFFFF) / 65536.0 - 0.5);
+        base[e] = r == c ? (T)n : off;
+    }
+}
+
+constexpr int kClasses = 8;  // n in (32c, 32(c+1)], c = 0..7; larger n use class 7
+
+struct BatchPlan {
+    int* dev = nullptr;  // [n | lda | order | tile | counter] in one allocation
+    int batch = 0;
+    int bmax = 16;
+};
+
+struct BatchState {
+    std::mutex mu;
+    bool tuned[2] = {false, false};
+    int tiles[2][kClasses];
+    std::map<std::vector<int>, BatchPlan> plans[2];
+};
+
+BatchState& batch_state(int dev) {
+    static std::mutex mu;
+    static std::map<int, BatchState*> m;
+    std::lock_guard<std::mutex> lk(mu);
+    auto& s = m[dev];
+    if (!s) s = new BatchState();
+    return *s;
+}
+
+int size_class(int n) {
+    const int c = (n - 1) / 32;
+    return c < 0 ? 0 : (c >= kClasses ? kClasses - 1 : c);
+}
+
+// Autotuner: for every size class, time the batched kernel on a synthetic
+// batch of that class's largest size with each candidate tile, keep the
+// fastest.  Runs once per device and precision (or takes SPDINV_BATCHED_TILE).
+template <typename T>
+cudaError_t autotune(BatchState& bs, int num_sms, int* tiles) {
+    const int fp = sizeof(T) == 4 ? 1 : 0;
+    if (bs.tuned[fp]) {
+        std::memcpy(tiles, bs.tiles[fp], sizeof(int) * kClasses);
+        return cudaSuccess;
+    }
+    if (const char* env = std::getenv("SPDINV_BATCHED_TILE")) {
+        const int b = std::atoi(env);
+        if (b == 16 || b == 32 || (b == 64 && fp == 1)) {
+            for (int c = 0; c < kClasses; ++c) bs.tiles[fp][c] = b;
+            bs.tuned[fp] = true;
+            std::memcpy(tiles, bs.tiles[fp], sizeof(int) * kClasses);
+            return cudaSuccess;
+        }
+    }
+    const std::vector<int> cands = fp ? std::vector<int>{16, 32, 64} : std::vector<int>{16, 32};
+    const int count = 2 * num_sms;
+    const int nmax = 32 * kClasses;
+    T* data = nullptr;
+    T** ptrs = nullptr;
+    int* ints = nullptr;
+    cudaError_t e = cudaMalloc(&data, sizeof(T) * (size_t)nmax * nmax * count);
+    if (e == cudaSuccess) e = cudaMalloc(&ptrs, sizeof(T*) * count);
+    if (e == cudaSuccess) e = cudaMalloc(&ints, sizeof(int) * (4 * count + 1));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    std::vector<T*> hp(count);
+    std::vector<int> hints(4 * count);
+    for (int c = 0; c < kClasses && e == cudaSuccess; ++c) {
+        const int n = 32 * (c + 1);
+        for (int q = 0; q < count; ++q) {
+            hp[q] = data + (size_t)q * n * n;
+            hints[q] = n;              // n
+            hints[count + q] = n;      // lda
+            hints[2 * count + q] = q;  // order
+        }
+        e = cudaMemcpy(ptrs, hp.data(), sizeof(T*) * count, cudaMemcpyHostToDevice);
+        float best = 1e30f;
+        int bestb = cands[0];
+        for (int b : cands) {
+            if (e != cudaSuccess) break;
+            for (int q = 0; q < count; ++q) hints[3 * count + q] = b;
+            e = cudaMemcpy(ints, hints.data(), sizeof(int) * 4 * count, cudaMemcpyHostToDevice);
+            BatchParams<T> p{count, ints + 2 * count, ints, ints + count, ints + 3 * count, ptrs, nullptr,
+                             ints + 4 * count};
+            float ms_min = 1e30f;
+            for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
+                fill_tuning_batch<T><<<256, 256>>>(data, n, count);
+                cudaMemset(ints + 4 * count, 0, sizeof(int));
+                cudaEventRecord(e0);
+                e = launch_batched<T>(p, b, num_sms, 0);
+                cudaEventRecord(e1);
+                if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                float ms = 0;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (rep > 0) ms_min = std::min(ms_min, ms);
+            }
+            if (ms_min < best) {
+                best = ms_min;
+                bestb = b;
+            }
+        }
+        bs.tiles[fp][c] = bestb;
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(data);
+    cudaFree(ptrs);
+    cudaFree(ints);
+    if (e != cudaSuccess) return e;
+    bs.tuned[fp] = true;
+    std::memcpy(tiles, bs.tiles[fp], sizeof(int) * kClasses);
+    return cudaSuccess;
+}
+
+template <typename T>
+spdinv_status run_batched(int batch, const int* h_n, T* const* d_Aptrs, const int* h_lda, int* d_info,
+                          cudaStream_t stream) {
+    if (batch < 0) return SPDINV_ERR_N;
+    if (batch == 0) return SPDINV_OK;
+    if (!h_n || !h_lda || !d_Aptrs) return SPDINV_ERR_NULL;
+    for (int k = 0; k < batch; ++k) {
+        if (h_n[k] < 0 || h_n[k] > 4096) return SPDINV_ERR_N;
+        if (h_lda[k] < (h_n[k] > 1 ? h_n[k] : 1)) return SPDINV_ERR_LDA;
+    }
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e);
+    const int num_sms = device_state(dev).num_sms;
+    BatchState& bs = batch_state(dev);
+    std::lock_guard<std::mutex> lk(bs.mu);
+    const int fp = sizeof(T) == 4 ? 1 : 0;
+    std::vector<int> key(h_n, h_n + batch);
+    key.insert(key.end(), h_lda, h_lda + batch);
+    auto it = bs.plans[fp].find(key);
+    if (it == bs.plans[fp].end()) {
+        int tiles[kClasses];
+        e = autotune<T>(bs, num_sms, tiles);
+        if (e != cudaSuccess) return cuda_fail(e);
+        std::vector<int> h(4 * batch + 1, 0);
+        std::vector<int> order(batch);
+        std::iota(order.begin(), order.end(), 0);
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return h_n[a] > h_n[b]; });
+        int bmax = 16;
+        for (int k = 0; k < batch; ++k) {
+            h[k] = h_n[k];
+            h[batch + k] = h_lda[k];
+            h[2 * batch + k] = order[k];
+            const int b = tiles[size_class(h_n[k])];
+            h[3 * batch + k] = b;
+            bmax = std::max(bmax, b);
+        }
+        BatchPlan bp;
+        bp.batch = batch;
+        bp.bmax = bmax;
+        e = cudaMalloc(&bp.dev, sizeof(int) * h.size());
+        if (e != cudaSuccess) return cuda_fail(e);
+        e = cudaMemcpy(bp.dev, h.data(), sizeof(int) * h.size(), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            cudaFree(bp.dev);
+            return cuda_fail(e);
+        }
+        it = bs.plans[fp].emplace(std::move(key), bp).first;
+    }
+    const BatchPlan& bp = it->second;
+    BatchParams<T> p{batch, bp.dev + 2 * batch, bp.dev, bp.dev + batch, bp.dev + 3 * batch, d_Aptrs, d_info,
+                     bp.dev + 4 * batch};
+    e = cudaMemsetAsync(p.counter, 0, sizeof(int), stream);
+    if (e != cudaSuccess) return cuda_fail(e);
+    e = launch_batched<T>(p, bp.bmax, num_sms, stream);
+    if (e != cudaSuccess) return cuda_fail(e);
+    count_launches(1);
+    return SPDINV_OK;
+}
+
+}  // namespace
+}  // namespace spdinv
+
+using namespace spdinv;
+
+extern "C" {
+
+SPDINV_API spdinv_status spdinv_potri_batched(int batch, const int* h_n, double* const* d_Aptrs, const int* h_lda,
+                                              int* d_info, cudaStream_t stream) {
+    return run_batched<double>(batch, h_n, d_Aptrs, h_lda, d_info, stream);
+}
+
+SPDINV_API spdinv_status spdinv_spotri_batched(int batch, const int* h_n, float* const* d_Aptrs, const int* h_lda,
+                                               int* d_info, cudaStream_t stream) {
+    return run_batched<float>(batch, h_n, d_Aptrs, h_lda, d_info, stream);
+}
+
+SPDINV_API spdinv_status spdinv_batched_tiles(int fp32, int tiles[8]) {
+    if (!tiles) return SPDINV_ERR_NULL;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e);
+    const int num_sms = device_state(dev).num_sms;
+    BatchState& bs = batch_state(dev);
+    std::lock_guard<std::mutex> lk(bs.mu);
+    e = fp32 ? autotune<float>(bs, num_sms, tiles) : autotune<double>(bs, num_sms, tiles);
+    return e == cudaSuccess ? SPDINV_OK : cuda_fail(e);
+}
+
+}  // extern "C"

@@ -86,3 +86,107 @@ def mirror_lower(A):
     """Full symmetric matrix from the lower triangle (a new tensor)."""
     Lo = torch.tril(A)
     return Lo + torch.tril(Lo, -1).t()
+
+
+# ---------------------------------------------------------------- batched
+class PreparedBatch:
+    """The host size arrays and the device pointer array of a batch of
+    column-major matrices (float64 or float32), kept alive so that repeated
+    calls -- including calls captured in a CUDA graph -- need no host work
+    beyond the launch.  Call run() once outside capture first: the first call
+    with a new size list builds and uploads its plan."""
+
+    def __init__(self, mats):
+        import numpy as np
+        if not mats:
+            raise ValueError("empty batch")
+        self.dtype = mats[0].dtype
+        if self.dtype not in (torch.float64, torch.float32):
+            raise ValueError("float64 or float32 matrices expected")
+        dev = mats[0].device
+        ns, ldas, ptrs = [], [], []
+        for M in mats:
+            n, lda = _lda(M, self.dtype)
+            if M.device != dev:
+                raise ValueError("all matrices must be on one device")
+            ns.append(n)
+            ldas.append(lda)
+            ptrs.append(M.data_ptr())
+        self.mats = list(mats)
+        self.h_n = np.ascontiguousarray(ns, dtype=np.int32)
+        self.h_lda = np.ascontiguousarray(ldas, dtype=np.int32)
+        self.d_ptrs = torch.tensor(ptrs, dtype=torch.int64, device=dev)
+        self.info = torch.zeros(len(mats), dtype=torch.int32, device=dev)
+
+    def run(self, stream=None):
+        fn = L.spdinv_potri_batched if self.dtype == torch.float64 else L.spdinv_spotri_batched
+        st = fn(len(self.mats), self.h_n.ctypes.data, self.d_ptrs.data_ptr(), self.h_lda.ctypes.data,
+                self.info.data_ptr(), _stream(stream))
+        _check(st, "spdinv_(s)potri_batched")
+        return self.info
+
+
+def potri_batched_(mats, stream=None):
+    """In place on every matrix of the list (column-major float64/float32
+    CUDA tensors of any sizes): lower triangle <- lower triangle of its
+    inverse, in one launch.  Returns the per-matrix info tensor."""
+    return PreparedBatch(mats).run(stream)
+
+
+# ---------------------------------------------------------------- autograd
+def _as_batch(A):
+    if A.dim() == 2:
+        return A.unsqueeze(0), True
+    if A.dim() == 3:
+        return A, False
+    raise ValueError("expected (n, n) or (batch, n, n)")
+
+
+def _batched_views(buf):
+    """Column-major views of each matrix of a contiguous (batch, n, n) buffer
+    holding the matrices transposed (buf[k] row-major = A_k column-major)."""
+    return [buf[k].t() for k in range(buf.shape[0])]
+
+
+class SpdInverse(torch.autograd.Function):
+    """X = A^{-1} for symmetric positive definite A (float64 or float32,
+    (n, n) or (batch, n, n)), with grad_A = -sym(X G X) in the backward.
+
+    Forward: the batched inversion (lower triangles) and a mirror kernel that
+    completes the symmetric X; backward: the grad kernel.  All arithmetic in
+    libspdinv.so."""
+
+    @staticmethod
+    def forward(ctx, A):
+        A3, squeeze = _as_batch(A)
+        if not A3.is_cuda:
+            raise ValueError("CUDA tensor expected")
+        b, n, _ = A3.shape
+        buf = A3.detach().transpose(-1, -2).contiguous()  # column-major copies
+        info = PreparedBatch(_batched_views(buf)).run()
+        s = _stream(None)
+        mirror = L.spdinv_mirror_lower if buf.dtype == torch.float64 else L.spdinv_smirror_lower
+        _check(mirror(b, n, buf.data_ptr(), max(n, 1), n * n, s), "spdinv_mirror_lower")
+        ctx.save_for_backward(buf)
+        ctx.info = info
+        ctx.squeeze = squeeze
+        return buf[0] if squeeze else buf
+
+    @staticmethod
+    def backward(ctx, G):
+        (X,) = ctx.saved_tensors
+        G3 = (G.unsqueeze(0) if ctx.squeeze else G).contiguous()
+        b, n, _ = X.shape
+        grad = torch.empty_like(X)
+        fn = L.spdinv_potri_backward if X.dtype == torch.float64 else L.spdinv_spotri_backward
+        # X, sym(G) and grad are symmetric, so the row-/column-major reading of
+        # their buffers does not matter.
+        st = fn(b, n, X.data_ptr(), max(n, 1), n * n, G3.data_ptr(), max(n, 1), n * n,
+                grad.data_ptr(), max(n, 1), n * n, _stream(None))
+        _check(st, "spdinv_potri_backward")
+        return grad[0] if ctx.squeeze else grad
+
+
+def spd_inverse(A):
+    """Differentiable A^{-1} of SPD matrices (see SpdInverse)."""
+    return SpdInverse.apply(A)
