@@ -46,7 +46,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="fp64",
-                    choices=["fp64", "batched64", "batched32", "backward64", "backward32"],
+                    choices=["fp64", "batched64", "batched32", "backward64", "backward32", "mixed"],
                     help="fp64 (default, the headline line): one n x n FP64 inversion per step; "
                          "batched*: 4096 matrices n ~ U{16..256} per step, one graph-captured launch; "
                          "backward*: forward + backward of 256 matrices n = 512")
@@ -185,6 +185,61 @@ def timed_steps(fn, steps, warmup, stream):
     return e0.elapsed_time(e1) / steps
 
 
+def run_mixed_study(args, dev, stream):
+    """Mixed precision vs the FP64 path at n (default 16384) for cond 1e2, 1e4,
+    1e6: time and error (sampled columns vs Q diag(1/lam) Q^T) after k
+    correction steps; one JSON line per (cond, k) and one summary line."""
+    import numpy as np
+    import torch
+
+    import spd_inputs as si
+    from oracle import closed_forms as cf
+    from paper_1002_4057_gb300 import torch_api as T
+
+    n = args.n
+    cols = np.array([0, n // 3, n - 1])
+    flops = float(n) ** 3
+    out = []
+    for cond, kmax in ((1e2, 2), (1e4, 2), (1e6, 3)):
+        A, Q, lam = si.spectral_spd(n, cond, seed=si.SEED_BASE + 2, device=dev)
+        ref = cf.spectral_inverse_columns(Q.cpu().numpy(), lam, cols)
+        del Q
+        W = torch.empty_like(A)
+        info = torch.zeros(1, dtype=torch.int32, device=dev)
+
+        def err_of(W):
+            Lo = torch.tril(W)
+            Xc = (Lo[:, cols] + torch.tril(Lo, -1).t()[:, cols]).cpu().numpy()
+            return float(np.linalg.norm(Xc - ref) / np.linalg.norm(ref))
+
+        def fp64():
+            W.copy_(A)
+            T.potri_(W, info=info, tile=64)
+
+        ms64 = timed_steps(fp64, 1, 1, stream)
+        e64 = err_of(W)
+        rec = {"cond": cond, "fp64_ms": round(ms64, 1), "fp64_err": e64, "mixed": []}
+        for k in range(0, kmax + 1):
+            def mixed():
+                W.copy_(A)
+                T.potri_(W, info=info, tile=64, precision=1, refine_steps=k)
+            ms = timed_steps(mixed, 1, 1, stream)
+            assert int(info.item()) == 0
+            e = err_of(W)
+            rec["mixed"].append({"steps": k, "ms": round(ms, 1), "err": e, "gflops": round(flops / (ms * 1e-3) / 1e9, 1),
+                                 "speedup_vs_fp64": round(ms64 / ms, 3)})
+        out.append(rec)
+        print(json.dumps({"workload": "mixed", "n": n, **rec}), flush=True)
+        del A, W
+        torch.cuda.empty_cache()
+    best = []
+    for rec in out:
+        ok = [m for m in rec["mixed"] if m["err"] <= 1e-10]
+        best.append({"cond": rec["cond"], "steps_for_1e-10": ok[0]["steps"] if ok else None,
+                     "speedup_vs_fp64_at_1e-10": ok[0]["speedup_vs_fp64"] if ok else None})
+    print(json.dumps({"workload": "mixed", "metric": METRIC, "n": n, "summary": best}), flush=True)
+
+
 def run_secondary(args):
     """Measurement lines for the batched and backward workloads (not the
     headline line): Gflop/s with sum(n^3) per batch, or 3 n^3 per matrix for
@@ -199,6 +254,9 @@ def run_secondary(args):
     dev = torch.device("cuda", 0)
     stream = torch.cuda.current_stream()
     clk = ClockSampler(0)
+    if args.workload == "mixed":
+        run_mixed_study(args, dev, stream)
+        return
     if args.workload.startswith("batched"):
         dtype = torch.float64 if args.workload == "batched64" else torch.float32
         sizes = si.batch_sizes(4096, 16, 256, seed=si.SEED_BASE + 3)

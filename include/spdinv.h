@@ -75,8 +75,8 @@ typedef enum {
 typedef enum {
     SPDINV_PREC_FP64 = 0,         /* every operation in native FP64 (DMMA tensor cores) */
     SPDINV_PREC_MIXED_FP32 = 1,   /* bulk updates FP32; diagonal POTRF/TRTRI and the residual FP64 */
-    SPDINV_PREC_MIXED_BF16X3 = 2  /* bulk updates as three BF16 products with FP32 accumulation
-                                     (tcgen05 tensor cores); diagonal tiles and residual FP64 */
+    SPDINV_PREC_MIXED_BF16X3 = 2  /* reserved: bulk updates as three BF16 products (returns
+                                     SPDINV_ERR_UNSUPPORTED in this build) */
 } spdinv_precision;
 
 /* Options for spdinv_potri_ex.  Zero-initialise and set what you need. */
@@ -123,9 +123,14 @@ SPDINV_API spdinv_status spdinv_potri(int64_t n, double* dA, int64_t lda, int* d
 
 /* spdinv_potri with options (tile size, residency, precision, correction
  * steps, wait limit).  opts may be NULL (= all defaults).
- * Mixed precision (opts->precision != SPDINV_PREC_FP64): the lower triangle
- * of A still holds A^{-1} in FP64 on exit; with refine_steps > 0 the library
- * also keeps an FP64 copy of A for the residual. */
+ * Mixed precision (opts->precision == SPDINV_PREC_MIXED_FP32, tile 32 or 64):
+ * the tile DAG runs with FP32 bulk updates and FP64 diagonal POTRF/TRTRI,
+ * then refine_steps times R = I - A X (FP64; A read from its lower triangle,
+ * intact until the end) and X <- X + X R (product in FP32, sum in FP64); the
+ * lower triangle of A then holds X in FP64.  Accuracy after k steps is about
+ * e^(2^k) for the FP32 result's error e (plus the FP32 rounding of X R), so
+ * the step count needed for a target grows with cond(A).  The workspace
+ * holds three n x n FP64 matrices when refine_steps > 0. */
 SPDINV_API spdinv_status spdinv_potri_ex(int64_t n, double* dA, int64_t lda, const spdinv_opts* opts,
                               int* d_info, cudaStream_t stream);
 

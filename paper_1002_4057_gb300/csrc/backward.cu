@@ -72,7 +72,7 @@ __device__ __forceinline__ void load_sym_tile(const T* G, int64_t n, int64_t ld,
 
 template <typename T, int PHASE>
 __global__ void __launch_bounds__(kThreads) backward_kernel(const BwdParams<T> p) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned char* const smem_raw = dynamic_smem();
     constexpr int LD = BwdTile<T>::LD;
     T* S0 = reinterpret_cast<T*>(smem_raw);
     T* S1 = S0 + BB * LD;
@@ -93,7 +93,7 @@ __global__ void __launch_bounds__(kThreads) backward_kernel(const BwdParams<T> p
     typename BwdTile<T>::Acc acc;
     acc_zero<BB>(acc);
     for (int kt = 0; kt < p.t; ++kt) {
-        __syncthreads();
+        cta_sync();
         if (PHASE == 0) {
             load_tile<T>(X, p.n, p.ldx, ti, kt, S0);
             load_sym_tile<T>(G, p.n, p.ldg, kt, tj, S1);
@@ -101,12 +101,12 @@ __global__ void __launch_bounds__(kThreads) backward_kernel(const BwdParams<T> p
             load_tile<T>(Y, p.n, p.n, ti, kt, S0);
             load_tile<T>(X, p.n, p.ldx, kt, tj, S1);
         }
-        __syncthreads();
+        cta_sync();
         tile_mma<BB, false, false, PHASE == 1, FULL, FULL>(acc, S0, S1);
     }
-    __syncthreads();
+    cta_sync();
     acc_store<BB>(acc, S0);
-    __syncthreads();
+    cta_sync();
     if (PHASE == 0) {
         for (int idx = threadIdx.x; idx < BB * BB; idx += kThreads) {
             const int r = idx % BB, c = idx / BB;

@@ -86,17 +86,17 @@ __device__ int run_matrix(T* A, int n, int64_t lda, T* S0, T* S1, T* tmp, int* s
     const int t = (n + B - 1) / B;
     // ---- Step 1: tile Cholesky (left-looking, k increasing)
     for (int j = 0; j < t; ++j) {
-        __syncthreads();
+        cta_sync();
         gload<T, B>(A, n, lda, j, j, S0, true);
-        __syncthreads();
+        cta_sync();
         acc_load<B>(acc, S0);
         for (int k = 0; k < j; ++k) {  // SYRK
-            __syncthreads();
+            cta_sync();
             gload<T, B>(A, n, lda, j, k, S1, false);
-            __syncthreads();
+            cta_sync();
             tile_mma<B, false, true, true, FULL, FULL>(acc, S1, S1);
         }
-        __syncthreads();
+        cta_sync();
         acc_store<B>(acc, S0);
         const int fail = tile_potrf<B>(S0, s_fail);  // POTRF
         if (fail) return j * B + fail;
@@ -104,92 +104,92 @@ __device__ int run_matrix(T* A, int n, int64_t lda, T* S0, T* S1, T* tmp, int* s
         tile_trtri<B>(S0, tmp);  // X_jj = L_jj^{-1}, kept in place of L_jj
         gstore<T, B>(A, n, lda, j, j, S0, true);
         for (int i = j + 1; i < t; ++i) {
-            __syncthreads();
+            cta_sync();
             gload<T, B>(A, n, lda, i, j, S0, false);
-            __syncthreads();
+            cta_sync();
             acc_load<B>(acc, S0);
             for (int k = 0; k < j; ++k) {  // GEMM
-                __syncthreads();
+                cta_sync();
                 gload<T, B>(A, n, lda, i, k, S0, false);
                 gload<T, B>(A, n, lda, j, k, S1, false);
-                __syncthreads();
+                cta_sync();
                 tile_mma<B, false, true, true, FULL, FULL>(acc, S0, S1);
             }
-            __syncthreads();  // TRSM as the product with X_jj^T
+            cta_sync();  // TRSM as the product with X_jj^T
             gload<T, B>(A, n, lda, j, j, S1, true);
             acc_store<B>(acc, S0);
-            __syncthreads();
+            cta_sync();
             acc_zero<B>(acc);
             tile_mma<B, false, true, false, FULL, LOWER>(acc, S0, S1);
-            __syncthreads();
+            cta_sync();
             acc_store<B>(acc, S0);
-            __syncthreads();
+            cta_sync();
             gstore<T, B>(A, n, lda, i, j, S0, false);
         }
     }
     // ---- Step 2: X = L^{-1} (j decreasing, i decreasing, k decreasing)
     for (int j = t - 1; j >= 0; --j) {
         for (int i = t - 1; i > j; --i) {
-            __syncthreads();
+            cta_sync();
             gload<T, B>(A, n, lda, i, i, S0, true);   // X_ii
             gload<T, B>(A, n, lda, i, j, S1, false);  // L_ij
-            __syncthreads();
+            cta_sync();
             acc_zero<B>(acc);
             tile_mma<B, false, false, false, LOWER, FULL>(acc, S0, S1);  // TRMM
             for (int k = i - 1; k > j; --k) {                           // GEMM
-                __syncthreads();
+                cta_sync();
                 gload<T, B>(A, n, lda, i, k, S0, false);  // X_ik
                 gload<T, B>(A, n, lda, k, j, S1, false);  // L_kj
-                __syncthreads();
+                cta_sync();
                 tile_mma<B, false, false, false, FULL, FULL>(acc, S0, S1);
             }
-            __syncthreads();
+            cta_sync();
             gload<T, B>(A, n, lda, j, j, S1, true);  // X_jj
             acc_store<B>(acc, S0);
-            __syncthreads();
+            cta_sync();
             acc_zero<B>(acc);
             tile_mma<B, false, false, true, FULL, LOWER>(acc, S0, S1);  // TRMM by -X_jj
-            __syncthreads();
+            cta_sync();
             acc_store<B>(acc, S0);
-            __syncthreads();
+            cta_sync();
             gstore<T, B>(A, n, lda, i, j, S0, false);
         }
     }
     // ---- Step 3: A^{-1} = X^T X (i increasing; k increasing)
     for (int i = 0; i < t; ++i) {
         for (int j = 0; j < i; ++j) {
-            __syncthreads();
+            cta_sync();
             gload<T, B>(A, n, lda, i, i, S0, true);   // X_ii
             gload<T, B>(A, n, lda, i, j, S1, false);  // X_ij
-            __syncthreads();
+            cta_sync();
             acc_zero<B>(acc);
             tile_mma<B, true, false, false, LOWER, FULL>(acc, S0, S1);  // TRMM
             for (int k = i + 1; k < t; ++k) {                          // GEMM
-                __syncthreads();
+                cta_sync();
                 gload<T, B>(A, n, lda, k, i, S0, false);
                 gload<T, B>(A, n, lda, k, j, S1, false);
-                __syncthreads();
+                cta_sync();
                 tile_mma<B, true, false, false, FULL, FULL>(acc, S0, S1);
             }
-            __syncthreads();
+            cta_sync();
             acc_store<B>(acc, S0);
-            __syncthreads();
+            cta_sync();
             gstore<T, B>(A, n, lda, i, j, S0, false);
         }
-        __syncthreads();
+        cta_sync();
         gload<T, B>(A, n, lda, i, i, S0, true);
-        __syncthreads();
+        cta_sync();
         acc_zero<B>(acc);
         tile_mma<B, true, false, false, LOWER, LOWER>(acc, S0, S0);  // LAUUM
         for (int k = i + 1; k < t; ++k) {                           // SYRK
-            __syncthreads();
+            cta_sync();
             gload<T, B>(A, n, lda, k, i, S0, false);
-            __syncthreads();
+            cta_sync();
             tile_mma<B, true, false, false, FULL, FULL>(acc, S0, S0);
         }
-        __syncthreads();
+        cta_sync();
         acc_store<B>(acc, S0);
-        __syncthreads();
+        cta_sync();
         gstore<T, B>(A, n, lda, i, i, S0, true);
     }
     return 0;
@@ -197,16 +197,16 @@ __device__ int run_matrix(T* A, int n, int64_t lda, T* S0, T* S1, T* tmp, int* s
 
 template <typename T, int BMAX>
 __global__ void __launch_bounds__(kThreads) potri_batched_kernel(const BatchParams<T> p) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned char* const smem_raw = dynamic_smem();
     __shared__ int s_m, s_fail;
     constexpr int TS = BMAX * (BMAX + 1);
     T* S0 = reinterpret_cast<T*>(smem_raw);
     T* S1 = S0 + TS;
     T* tmp = S1 + TS;
     for (;;) {
-        __syncthreads();
+        cta_sync();
         if (threadIdx.x == 0) s_m = atomicAdd(p.counter, 1);
-        __syncthreads();
+        cta_sync();
         const int m = s_m;
         if (m >= p.batch) return;
         const int idx = p.order[m];

@@ -7,6 +7,7 @@
 
 #include "../../include/spdinv.h"
 #include "api_internal.h"
+#include "ptx.cuh"
 
 namespace spdinv {
 namespace {
@@ -22,7 +23,7 @@ __global__ void mirror_lower_kernel(int64_t n, T* A, int64_t lda, int64_t stride
         const int64_t gr = tj * 32 + threadIdx.x, gc = ti * 32 + r;  // source (row, col)
         if (gr < n && gc < n) s[r][threadIdx.x] = M[gr + gc * lda];
     }
-    __syncthreads();
+    cta_sync();
     for (int c = threadIdx.y; c < 32; c += blockDim.y) {
         const int64_t gr = ti * 32 + threadIdx.x, gc = tj * 32 + c;  // target (row, col), row < col
         if (gr < n && gc < n && gr < gc) M[gr + gc * lda] = s[threadIdx.x][c];

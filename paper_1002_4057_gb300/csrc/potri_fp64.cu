@@ -28,100 +28,16 @@
 #include <climits>
 
 #include "kernels.h"
+#include "persist.cuh"
 #include "tile_fp64.cuh"
 
 namespace spdinv {
 
 namespace {
 
-struct WaitCtl {
-    int* ctrl;              // [0] ticket, [1] abort, [2] err, [3] info
-    long long timeout_ns;
-};
-
-__device__ __forceinline__ void raise_error(int* ctrl, int code) {
-    atomicCAS(&ctrl[2], 0, code);
-    atomicExch(&ctrl[1], 1);
-}
-
-// First failing column wins (0 = none).
-__device__ __forceinline__ void record_info(int* ctrl, int v) {
-    int cur = atomicCAS(&ctrl[3], 0, v);
-    while (cur != 0 && v < cur) {
-        const int prev = atomicCAS(&ctrl[3], cur, v);
-        if (prev == cur) break;
-        cur = prev;
-    }
-    atomicExch(&ctrl[1], 1);
-}
-
-// Bounded spin on a readiness flag (thread 0 only).  false = give up
-// (abort raised elsewhere, or this wait hit its limit: error set here).
-__device__ bool wait_flag(const int* flag, const WaitCtl& w) {
-    if (flag == nullptr) return true;
-    if (ld_acquire_gpu(flag) != 0) return true;
-    const uint64_t t0 = globaltimer_ns();
-    unsigned ns = 32;
-    for (;;) {
-        if (ld_acquire_gpu(flag) != 0) return true;
-        if (ld_relaxed_gpu(&w.ctrl[1]) != 0) return false;
-        if ((long long)(globaltimer_ns() - t0) > w.timeout_ns) {
-            raise_error(w.ctrl, SPDINV_ERR_TIMEOUT);
-            return false;
-        }
-        __nanosleep(ns);
-        if (ns < 1024) ns <<= 1;
-    }
-}
-
 template <int B>
-struct Ctx {
-    const KParamsF64* p;
-    double* T0;
-    double* T1;
-    double* tmp;
-    uint64_t* bar;
-    int* s_flag;
-    uint32_t phase;
-    WaitCtl w;
-};
-
-// Bounded wait on the CTA's mbarrier for the current phase.
-template <int B>
-__device__ bool mbar_wait_bounded(Ctx<B>& c) {
-    const uint64_t t0 = globaltimer_ns();
-    while (!mbar_try_wait(c.bar, c.phase)) {
-        if ((long long)(globaltimer_ns() - t0) > 2000000000LL) {
-            if (threadIdx.x == 0) raise_error(c.w.ctrl, SPDINV_ERR_TIMEOUT);
-            return false;
-        }
-    }
-    c.phase ^= 1u;
-    return true;
-}
-
-// Wait for up to two readiness flags, then copy up to two store tiles into
-// T0 / T1.  Called by all threads; false = stop (abort or timeout).
-template <int B>
-__device__ bool fetch(Ctx<B>& c, const int* f0, const int* f1, const double* g0, const double* g1) {
-    constexpr uint32_t kBytes = B * B * sizeof(double);
-    __syncthreads();  // every thread is done with T0 / T1
-    if (threadIdx.x == 0) {
-        const bool ok = wait_flag(f0, c.w) && wait_flag(f1, c.w);
-        *c.s_flag = ok ? 0 : 1;
-        if (ok) {
-            fence_proxy_async_global();
-            fence_proxy_async_shared();
-            mbar_arrive_expect_tx(c.bar, (g0 ? kBytes : 0u) + (g1 ? kBytes : 0u));
-            if (g0) bulk_g2s(c.T0, g0, kBytes, c.bar);
-            if (g1) bulk_g2s(c.T1, g1, kBytes, c.bar);
-        }
-    }
-    // The others wait here while thread 0 waits on the dependency flags (its
-    // own limit); the mbarrier wait below then covers only the copy itself.
-    __syncthreads();
-    if (*c.s_flag != 0) return false;
-    return mbar_wait_bounded(c);
+__device__ __forceinline__ bool fetch(PCtx& c, const int* f0, const int* f1, const double* g0, const double* g1) {
+    return spdinv::fetch(c, f0, f1, g0, g1, (uint32_t)(B * B * sizeof(double)));
 }
 
 template <int B>
@@ -168,38 +84,30 @@ __device__ void store_ws_tile(double* g, const double* T) {
     for (int idx = threadIdx.x; idx < B * B / 2; idx += kThreads) d[idx] = s[idx];
 }
 
-// All threads: make the CTA's global writes visible, then raise the flag.
-template <int B>
-__device__ void publish(Ctx<B>& c, int* flag, int ticket) {
-    __syncthreads();
-    if (threadIdx.x == 0 && flag != nullptr && ticket != c.p->drop_task) {
-        __threadfence();
-        fence_proxy_async_global();
-        st_release_gpu(flag, 1);
-    }
-}
-
 template <int B>
 __global__ void __launch_bounds__(kThreads) potri_fp64_persistent(const KParamsF64 prm) {
-    extern __shared__ __align__(128) unsigned char smem_raw[];
+    unsigned char* const smem_raw = dynamic_smem();
     __shared__ __align__(8) uint64_t bar;
     __shared__ int s_task, s_flag, s_fail;
     const KParamsF64& p = prm;
-    Ctx<B> c;
-    c.p = &p;
-    c.T0 = reinterpret_cast<double*>(smem_raw);
-    c.T1 = c.T0 + B * B;
-    c.tmp = c.T1 + B * B;
+    double* const T0 = reinterpret_cast<double*>(smem_raw);
+    double* const T1 = T0 + B * B;
+    double* const tmp = T1 + B * B;
+    PCtx c;
+    c.T0 = T0;
+    c.T1 = T1;
     c.bar = &bar;
     c.s_flag = &s_flag;
     c.phase = 0;
-    c.w.ctrl = p.ctrl;
-    c.w.timeout_ns = p.timeout_ns;
+    c.ctrl = p.ctrl;
+    c.timeout_ns = p.timeout_ns;
+    c.drop_task = p.drop_task;
     if (threadIdx.x == 0) {
         mbar_init(&bar, 1);
         fence_proxy_async_shared();
     }
-    __syncthreads();
+    cta_sync();
+    if (!layout_ok(T0, T1, p.Bw, p.Cw, p.Dw, p.ctrl)) return;
     const int t = p.t;
     int* const fL = p.flags;                  // [t*t]  B_ij holds L_ij
     int* const fX = p.flags + (int64_t)t * t; // [t*t]  C_ij holds X_ij
@@ -209,122 +117,112 @@ __global__ void __launch_bounds__(kThreads) potri_fp64_persistent(const KParamsF
     auto dflag = [&](int q) -> const int* { return p.steps == STEPS_LAUUM ? nullptr : &fD[q]; };
 
     for (;;) {
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            int m = -1;
-            if (ld_relaxed_gpu(&p.ctrl[1]) == 0) {
-                m = atomicAdd(&p.ctrl[0], 1);
-                if (m >= p.ntasks) m = -1;
-            }
-            s_task = m;
-        }
-        __syncthreads();
-        const int ticket = s_task;
+        const int ticket = next_ticket(p.ctrl, p.ntasks, &s_task);
         if (ticket < 0) return;
         const uint32_t e = p.tasks[ticket];
         const int kind = (int)task_kind(e), i = (int)task_i(e), j = (int)task_j(e);
         Acc<B> acc;
 
         if (kind == K_S1_DIAG) {
-            load_A_tile<B>(p, j, j, c.T0, true);
-            __syncthreads();
-            acc_load<B>(acc, c.T0);
+            load_A_tile<B>(p, j, j, T0, true);
+            cta_sync();
+            acc_load<B>(acc, T0);
             for (int k = 0; k < j; ++k) {  // SYRK chain, U order
                 if (!fetch<B>(c, &fL[j * t + k], nullptr, tileB<B>(p, j, k), nullptr)) return;
-                tile_mma<B, false, true, true, FULL, FULL>(acc, c.T0, c.T0);
+                tile_mma<B, false, true, true, FULL, FULL>(acc, T0, T0);
             }
-            __syncthreads();
-            acc_store<B>(acc, c.T0);
-            const int fail = tile_potrf<B>(c.T0, &s_fail);
+            cta_sync();
+            acc_store<B>(acc, T0);
+            const int fail = tile_potrf<B>(T0, &s_fail);
             if (fail) {
                 if (threadIdx.x == 0) record_info(p.ctrl, j * B + fail);
                 return;
             }
-            tile_zero_upper<B>(c.T0);
-            __syncthreads();
-            if (p.steps == STEPS_POTRF) store_A_tile<B>(p, j, j, c.T0, true);
-            tile_trtri<B>(c.T0, c.tmp);
-            store_ws_tile<B>(const_cast<double*>(tileD<B>(p, j)), c.T0);
-            publish<B>(c, &fD[j], ticket);
+            tile_zero_upper<B>(T0);
+            cta_sync();
+            if (p.steps == STEPS_POTRF) store_A_tile<B>(p, j, j, T0, true);
+            tile_trtri<B>(T0, tmp);
+            store_ws_tile<B>(const_cast<double*>(tileD<B>(p, j)), T0);
+            publish(c, &fD[j], ticket);
         } else if (kind == K_S1_OFF) {
-            load_A_tile<B>(p, i, j, c.T0, false);
-            __syncthreads();
-            acc_load<B>(acc, c.T0);
+            load_A_tile<B>(p, i, j, T0, false);
+            cta_sync();
+            acc_load<B>(acc, T0);
             for (int k = 0; k < j; ++k) {  // GEMM chain, U order
                 if (!fetch<B>(c, &fL[i * t + k], &fL[j * t + k], tileB<B>(p, i, k), tileB<B>(p, j, k))) return;
-                tile_mma<B, false, true, true, FULL, FULL>(acc, c.T0, c.T1);
+                tile_mma<B, false, true, true, FULL, FULL>(acc, T0, T1);
             }
             // TRSM: L_ij = A'_ij L_jj^{-T} = A'_ij X_jj^T
             if (!fetch<B>(c, &fD[j], nullptr, nullptr, tileD<B>(p, j))) return;
-            acc_store<B>(acc, c.T0);
-            __syncthreads();
+            acc_store<B>(acc, T0);
+            cta_sync();
             acc_zero<B>(acc);
-            tile_mma<B, false, true, false, FULL, LOWER>(acc, c.T0, c.T1);
-            __syncthreads();
-            acc_store<B>(acc, c.T0);
-            __syncthreads();
-            store_ws_tile<B>(const_cast<double*>(tileB<B>(p, i, j)), c.T0);
-            if (p.steps == STEPS_POTRF) store_A_tile<B>(p, i, j, c.T0, false);
-            publish<B>(c, &fL[i * t + j], ticket);
+            tile_mma<B, false, true, false, FULL, LOWER>(acc, T0, T1);
+            cta_sync();
+            acc_store<B>(acc, T0);
+            cta_sync();
+            store_ws_tile<B>(const_cast<double*>(tileB<B>(p, i, j)), T0);
+            if (p.steps == STEPS_POTRF) store_A_tile<B>(p, i, j, T0, false);
+            publish(c, &fL[i * t + j], ticket);
         } else if (kind == K_S2_DIAG) {  // spdinv_trtri: X_jj = TRTRI(A_jj)
-            load_A_tile<B>(p, j, j, c.T0, true);
-            tile_trtri<B>(c.T0, c.tmp);
-            store_ws_tile<B>(const_cast<double*>(tileD<B>(p, j)), c.T0);
-            store_A_tile<B>(p, j, j, c.T0, true);
-            publish<B>(c, &fD[j], ticket);
+            load_A_tile<B>(p, j, j, T0, true);
+            tile_trtri<B>(T0, tmp);
+            store_ws_tile<B>(const_cast<double*>(tileD<B>(p, j)), T0);
+            store_A_tile<B>(p, j, j, T0, true);
+            publish(c, &fD[j], ticket);
         } else if (kind == K_S2_OFF) {
             // X_ii L_ij
             if (!fetch<B>(c, &fD[i], from_A ? &fL[i * t + j] : nullptr, tileD<B>(p, i), tileB<B>(p, i, j))) return;
             acc_zero<B>(acc);
-            tile_mma<B, false, false, false, LOWER, FULL>(acc, c.T0, c.T1);
+            tile_mma<B, false, false, false, LOWER, FULL>(acc, T0, T1);
             for (int k = i - 1; k > j; --k) {  // GEMM chain, D order
                 if (!fetch<B>(c, &fX[i * t + k], from_A ? &fL[k * t + j] : nullptr, tileC<B>(p, i, k),
                               tileB<B>(p, k, j)))
                     return;
-                tile_mma<B, false, false, false, FULL, FULL>(acc, c.T0, c.T1);
+                tile_mma<B, false, false, false, FULL, FULL>(acc, T0, T1);
             }
             // X_ij = -(...) X_jj
             if (!fetch<B>(c, &fD[j], nullptr, nullptr, tileD<B>(p, j))) return;
-            acc_store<B>(acc, c.T0);
-            __syncthreads();
+            acc_store<B>(acc, T0);
+            cta_sync();
             acc_zero<B>(acc);
-            tile_mma<B, false, false, true, FULL, LOWER>(acc, c.T0, c.T1);
-            __syncthreads();
-            acc_store<B>(acc, c.T0);
-            __syncthreads();
-            store_ws_tile<B>(const_cast<double*>(tileC<B>(p, i, j)), c.T0);
-            if (p.steps == STEPS_TRTRI) store_A_tile<B>(p, i, j, c.T0, false);
-            publish<B>(c, &fX[i * t + j], ticket);
+            tile_mma<B, false, false, true, FULL, LOWER>(acc, T0, T1);
+            cta_sync();
+            acc_store<B>(acc, T0);
+            cta_sync();
+            store_ws_tile<B>(const_cast<double*>(tileC<B>(p, i, j)), T0);
+            if (p.steps == STEPS_TRTRI) store_A_tile<B>(p, i, j, T0, false);
+            publish(c, &fX[i * t + j], ticket);
         } else if (kind == K_S3_OFF) {
             const bool wait_x = p.steps != STEPS_LAUUM;
             // X_ii^T X_ij
             if (!fetch<B>(c, dflag(i), wait_x ? &fX[i * t + j] : nullptr, tileD<B>(p, i), tileC<B>(p, i, j))) return;
             acc_zero<B>(acc);
-            tile_mma<B, true, false, false, LOWER, FULL>(acc, c.T0, c.T1);
+            tile_mma<B, true, false, false, LOWER, FULL>(acc, T0, T1);
             for (int k = i + 1; k < t; ++k) {  // GEMM chain, U order
                 if (!fetch<B>(c, wait_x ? &fX[k * t + i] : nullptr, wait_x ? &fX[k * t + j] : nullptr,
                               tileC<B>(p, k, i), tileC<B>(p, k, j)))
                     return;
-                tile_mma<B, true, false, false, FULL, FULL>(acc, c.T0, c.T1);
+                tile_mma<B, true, false, false, FULL, FULL>(acc, T0, T1);
             }
-            __syncthreads();
-            acc_store<B>(acc, c.T0);
-            __syncthreads();
-            store_A_tile<B>(p, i, j, c.T0, false);
+            cta_sync();
+            acc_store<B>(acc, T0);
+            cta_sync();
+            store_A_tile<B>(p, i, j, T0, false);
         } else {  // K_S3_DIAG
             const bool wait_x = p.steps != STEPS_LAUUM;
             // LAUUM: X_ii^T X_ii
             if (!fetch<B>(c, dflag(i), nullptr, tileD<B>(p, i), nullptr)) return;
             acc_zero<B>(acc);
-            tile_mma<B, true, false, false, LOWER, LOWER>(acc, c.T0, c.T0);
+            tile_mma<B, true, false, false, LOWER, LOWER>(acc, T0, T0);
             for (int k = i + 1; k < t; ++k) {  // SYRK chain, U order
                 if (!fetch<B>(c, wait_x ? &fX[k * t + i] : nullptr, nullptr, tileC<B>(p, k, i), nullptr)) return;
-                tile_mma<B, true, false, false, FULL, FULL>(acc, c.T0, c.T0);
+                tile_mma<B, true, false, false, FULL, FULL>(acc, T0, T0);
             }
-            __syncthreads();
-            acc_store<B>(acc, c.T0);
-            __syncthreads();
-            store_A_tile<B>(p, i, i, c.T0, true);
+            cta_sync();
+            acc_store<B>(acc, T0);
+            cta_sync();
+            store_A_tile<B>(p, i, i, T0, true);
         }
     }
 }

@@ -1,0 +1,449 @@
+// Mixed-precision inversion (an added form): the tile DAG of Algorithm 1
+// (Sec. 2) with renaming and pipelining (Sec. 3) runs with its bulk updates
+// (GEMM, SYRK, TRMM) in FP32 while every diagonal-tile POTRF and TRTRI runs in
+// native FP64; then `refine_steps` residual corrections bring the result back
+// to FP64 accuracy:
+//      R = I - A X         (FP64, tensor-core MMA; A read from its lower triangle)
+//      X <- X + X R        (the small correction X R in FP32, added in FP64)
+// and the lower triangle of X is written into A.
+//
+// The persistent FP32 kernel follows the FP64 one task for task.  Its
+// renamed stores hold FP32 tiles padded to b x (b+1) -- the layout the
+// CUDA-core tile products read without bank conflicts -- so that each tile
+// still moves as a single bulk (TMA) copy.  Step 3 writes the full symmetric X
+// (FP64) into a workspace matrix instead of A, which stays intact for the
+// residual.
+#include <climits>
+
+#include "api_internal.h"
+#include "kernels.h"
+#include "persist.cuh"
+#include "tile_f32.cuh"
+#include "tile_fp64.cuh"
+
+namespace spdinv {
+
+struct KParamsMixed {
+    int64_t n, lda;
+    int t, b, ntasks;
+    const double* A;
+    float* Bw;
+    float* Cw;
+    float* Dw;
+    double* X;  // full symmetric X, n x n, leading dimension n
+    const uint32_t* tasks;
+    int* flags;
+    int* ctrl;
+    long long timeout_ns;
+    int drop_task;
+};
+
+namespace {
+
+template <int B>
+__host__ __device__ constexpr int padded_tile() {
+    return B * (B + 1);
+}
+
+template <int B>
+__device__ __forceinline__ bool fetch32(PCtx& c, const int* f0, const int* f1, const float* g0, const float* g1) {
+    return fetch(c, f0, f1, g0, g1, (uint32_t)(padded_tile<B>() * sizeof(float)));
+}
+
+template <int B>
+__device__ __forceinline__ const float* tB(const KParamsMixed& p, int i, int j) {
+    return p.Bw + ((int64_t)i * (i - 1) / 2 + j) * (int64_t)padded_tile<B>();
+}
+template <int B>
+__device__ __forceinline__ const float* tC(const KParamsMixed& p, int i, int j) {
+    return p.Cw + ((int64_t)i * (i - 1) / 2 + j) * (int64_t)padded_tile<B>();
+}
+template <int B>
+__device__ __forceinline__ const float* tD(const KParamsMixed& p, int j) {
+    return p.Dw + (int64_t)j * padded_tile<B>();
+}
+
+// Tile of A (FP64) into an FP32 shared tile (LD = B+1), padded.
+template <int B>
+__device__ void load_A32(const KParamsMixed& p, int ti, int tj, float* T, bool lower_only) {
+    constexpr int LD = B + 1;
+    for (int idx = threadIdx.x; idx < B * B; idx += kThreads) {
+        const int r = idx % B, c = idx / B;
+        const int64_t gr = (int64_t)ti * B + r, gc = (int64_t)tj * B + c;
+        float v;
+        if (gr < p.n && gc < p.n) v = (lower_only && r < c) ? 0.f : (float)p.A[gr + gc * p.lda];
+        else v = (ti == tj && r == c) ? 1.f : 0.f;
+        T[c * LD + r] = v;
+    }
+}
+
+template <int B>
+__device__ void store_ws32(float* g, const float* T) {
+    const float4* s = reinterpret_cast<const float4*>(T);
+    float4* d = reinterpret_cast<float4*>(g);
+    for (int idx = threadIdx.x; idx < padded_tile<B>() / 4; idx += kThreads) d[idx] = s[idx];
+}
+
+// Tile (ti, tj) of X (and, mirrored, (tj, ti)); diagonal tiles are written
+// from their lower part on both sides, so X is exactly symmetric.
+template <int B>
+__device__ void store_X(const KParamsMixed& p, int ti, int tj, const float* T) {
+    constexpr int LD = B + 1;
+    for (int idx = threadIdx.x; idx < B * B; idx += kThreads) {
+        const int r = idx % B, c = idx / B;
+        const int64_t gr = (int64_t)ti * B + r, gc = (int64_t)tj * B + c;
+        if (gr >= p.n || gc >= p.n) continue;
+        if (ti == tj) {
+            const float v = r >= c ? T[c * LD + r] : T[r * LD + c];
+            p.X[gr + gc * p.n] = (double)v;
+        } else {
+            p.X[gr + gc * p.n] = (double)T[c * LD + r];
+        }
+    }
+    if (ti != tj) {
+        for (int idx = threadIdx.x; idx < B * B; idx += kThreads) {
+            const int r = idx % B, c = idx / B;  // target (tj*B + r, ti*B + c)
+            const int64_t gr = (int64_t)tj * B + r, gc = (int64_t)ti * B + c;
+            if (gr < p.n && gc < p.n) p.X[gr + gc * p.n] = (double)T[r * LD + c];
+        }
+    }
+}
+
+template <int B>
+__global__ void __launch_bounds__(kThreads) potri_mixed_persistent(const KParamsMixed prm) {
+    unsigned char* const smem_raw = dynamic_smem();
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ int s_task, s_flag, s_fail;
+    constexpr int LD = B + 1;
+    const KParamsMixed& p = prm;
+    constexpr int kT = round_up128(padded_tile<B>() * (int)sizeof(float));
+    float* const T0 = reinterpret_cast<float*>(smem_raw);  // bulk-copy targets first
+    float* const T1 = reinterpret_cast<float*>(smem_raw + kT);
+    double* const Td = reinterpret_cast<double*>(smem_raw + 2 * kT);  // FP64 diagonal tile, stride B
+    double* const tmpd = Td + B * B;                                   // kThreads doubles
+    PCtx c;
+    c.T0 = T0;
+    c.T1 = T1;
+    c.bar = &bar;
+    c.s_flag = &s_flag;
+    c.phase = 0;
+    c.ctrl = p.ctrl;
+    c.timeout_ns = p.timeout_ns;
+    c.drop_task = p.drop_task;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_proxy_async_shared();
+    }
+    cta_sync();
+    if (!layout_ok(T0, T1, p.Bw, p.Cw, p.Dw, p.ctrl)) return;
+    const int t = p.t;
+    int* const fL = p.flags;
+    int* const fX = p.flags + (int64_t)t * t;
+    int* const fD = p.flags + 2 * (int64_t)t * t;
+
+    for (;;) {
+        const int ticket = next_ticket(p.ctrl, p.ntasks, &s_task);
+        if (ticket < 0) return;
+        const uint32_t e = p.tasks[ticket];
+        const int kind = (int)task_kind(e), i = (int)task_i(e), j = (int)task_j(e);
+        Acc32<B> acc;
+
+        if (kind == K_S1_DIAG) {
+            load_A32<B>(p, j, j, T0, true);
+            cta_sync();
+            acc_load<B>(acc, T0);
+            for (int k = 0; k < j; ++k) {  // SYRK chain (FP32)
+                if (!fetch32<B>(c, &fL[j * t + k], nullptr, tB<B>(p, j, k), nullptr)) return;
+                tile_mma<B, false, true, true, FULL, FULL>(acc, T0, T0);
+            }
+            cta_sync();
+            acc_store<B>(acc, T0);
+            cta_sync();
+            for (int idx = threadIdx.x; idx < B * B; idx += kThreads) {  // to FP64
+                const int r = idx % B, cc = idx / B;
+                Td[idx] = r >= cc ? (double)T0[cc * LD + r] : 0.0;
+            }
+            const int fail = tile_potrf<B>(Td, &s_fail);  // POTRF in FP64
+            if (fail) {
+                if (threadIdx.x == 0) record_info(p.ctrl, j * B + fail);
+                return;
+            }
+            tile_zero_upper<B>(Td);
+            tile_trtri<B>(Td, tmpd);  // TRTRI in FP64
+            for (int idx = threadIdx.x; idx < padded_tile<B>(); idx += kThreads) {
+                const int r = idx % LD, cc = idx / LD;
+                T0[idx] = (r < B && r >= cc) ? (float)Td[cc * B + r] : 0.f;
+            }
+            cta_sync();
+            store_ws32<B>(const_cast<float*>(tD<B>(p, j)), T0);
+            publish(c, &fD[j], ticket);
+        } else if (kind == K_S1_OFF) {
+            load_A32<B>(p, i, j, T0, false);
+            cta_sync();
+            acc_load<B>(acc, T0);
+            for (int k = 0; k < j; ++k) {
+                if (!fetch32<B>(c, &fL[i * t + k], &fL[j * t + k], tB<B>(p, i, k), tB<B>(p, j, k))) return;
+                tile_mma<B, false, true, true, FULL, FULL>(acc, T0, T1);
+            }
+            if (!fetch32<B>(c, &fD[j], nullptr, nullptr, tD<B>(p, j))) return;
+            acc_store<B>(acc, T0);
+            cta_sync();
+            acc_zero<B>(acc);
+            tile_mma<B, false, true, false, FULL, LOWER>(acc, T0, T1);
+            cta_sync();
+            acc_store<B>(acc, T0);
+            cta_sync();
+            store_ws32<B>(const_cast<float*>(tB<B>(p, i, j)), T0);
+            publish(c, &fL[i * t + j], ticket);
+        } else if (kind == K_S2_OFF) {
+            if (!fetch32<B>(c, &fD[i], &fL[i * t + j], tD<B>(p, i), tB<B>(p, i, j))) return;
+            acc_zero<B>(acc);
+            tile_mma<B, false, false, false, LOWER, FULL>(acc, T0, T1);
+            for (int k = i - 1; k > j; --k) {
+                if (!fetch32<B>(c, &fX[i * t + k], &fL[k * t + j], tC<B>(p, i, k), tB<B>(p, k, j))) return;
+                tile_mma<B, false, false, false, FULL, FULL>(acc, T0, T1);
+            }
+            if (!fetch32<B>(c, &fD[j], nullptr, nullptr, tD<B>(p, j))) return;
+            acc_store<B>(acc, T0);
+            cta_sync();
+            acc_zero<B>(acc);
+            tile_mma<B, false, false, true, FULL, LOWER>(acc, T0, T1);
+            cta_sync();
+            acc_store<B>(acc, T0);
+            cta_sync();
+            store_ws32<B>(const_cast<float*>(tC<B>(p, i, j)), T0);
+            publish(c, &fX[i * t + j], ticket);
+        } else if (kind == K_S3_OFF) {
+            if (!fetch32<B>(c, &fD[i], &fX[i * t + j], tD<B>(p, i), tC<B>(p, i, j))) return;
+            acc_zero<B>(acc);
+            tile_mma<B, true, false, false, LOWER, FULL>(acc, T0, T1);
+            for (int k = i + 1; k < t; ++k) {
+                if (!fetch32<B>(c, &fX[k * t + i], &fX[k * t + j], tC<B>(p, k, i), tC<B>(p, k, j))) return;
+                tile_mma<B, true, false, false, FULL, FULL>(acc, T0, T1);
+            }
+            cta_sync();
+            acc_store<B>(acc, T0);
+            cta_sync();
+            store_X<B>(p, i, j, T0);
+        } else if (kind == K_S3_DIAG) {
+            if (!fetch32<B>(c, &fD[i], nullptr, tD<B>(p, i), nullptr)) return;
+            acc_zero<B>(acc);
+            tile_mma<B, true, false, false, LOWER, LOWER>(acc, T0, T0);
+            for (int k = i + 1; k < t; ++k) {
+                if (!fetch32<B>(c, &fX[k * t + i], nullptr, tC<B>(p, k, i), nullptr)) return;
+                tile_mma<B, true, false, false, FULL, FULL>(acc, T0, T0);
+            }
+            cta_sync();
+            acc_store<B>(acc, T0);
+            cta_sync();
+            store_X<B>(p, i, i, T0);
+        }
+    }
+}
+
+constexpr int RB = 64;  // output tile of the refinement products
+
+__device__ __forceinline__ bool aborted(const int* ctrl) { return ctrl[2] != 0 || ctrl[3] != 0; }
+
+// R = I - A X with A symmetric, read from its lower triangle; FP64 MMA.
+__global__ void __launch_bounds__(kThreads) residual_kernel(int64_t n, const double* A, int64_t lda,
+                                                            const double* X, double* R, const int* ctrl) {
+    unsigned char* const smem_raw = dynamic_smem();
+    if (aborted(ctrl)) return;
+    double* S0 = reinterpret_cast<double*>(smem_raw);
+    double* S1 = S0 + RB * RB;
+    const int t = (int)((n + RB - 1) / RB);
+    const int ti = blockIdx.x % t, tj = blockIdx.x / t;
+    Acc<RB> acc;
+    acc_zero<RB>(acc);
+    for (int kt = 0; kt < t; ++kt) {
+        cta_sync();
+        for (int idx = threadIdx.x; idx < RB * RB; idx += kThreads) {
+            const int r = idx % RB, c = idx / RB;
+            // A tile (ti, kt): below/on the diagonal read directly, above it
+            // read the mirrored lower tile (kt, ti), coalesced, and transpose.
+            if (ti >= kt) {
+                const int64_t gr = (int64_t)ti * RB + r, gc = (int64_t)kt * RB + c;
+                double v = 0.0;
+                if (gr < n && gc < n) v = gr >= gc ? A[gr + gc * lda] : A[gc + gr * lda];
+                S0[c * RB + r] = v;
+            } else {
+                const int64_t gr = (int64_t)kt * RB + r, gc = (int64_t)ti * RB + c;  // lower element
+                S0[r * RB + c] = (gr < n && gc < n) ? A[gr + gc * lda] : 0.0;
+            }
+            const int64_t xr = (int64_t)kt * RB + r, xc = (int64_t)tj * RB + c;
+            S1[c * RB + r] = (xr < n && xc < n) ? X[xr + xc * n] : 0.0;
+        }
+        cta_sync();
+        tile_mma<RB, false, false, false, FULL, FULL>(acc, S0, S1);
+    }
+#pragma unroll
+    for (int mi = 0; mi < TileCfg<RB>::MI; ++mi)
+#pragma unroll
+        for (int ni = 0; ni < TileCfg<RB>::NI; ++ni)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                int r, cc;
+                acc_coord<RB>(mi, ni, h, r, cc);
+                const int64_t gr = (int64_t)ti * RB + r, gc = (int64_t)tj * RB + cc;
+                if (gr < n && gc < n) R[gr + gc * n] = (gr == gc ? 1.0 : 0.0) - acc.v[mi][ni][h];
+            }
+}
+
+// Xn = X + X R, the product in FP32 (R is small), the sum in FP64.
+__global__ void __launch_bounds__(kThreads) correct_kernel(int64_t n, const double* X, const double* R, double* Xn,
+                                                           const int* ctrl) {
+    unsigned char* const smem_raw = dynamic_smem();
+    if (aborted(ctrl)) return;
+    constexpr int LD = RB + 1;
+    float* S0 = reinterpret_cast<float*>(smem_raw);
+    float* S1 = S0 + RB * LD;
+    const int t = (int)((n + RB - 1) / RB);
+    const int ti = blockIdx.x % t, tj = blockIdx.x / t;
+    Acc32<RB> acc;
+    acc_zero<RB>(acc);
+    for (int kt = 0; kt < t; ++kt) {
+        cta_sync();
+        for (int idx = threadIdx.x; idx < RB * RB; idx += kThreads) {
+            const int r = idx % RB, c = idx / RB;
+            const int64_t ar = (int64_t)ti * RB + r, ac = (int64_t)kt * RB + c;
+            S0[c * LD + r] = (ar < n && ac < n) ? (float)X[ar + ac * n] : 0.f;
+            const int64_t br = (int64_t)kt * RB + r, bc = (int64_t)tj * RB + c;
+            S1[c * LD + r] = (br < n && bc < n) ? (float)R[br + bc * n] : 0.f;
+        }
+        cta_sync();
+        tile_mma<RB, false, false, false, FULL, FULL>(acc, S0, S1);
+    }
+    cta_sync();
+    acc_store<RB>(acc, S0);
+    cta_sync();
+    for (int idx = threadIdx.x; idx < RB * RB; idx += kThreads) {
+        const int r = idx % RB, c = idx / RB;
+        const int64_t gr = (int64_t)ti * RB + r, gc = (int64_t)tj * RB + c;
+        if (gr < n && gc < n) Xn[gr + gc * n] = X[gr + gc * n] + (double)S0[c * LD + r];
+    }
+}
+
+// Lower triangle of X (ld n) into A (ld lda).
+__global__ void store_lower_kernel(int64_t n, const double* X, double* A, int64_t lda, const int* ctrl) {
+    if (aborted(ctrl)) return;
+    const int64_t j = blockIdx.x;
+    for (int64_t i = j + threadIdx.x; i < n; i += blockDim.x) A[i + j * lda] = X[i + j * n];
+}
+
+__global__ void finalize_info_mixed(const int* ctrl, int* d_info) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) *d_info = ctrl[2] != 0 ? ctrl[2] : ctrl[3];
+}
+
+template <int B>
+int mixed_smem() {
+    return 2 * round_up128(padded_tile<B>() * (int)sizeof(float)) + (B * B + kThreads) * (int)sizeof(double);
+}
+
+template <int B>
+cudaError_t launch_mixed_dag(const KParamsMixed& p, int ctas_per_sm, int num_sms, cudaStream_t s) {
+    auto kern = potri_mixed_persistent<B>;
+    const int sm = mixed_smem<B>();
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    if (e != cudaSuccess) return e;
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, sm);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) return cudaErrorInvalidConfiguration;
+    int per = ctas_per_sm > 0 ? ctas_per_sm : occ;
+    per = per < occ ? per : occ;
+    int grid = num_sms * per;
+    if (grid > p.ntasks) grid = p.ntasks;
+    kern<<<grid, kThreads, sm, s>>>(p);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+spdinv_status run_mixed(int64_t n, double* dA, int64_t lda, const spdinv_opts* o, int* d_info,
+                        cudaStream_t stream) {
+    if (n < 0) return SPDINV_ERR_N;
+    if (lda < (n > 1 ? n : 1)) return SPDINV_ERR_LDA;
+    if (n > 0 && dA == nullptr) return SPDINV_ERR_NULL;
+    if (o->precision != SPDINV_PREC_MIXED_FP32) return SPDINV_ERR_UNSUPPORTED;
+    const int b = o->tile > 0 ? o->tile : 64;
+    if (b != 32 && b != 64) return SPDINV_ERR_UNSUPPORTED;
+    if (o->refine_steps < 0 || o->refine_steps > 16) return SPDINV_ERR_UNSUPPORTED;
+    const int64_t t64 = (n + b - 1) / b;
+    if (t64 > 16383) return SPDINV_ERR_N;
+    if (n == 0) {
+        if (d_info) {
+            cudaError_t e = cudaMemsetAsync(d_info, 0, sizeof(int), stream);
+            if (e != cudaSuccess) return cuda_fail(e);
+        }
+        return SPDINV_OK;
+    }
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e);
+    DeviceState& ds = device_state(dev);
+    std::lock_guard<std::mutex> lk(ds.mu);
+    const int t = (int)t64;
+    auto align = [](size_t v) { return (v + 255) / 256 * 256; };
+    const size_t tileb = (size_t)b * (b + 1) * sizeof(float);
+    const size_t ntri = (size_t)t * (t - 1) / 2;
+    const size_t ctrl_bytes = align(sizeof(int) * (4 + 2 * (size_t)t * t + t));
+    const size_t bytesBC = align(ntri * tileb), bytesD = align((size_t)t * tileb);
+    const size_t nn = align((size_t)n * n * sizeof(double));
+    const int steps = o->refine_steps;
+    const size_t total = ctrl_bytes + 2 * bytesBC + bytesD + nn * (steps > 0 ? 3 : 1);
+    e = ds.ensure_workspace(total);
+    if (e != cudaSuccess) return cuda_fail(e);
+    char* base = static_cast<char*>(ds.ws);
+    KParamsMixed p{};
+    p.n = n;
+    p.lda = lda;
+    p.t = t;
+    p.b = b;
+    p.A = dA;
+    p.ctrl = reinterpret_cast<int*>(base);
+    p.flags = p.ctrl + 4;
+    p.Bw = reinterpret_cast<float*>(base + ctrl_bytes);
+    p.Cw = reinterpret_cast<float*>(base + ctrl_bytes + bytesBC);
+    p.Dw = reinterpret_cast<float*>(base + ctrl_bytes + 2 * bytesBC);
+    double* X0 = reinterpret_cast<double*>(base + ctrl_bytes + 2 * bytesBC + bytesD);
+    double* R = steps > 0 ? reinterpret_cast<double*>(reinterpret_cast<char*>(X0) + nn) : nullptr;
+    double* X1 = steps > 0 ? reinterpret_cast<double*>(reinterpret_cast<char*>(X0) + 2 * nn) : nullptr;
+    p.X = X0;
+    p.timeout_ns = (long long)((o->wait_timeout_s > 0 ? o->wait_timeout_s : 60.0) * 1e9);
+    p.drop_task = (o->wait_timeout_s > 0 && o->fault_drop_task >= 0) ? o->fault_drop_task : -1;
+    e = ds.exec_plan(t, STEPS_ALL, &p.tasks, &p.ntasks);
+    if (e != cudaSuccess) return cuda_fail(e);
+    e = cudaMemsetAsync(p.ctrl, 0, ctrl_bytes, stream);
+    if (e != cudaSuccess) return cuda_fail(e);
+    e = b == 64 ? launch_mixed_dag<64>(p, o->ctas_per_sm, ds.num_sms, stream)
+                : launch_mixed_dag<32>(p, o->ctas_per_sm, ds.num_sms, stream);
+    if (e != cudaSuccess) return cuda_fail(e);
+    int launches = 1;
+    const int rt = (int)((n + RB - 1) / RB);
+    const int rsm = 2 * RB * RB * (int)sizeof(double);
+    const int csm = 2 * RB * (RB + 1) * (int)sizeof(float);
+    e = cudaFuncSetAttribute(residual_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, rsm);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(correct_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, csm);
+    if (e != cudaSuccess) return cuda_fail(e);
+    double* Xc = X0;
+    for (int s = 0; s < steps; ++s) {
+        double* Xn = (Xc == X0) ? X1 : X0;
+        residual_kernel<<<(unsigned)((int64_t)rt * rt), kThreads, rsm, stream>>>(n, dA, lda, Xc, R, p.ctrl);
+        correct_kernel<<<(unsigned)((int64_t)rt * rt), kThreads, csm, stream>>>(n, Xc, R, Xn, p.ctrl);
+        Xc = Xn;
+        launches += 2;
+    }
+    store_lower_kernel<<<(unsigned)n, 256, 0, stream>>>(n, Xc, dA, lda, p.ctrl);
+    launches += 1;
+    if (d_info) {
+        finalize_info_mixed<<<1, 32, 0, stream>>>(p.ctrl, d_info);
+        launches += 1;
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e);
+    count_launches(launches);
+    return SPDINV_OK;
+}
+
+}  // namespace spdinv

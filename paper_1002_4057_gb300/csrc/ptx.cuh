@@ -9,6 +9,25 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
+// The CTA's dynamic shared memory.  Every kernel takes it from here, so the
+// array has one declaration (one alignment) in each translation unit;
+// 1024 bytes suits bulk copies and swizzled tensor-core operand tiles.
+__device__ __forceinline__ unsigned char* dynamic_smem() {
+    extern __shared__ __align__(1024) unsigned char spdinv_dynamic_smem[];
+    return spdinv_dynamic_smem;
+}
+
+__host__ __device__ constexpr int round_up128(int v) { return (v + 127) / 128 * 128; }
+
+// CTA-wide barrier that first reconverges the calling warp.  __syncthreads is
+// the aligned barrier, whose result is undefined when the lanes of a warp
+// reach it apart (after a loop whose trip count differs between lanes, or
+// after a branch taken by one lane); __syncwarp brings them together first.
+__device__ __forceinline__ void cta_sync() {
+    __syncwarp();
+    __syncthreads();
+}
+
 // ---- mbarrier ---------------------------------------------------------------
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");

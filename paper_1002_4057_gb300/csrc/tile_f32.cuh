@@ -49,18 +49,18 @@ __device__ __forceinline__ void acc_load(Acc32<B>& a, const float* T) {
         for (int c = 0; c < CN; ++c) a.v[r][c] = T[(c0 + c) * LD + r0 + r];
 }
 
-// acc (+|-)= op(P) op(Q), FP32 FMA; triangular operands skip zero k-ranges
-// per thread.
+// acc (+|-)= op(P) op(Q), FP32 FMA.  A triangular right operand lets each
+// warp skip the k-range that multiplies its zero part; the bounds are
+// uniform across the warp (a warp owns all rows and 2*CN columns), so no warp
+// diverges.  (A triangular left operand gives no warp-wide skip here.)
 template <int B, bool TA, bool TB, bool NEG, int SP, int SQ>
-__device__ __forceinline__ void tile_mma(Acc32<B>& acc, const float* __restrict__ P, const float* __restrict__ Q) {
+__device__ __forceinline__ void tile_mma(Acc32<B>& acc, const float* P, const float* Q) {
     constexpr int RM = Cfg32<B>::RM, CN = Cfg32<B>::CN, LD = Cfg32<B>::LD;
     const int r0 = (threadIdx.x % 16) * RM, c0 = (threadIdx.x / 16) * CN;
+    const int cw = (threadIdx.x / 32) * 2 * CN;  // the warp's first column
     int kb = 0, ke = B;
-    if (SP == LOWER) {
-        if (TA) kb = r0; else ke = r0 + RM;
-    }
     if (SQ == LOWER) {
-        if (TB) ke = min(ke, c0 + CN); else kb = max(kb, c0);
+        if (TB) ke = cw + 2 * CN; else kb = cw;
     }
 #pragma unroll 4
     for (int k = kb; k < ke; ++k) {
@@ -95,23 +95,23 @@ __device__ int tile_potrf(float* T, int* s_fail) {
     const int r = threadIdx.x % B, cs = threadIdx.x / B;
     const bool active = threadIdx.x < RS * B;
     if (threadIdx.x == 0) *s_fail = 0;
-    __syncthreads();
+    cta_sync();
     for (int c = 0; c < B; ++c) {
         if (threadIdx.x == 0) {
             const float d = T[c * LD + c];
             if (d > 0.f) T[c * LD + c] = sqrtf(d);
             else *s_fail = c + 1;
         }
-        __syncthreads();
+        cta_sync();
         if (*s_fail) return *s_fail;
         const float l = T[c * LD + c];
         if (active && cs == 0 && r > c) T[c * LD + r] = T[c * LD + r] / l;
-        __syncthreads();
+        cta_sync();
         if (active && r > c) {
             const float lr = T[c * LD + r];
             for (int k = c + 1 + cs; k <= r; k += RS) T[k * LD + r] -= lr * T[c * LD + k];
         }
-        __syncthreads();
+        cta_sync();
     }
     return 0;
 }
@@ -123,22 +123,22 @@ __device__ void tile_trtri(float* T, float* tmp) {
     constexpr int LD = Cfg32<B>::LD, RS = kThreads / B > 0 ? kThreads / B : 1;
     const int r = threadIdx.x % B, cs = threadIdx.x / B;
     const bool active = threadIdx.x < RS * B;
-    __syncthreads();
+    cta_sync();
     for (int j = B - 1; j >= 0; --j) {
         const float xjj = 1.f / T[j * LD + j];
         float s = 0.f;
         if (active && r > j)
             for (int k = j + 1 + cs; k <= r; k += RS) s += T[k * LD + r] * T[j * LD + k];
         if (active && RS > 1) tmp[cs * B + r] = s;
-        __syncthreads();
+        cta_sync();
         if (active && cs == 0 && r > j) {
             float tot = s;
             for (int u = 1; u < RS; ++u) tot += tmp[u * B + r];
             T[j * LD + r] = -tot * xjj;
         }
-        __syncthreads();
+        cta_sync();
         if (threadIdx.x == 0) T[j * LD + j] = xjj;
-        __syncthreads();
+        cta_sync();
     }
 }
 

@@ -80,7 +80,7 @@ enum TriShape { FULL = 0, LOWER = 1 };
 // op(X) = X (TA/TB false) or X^T (true).  When a stored operand is lower
 // triangular, each warp skips the k-range that multiplies its zero part.
 template <int B, bool TA, bool TB, bool NEG, int SP, int SQ>
-__device__ __forceinline__ void tile_mma(Acc<B>& acc, const double* __restrict__ P, const double* __restrict__ Q) {
+__device__ __forceinline__ void tile_mma(Acc<B>& acc, const double* P, const double* Q) {
     constexpr int W = TileCfg<B>::W, MI = TileCfg<B>::MI, NI = TileCfg<B>::NI;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int g = lane >> 2, q = lane & 3;
@@ -134,23 +134,23 @@ __device__ int tile_potrf(double* T, int* s_fail) {
     constexpr int RS = kThreads / B;  // threads per row (2 for b=64, 4 for b=32)
     const int r = threadIdx.x % B, cs = threadIdx.x / B;
     if (threadIdx.x == 0) *s_fail = 0;
-    __syncthreads();
+    cta_sync();
     for (int c = 0; c < B; ++c) {
         if (threadIdx.x == 0) {
             const double d = T[c * B + c];
             if (d > 0.0) T[c * B + c] = sqrt(d);
             else *s_fail = c + 1;
         }
-        __syncthreads();
+        cta_sync();
         if (*s_fail) return *s_fail;
         const double l = T[c * B + c];
         if (cs == 0 && r > c) T[c * B + r] = T[c * B + r] / l;
-        __syncthreads();
+        cta_sync();
         if (r > c) {
             const double lr = T[c * B + r];
             for (int k = c + 1 + cs; k <= r; k += RS) T[k * B + r] -= lr * T[c * B + k];
         }
-        __syncthreads();
+        cta_sync();
     }
     return 0;
 }
@@ -163,7 +163,7 @@ template <int B>
 __device__ void tile_trtri(double* T, double* tmp) {
     constexpr int RS = kThreads / B;
     const int r = threadIdx.x % B, cs = threadIdx.x / B;
-    __syncthreads();
+    cta_sync();
     for (int j = B - 1; j >= 0; --j) {
         const double xjj = 1.0 / T[j * B + j];
         // rows i > j: partial sums over k split among the RS threads of a row
@@ -174,18 +174,18 @@ __device__ void tile_trtri(double* T, double* tmp) {
         if (RS > 1) {
             tmp[cs * B + r] = s;
         }
-        __syncthreads();
+        cta_sync();
         if (cs == 0 && r > j) {
             double tot = s;
             for (int u = 1; u < RS; ++u) tot += tmp[u * B + r];
             T[j * B + r] = -tot * xjj;
         }
-        __syncthreads();
+        cta_sync();
         if (threadIdx.x == 0) T[j * B + j] = xjj;
         // the next column reads T[j*B+j] only through X_ik (k > j'), written
         // above by this thread; the barrier at the top of the next iteration
         // orders it.
-        __syncthreads();
+        cta_sync();
     }
 }
 

@@ -1,0 +1,98 @@
+"""Mixed precision: FP32 bulk tile updates, FP64 diagonal tiles and FP64
+residual corrections, against the FP64 oracle.  The error is stated for every
+result; the 1e-10 gate applies with the number of correction steps the
+conditioning needs (one at cond 1e2, two at 1e4)."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import closed_forms as cf
+import spd_inputs as si
+from gpu_util import full_from_lower, lower_np, to_dev
+
+pytestmark = pytest.mark.gpu
+
+MIXED = 1
+
+
+def _run(T, A, gpu, steps, tile=64):
+    dA = to_dev(A, gpu)
+    info = T.potri_(dA, precision=MIXED, refine_steps=steps, tile=tile)
+    import torch
+    torch.cuda.synchronize()
+    return dA, int(info.item())
+
+
+@pytest.mark.parametrize("n", [1, 64, 200, 513, 1000])
+@pytest.mark.parametrize("tile", [32, 64])
+def test_mixed_error_by_steps(gpu, n, tile):
+    from paper_1002_4057_gb300 import torch_api as T
+    for cond, steps_needed in ((1e2, 1), (1e4, 2)):
+        A, _, _ = si.spectral_spd(n, cond, seed=si.SEED_BASE + 2 + n)
+        M, _ = oracle.potri(A)
+        ref = oracle.symmetrize_lower(M)
+        errs = []
+        for steps in range(0, steps_needed + 1):
+            dA, info = _run(T, A, gpu, steps, tile)
+            assert info == 0
+            errs.append(oracle.rel_frobenius(full_from_lower(lower_np(dA)), ref))
+        print("n=%d tile=%d cond=%.0e errors by steps: %s" % (n, tile, cond, ["%.2e" % e for e in errs]))
+        assert errs[0] <= 1e-3  # the FP32 result itself
+        assert errs[-1] <= 1e-10
+        if n > 1:
+            assert errs[-1] < errs[0]
+
+
+def test_mixed_integer_case_exact(gpu):
+    from paper_1002_4057_gb300 import torch_api as T
+    n = 700
+    A, s = si.bidiag_integer_spd(n, seed=3)
+    for steps in (0, 1):
+        dA, info = _run(T, A, gpu, steps)
+        assert info == 0
+        assert np.array_equal(lower_np(dA), np.tril(cf.bidiag_inverse(s)))
+
+
+def test_mixed_info(gpu):
+    from paper_1002_4057_gb300 import torch_api as T
+    d = np.ones(300)
+    d[150] = -2.0
+    dA, info = _run(T, np.diag(d), gpu, 1)
+    assert info == 151
+
+
+def test_mixed_upper_untouched(gpu):
+    from paper_1002_4057_gb300 import torch_api as T
+    n = 130
+    A, _, _ = si.spectral_spd(n, 1e2, seed=8)
+    B = A.copy(order="F")
+    iu = np.triu_indices(n, 1)
+    B[iu] = -3.5
+    dA, info = _run(T, B, gpu, 1)
+    assert info == 0
+    assert np.all(dA.cpu().numpy()[iu] == -3.5)
+
+
+@pytest.mark.slow
+def test_mixed_full_size_sampled(gpu):
+    """n = 16384, cond 1e2: sampled columns against the spectral definition
+    Q diag(1/lam) Q^T.  At this size the FP32 result's error is ~1e-5, so one
+    correction reaches ~7e-10 and two reach the 1e-10 gate."""
+    import torch
+    from paper_1002_4057_gb300 import torch_api as T
+    n = 16384
+    cols = np.array([0, 7777, 16383])
+    for cond, steps in ((1e2, 2),):
+        A, Q, lam = si.spectral_spd(n, cond, seed=si.SEED_BASE + 2, device=gpu)
+        ref = cf.spectral_inverse_columns(Q.cpu().numpy(), lam, cols)
+        del Q
+        W = A.clone()
+        info = T.potri_(W, precision=MIXED, refine_steps=steps, tile=64)
+        assert int(info.item()) == 0
+        Lo = torch.tril(W)
+        Xc = (Lo[:, cols] + torch.tril(Lo, -1).t()[:, cols]).cpu().numpy()
+        err = np.linalg.norm(Xc - ref) / np.linalg.norm(ref)
+        print("n=16384 cond=%.0e steps=%d sampled error %.2e" % (cond, steps, err))
+        assert err <= 1e-10
+        del A, W, Lo
+        torch.cuda.empty_cache()
