@@ -90,7 +90,14 @@ typedef struct {
                             never signals completion, so its consumers hit the wait limit and
                             the call ends with d_info = SPDINV_ERR_TIMEOUT; -1 (or any value
                             below 0) = off.  Only honoured when wait_timeout_s > 0. */
+    int residual;        /* mixed precision: how R = I - A X is formed.
+                            SPDINV_RESIDUAL_EMULATED (0, default): FP64-accurate products of
+                            exact 8-bit slices on the BF16 tensor cores;
+                            SPDINV_RESIDUAL_FP64 (1): native FP64 tensor-core products. */
 } spdinv_opts;
+
+#define SPDINV_RESIDUAL_EMULATED 0
+#define SPDINV_RESIDUAL_FP64 1
 
 /* ------------------------------------------------------------------------
  * The three steps, separately (LAPACK lower-triangle semantics)
@@ -133,6 +140,16 @@ SPDINV_API spdinv_status spdinv_potri(int64_t n, double* dA, int64_t lda, int* d
  * holds three n x n FP64 matrices when refine_steps > 0. */
 SPDINV_API spdinv_status spdinv_potri_ex(int64_t n, double* dA, int64_t lda, const spdinv_opts* opts,
                               int* d_info, cudaStream_t stream);
+
+/* Residual of an approximate inverse (used by the mixed-precision
+ * correction; the paper has none): R = I - A X with A symmetric, given by the
+ * lower triangle of dA (column-major, lda), X full n x n (leading dimension n)
+ * and R full n x n (leading dimension n).  residual = SPDINV_RESIDUAL_EMULATED
+ * forms the products from exact 8-bit slices on the BF16 tensor cores
+ * (error about 1e-15 |A||X|); SPDINV_RESIDUAL_FP64 uses native FP64 MMA.
+ * Uses the library workspace (may allocate on first use). */
+SPDINV_API spdinv_status spdinv_inverse_residual(int64_t n, const double* dA, int64_t lda, const double* dX,
+                                                 double* dR, int residual, cudaStream_t stream);
 
 /* ------------------------------------------------------------------------
  * Inversion without device allocation (the paper has no counterpart)

@@ -31,6 +31,9 @@ SPDINV_PREC_MIXED_BF16X3 = 2
 
 SPDINV_NOALLOC_MAX_N = 1024
 
+SPDINV_RESIDUAL_EMULATED = 0
+SPDINV_RESIDUAL_FP64 = 1
+
 SPDINV_DAG_OUT_OF_PLACE = 1
 SPDINV_DAG_RENAME_DIAG = 2
 SPDINV_DAG_UUU = 4
@@ -43,7 +46,7 @@ STATUS_NAMES = {0: "SPDINV_OK", -1: "SPDINV_ERR_N", -2: "SPDINV_ERR_LDA", -3: "S
 
 class spdinv_opts(ctypes.Structure):
     _fields_ = [("tile", c_int), ("ctas_per_sm", c_int), ("precision", c_int), ("refine_steps", c_int),
-                ("wait_timeout_s", c_double), ("fault_drop_task", c_int)]
+                ("wait_timeout_s", c_double), ("fault_drop_task", c_int), ("residual", c_int)]
 
 
 # name -> (restype, argtypes); every symbol declared in include/spdinv.h
@@ -54,6 +57,7 @@ SIGNATURES = {
     "spdinv_potri": (c_int, [c_int64, P, c_int64, P, P]),
     "spdinv_potri_ex": (c_int, [c_int64, P, c_int64, ctypes.POINTER(spdinv_opts), P, P]),
     "spdinv_potri_noalloc": (c_int, [c_int64, P, c_int64, P, P]),
+    "spdinv_inverse_residual": (c_int, [c_int64, P, c_int64, P, P, c_int, P]),
     "spdinv_potri_batched": (c_int, [c_int, P, P, P, P, P]),
     "spdinv_spotri_batched": (c_int, [c_int, P, P, P, P, P]),
     "spdinv_potri_backward": (c_int, [c_int, c_int64, P, c_int64, c_int64, P, c_int64, c_int64,
@@ -112,6 +116,10 @@ def spdinv_potri(n, dA, lda, d_info, stream):
 
 def spdinv_potri_ex(n, dA, lda, opts, d_info, stream):
     return _call("spdinv_potri_ex", n, dA, lda, ctypes.byref(opts) if opts is not None else None, d_info, stream)
+
+
+def spdinv_inverse_residual(n, dA, lda, dX, dR, residual, stream):
+    return _call("spdinv_inverse_residual", n, dA, lda, dX, dR, residual, stream)
 
 
 def spdinv_potri_noalloc(n, dA, lda, d_info, stream):

@@ -17,6 +17,7 @@
 
 #include "api_internal.h"
 #include "kernels.h"
+#include "ozaki.h"
 #include "persist.cuh"
 #include "tile_f32.cuh"
 #include "tile_fp64.cuh"
@@ -241,6 +242,8 @@ __global__ void __launch_bounds__(kThreads) potri_mixed_persistent(const KParams
     }
 }
 
+}  // namespace
+
 constexpr int RB = 64;  // output tile of the refinement products
 
 __device__ __forceinline__ bool aborted(const int* ctrl) { return ctrl[2] != 0 || ctrl[3] != 0; }
@@ -324,6 +327,8 @@ __global__ void __launch_bounds__(kThreads) correct_kernel(int64_t n, const doub
     }
 }
 
+namespace {
+
 // Lower triangle of X (ld n) into A (ld lda).
 __global__ void store_lower_kernel(int64_t n, const double* X, double* A, int64_t lda, const int* ctrl) {
     if (aborted(ctrl)) return;
@@ -391,7 +396,11 @@ spdinv_status run_mixed(int64_t n, double* dA, int64_t lda, const spdinv_opts* o
     const size_t bytesBC = align(ntri * tileb), bytesD = align((size_t)t * tileb);
     const size_t nn = align((size_t)n * n * sizeof(double));
     const int steps = o->refine_steps;
-    const size_t total = ctrl_bytes + 2 * bytesBC + bytesD + nn * (steps > 0 ? 3 : 1);
+    const bool emulated = o->residual == SPDINV_RESIDUAL_EMULATED;
+    if (o->residual != SPDINV_RESIDUAL_EMULATED && o->residual != SPDINV_RESIDUAL_FP64) return SPDINV_ERR_UNSUPPORTED;
+    constexpr int kSlices = 7, kLevels = 6;
+    const size_t oz = (steps > 0 && emulated) ? align(ozaki_workspace_bytes(n, kSlices)) : 0;
+    const size_t total = ctrl_bytes + 2 * bytesBC + bytesD + nn * (steps > 0 ? 3 : 1) + oz;
     e = ds.ensure_workspace(total);
     if (e != cudaSuccess) return cuda_fail(e);
     char* base = static_cast<char*>(ds.ws);
@@ -409,6 +418,7 @@ spdinv_status run_mixed(int64_t n, double* dA, int64_t lda, const spdinv_opts* o
     double* X0 = reinterpret_cast<double*>(base + ctrl_bytes + 2 * bytesBC + bytesD);
     double* R = steps > 0 ? reinterpret_cast<double*>(reinterpret_cast<char*>(X0) + nn) : nullptr;
     double* X1 = steps > 0 ? reinterpret_cast<double*>(reinterpret_cast<char*>(X0) + 2 * nn) : nullptr;
+    void* ozws = oz ? static_cast<void*>(reinterpret_cast<char*>(X0) + 3 * nn) : nullptr;
     p.X = X0;
     p.timeout_ns = (long long)((o->wait_timeout_s > 0 ? o->wait_timeout_s : 60.0) * 1e9);
     p.drop_task = (o->wait_timeout_s > 0 && o->fault_drop_task >= 0) ? o->fault_drop_task : -1;
@@ -429,10 +439,16 @@ spdinv_status run_mixed(int64_t n, double* dA, int64_t lda, const spdinv_opts* o
     double* Xc = X0;
     for (int s = 0; s < steps; ++s) {
         double* Xn = (Xc == X0) ? X1 : X0;
-        residual_kernel<<<(unsigned)((int64_t)rt * rt), kThreads, rsm, stream>>>(n, dA, lda, Xc, R, p.ctrl);
+        if (emulated) {
+            e = ozaki_residual(n, dA, lda, Xc, R, ozws, kSlices, kLevels, stream, &launches);
+            if (e != cudaSuccess) return cuda_fail(e);
+        } else {
+            residual_kernel<<<(unsigned)((int64_t)rt * rt), kThreads, rsm, stream>>>(n, dA, lda, Xc, R, p.ctrl);
+            launches += 1;
+        }
         correct_kernel<<<(unsigned)((int64_t)rt * rt), kThreads, csm, stream>>>(n, Xc, R, Xn, p.ctrl);
         Xc = Xn;
-        launches += 2;
+        launches += 1;
     }
     store_lower_kernel<<<(unsigned)n, 256, 0, stream>>>(n, Xc, dA, lda, p.ctrl);
     launches += 1;
@@ -447,3 +463,42 @@ spdinv_status run_mixed(int64_t n, double* dA, int64_t lda, const spdinv_opts* o
 }
 
 }  // namespace spdinv
+
+using namespace spdinv;
+
+extern "C" SPDINV_API spdinv_status spdinv_inverse_residual(int64_t n, const double* dA, int64_t lda, const double* dX,
+                                                            double* dR, int residual, cudaStream_t stream) {
+    if (n < 0) return SPDINV_ERR_N;
+    if (lda < (n > 1 ? n : 1)) return SPDINV_ERR_LDA;
+    if (n == 0) return SPDINV_OK;
+    if (!dA || !dX || !dR) return SPDINV_ERR_NULL;
+    if (residual != SPDINV_RESIDUAL_EMULATED && residual != SPDINV_RESIDUAL_FP64) return SPDINV_ERR_UNSUPPORTED;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e);
+    DeviceState& ds = device_state(dev);
+    std::lock_guard<std::mutex> lk(ds.mu);
+    // status words (zero: no abort) + the slices
+    const size_t need = 256 + (residual == SPDINV_RESIDUAL_EMULATED ? ozaki_workspace_bytes(n, 7) : 0);
+    e = ds.ensure_workspace(need);
+    if (e != cudaSuccess) return cuda_fail(e);
+    int* ctrl = static_cast<int*>(ds.ws);
+    e = cudaMemsetAsync(ctrl, 0, 256, stream);
+    if (e != cudaSuccess) return cuda_fail(e);
+    int launches = 0;
+    if (residual == SPDINV_RESIDUAL_EMULATED) {
+        e = ozaki_residual(n, dA, lda, dX, dR, static_cast<char*>(ds.ws) + 256, 7, 6, stream, &launches);
+    } else {
+        const int rt = (int)((n + RB - 1) / RB);
+        const int rsm = 2 * RB * RB * (int)sizeof(double);
+        e = cudaFuncSetAttribute(residual_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, rsm);
+        if (e == cudaSuccess) {
+            residual_kernel<<<(unsigned)((int64_t)rt * rt), kThreads, rsm, stream>>>(n, dA, lda, dX, dR, ctrl);
+            launches = 1;
+            e = cudaGetLastError();
+        }
+    }
+    if (e != cudaSuccess) return cuda_fail(e);
+    count_launches(launches);
+    return SPDINV_OK;
+}

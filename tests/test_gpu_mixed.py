@@ -96,3 +96,58 @@ def test_mixed_full_size_sampled(gpu):
         assert err <= 1e-10
         del A, W, Lo
         torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("n", [1, 31, 127, 128, 129, 300, 1030])
+@pytest.mark.parametrize("residual", [0, 1])
+def test_inverse_residual_vs_fp64(gpu, n, residual):
+    """R = I - A X against the FP64 CPU product, for an X near A^{-1} (the
+    case the correction meets): |R - R_ref| <= 1e-13 |A| |X| elementwise-max."""
+    import torch
+    from paper_1002_4057_gb300 import _lib as L
+    A, _, _ = si.spectral_spd(n, 1e3, seed=900 + n)
+    X = np.linalg.inv(A).astype(np.float32).astype(np.float64)  # an FP32-accurate inverse
+    X = 0.5 * (X + X.T)
+    Rref = np.eye(n) - A @ X
+    dA = to_dev(A, gpu)
+    dX = torch.from_numpy(np.asfortranarray(X)).to(gpu)
+    dR = torch.zeros((n, n), dtype=torch.float64, device=gpu).t()
+    st = L.spdinv_inverse_residual(n, dA.data_ptr(), n, dX.data_ptr(), dR.data_ptr(), residual,
+                                   torch.cuda.current_stream().cuda_stream)
+    assert st == 0
+    torch.cuda.synchronize()
+    R = dR.cpu().numpy()
+    scale = np.max(np.abs(A) @ np.abs(X))
+    assert np.max(np.abs(R - Rref)) <= 1e-13 * scale, np.max(np.abs(R - Rref)) / scale
+
+
+def test_inverse_residual_exact_integer_case(gpu):
+    """Integer A and its exact integer inverse: R must be exactly zero."""
+    import torch
+    from paper_1002_4057_gb300 import _lib as L
+    n = 500
+    A, s = si.bidiag_integer_spd(n, seed=5)
+    X = cf.bidiag_inverse(s)
+    dA = to_dev(A, gpu)
+    dX = torch.from_numpy(np.asfortranarray(X)).to(gpu)
+    dR = torch.full((n, n), 7.0, dtype=torch.float64, device=gpu).t()
+    assert L.spdinv_inverse_residual(n, dA.data_ptr(), n, dX.data_ptr(), dR.data_ptr(), 0,
+                                     torch.cuda.current_stream().cuda_stream) == 0
+    torch.cuda.synchronize()
+    assert np.array_equal(dR.cpu().numpy(), np.zeros((n, n)))
+
+
+@pytest.mark.parametrize("n", [200, 700])
+def test_mixed_emulated_matches_native_residual(gpu, n):
+    from paper_1002_4057_gb300 import torch_api as T
+    A, _, _ = si.spectral_spd(n, 1e4, seed=1200 + n)
+    M, _ = oracle.potri(A)
+    ref = oracle.symmetrize_lower(M)
+    errs = {}
+    for residual in (0, 1):
+        dA = to_dev(A, gpu)
+        info = T.potri_(dA, precision=MIXED, refine_steps=2, tile=64, residual=residual)
+        assert int(info.item()) == 0
+        errs[residual] = oracle.rel_frobenius(full_from_lower(lower_np(dA)), ref)
+    print("n=%d errors emulated %.2e native %.2e" % (n, errs[0], errs[1]))
+    assert errs[0] <= 1e-10 and errs[1] <= 1e-10
