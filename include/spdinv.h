@@ -92,12 +92,15 @@ typedef struct {
                             below 0) = off.  Only honoured when wait_timeout_s > 0. */
     int residual;        /* mixed precision: how R = I - A X is formed.
                             SPDINV_RESIDUAL_EMULATED (0, default): FP64-accurate products of
-                            exact 8-bit slices on the BF16 tensor cores;
-                            SPDINV_RESIDUAL_FP64 (1): native FP64 tensor-core products. */
+                            exact 8-bit slices on the BF16 tensor cores (tcgen05, TMA);
+                            SPDINV_RESIDUAL_FP64 (1): native FP64 tensor-core products;
+                            SPDINV_RESIDUAL_EMULATED_MMA_SYNC (2): the slice products on the
+                            warp-level mma.sync tensor-core path (for comparison). */
 } spdinv_opts;
 
 #define SPDINV_RESIDUAL_EMULATED 0
 #define SPDINV_RESIDUAL_FP64 1
+#define SPDINV_RESIDUAL_EMULATED_MMA_SYNC 2
 
 /* ------------------------------------------------------------------------
  * The three steps, separately (LAPACK lower-triangle semantics)
@@ -146,7 +149,8 @@ SPDINV_API spdinv_status spdinv_potri_ex(int64_t n, double* dA, int64_t lda, con
  * lower triangle of dA (column-major, lda), X full n x n (leading dimension n)
  * and R full n x n (leading dimension n).  residual = SPDINV_RESIDUAL_EMULATED
  * forms the products from exact 8-bit slices on the BF16 tensor cores
- * (error about 1e-15 |A||X|); SPDINV_RESIDUAL_FP64 uses native FP64 MMA.
+ * (error about 1e-15 |A||X|; SPDINV_RESIDUAL_EMULATED_MMA_SYNC the same on the
+ * warp-level MMA); SPDINV_RESIDUAL_FP64 uses native FP64 MMA.
  * Uses the library workspace (may allocate on first use). */
 SPDINV_API spdinv_status spdinv_inverse_residual(int64_t n, const double* dA, int64_t lda, const double* dX,
                                                  double* dR, int residual, cudaStream_t stream);

@@ -33,6 +33,7 @@ SPDINV_NOALLOC_MAX_N = 1024
 
 SPDINV_RESIDUAL_EMULATED = 0
 SPDINV_RESIDUAL_FP64 = 1
+SPDINV_RESIDUAL_EMULATED_MMA_SYNC = 2
 
 SPDINV_DAG_OUT_OF_PLACE = 1
 SPDINV_DAG_RENAME_DIAG = 2

@@ -10,9 +10,16 @@ namespace spdinv {
 size_t ozaki_workspace_bytes(int64_t n, int S);
 
 // R = I - A X (n x n, ld n), A symmetric given by its lower triangle (lda),
-// X full (ld n); S slices per operand, slice pairs with s + t <= L.
-// Queues its kernels on s and adds their number to *launches.
+// X full (ld n); S slices per operand, slice pairs with s + t <= L.  The slice
+// products run on tcgen05 (tc = true) or on mma.sync.  err: device int that
+// records a device-side timeout.  Queues its kernels on s and adds their
+// number to *launches.
 cudaError_t ozaki_residual(int64_t n, const double* A, int64_t lda, const double* X, double* R, void* ws, int S,
-                           int L, cudaStream_t s, int* launches);
+                           int L, bool tc, int* err, cudaStream_t s, int* launches);
+
+// The slice products with tcgen05 (residual_tc.cu).
+cudaError_t ozaki_products_tc(int64_t n, int64_t npad, const void* Asl, const void* Xsl, int S, const int* ps,
+                              const int* pt, int npairs, const int* e, const int* f, double* R, int* err,
+                              cudaStream_t s);
 
 }  // namespace spdinv

@@ -396,8 +396,8 @@ spdinv_status run_mixed(int64_t n, double* dA, int64_t lda, const spdinv_opts* o
     const size_t bytesBC = align(ntri * tileb), bytesD = align((size_t)t * tileb);
     const size_t nn = align((size_t)n * n * sizeof(double));
     const int steps = o->refine_steps;
-    const bool emulated = o->residual == SPDINV_RESIDUAL_EMULATED;
-    if (o->residual != SPDINV_RESIDUAL_EMULATED && o->residual != SPDINV_RESIDUAL_FP64) return SPDINV_ERR_UNSUPPORTED;
+    const bool emulated = o->residual == SPDINV_RESIDUAL_EMULATED || o->residual == SPDINV_RESIDUAL_EMULATED_MMA_SYNC;
+    if (!emulated && o->residual != SPDINV_RESIDUAL_FP64) return SPDINV_ERR_UNSUPPORTED;
     constexpr int kSlices = 7, kLevels = 6;
     const size_t oz = (steps > 0 && emulated) ? align(ozaki_workspace_bytes(n, kSlices)) : 0;
     const size_t total = ctrl_bytes + 2 * bytesBC + bytesD + nn * (steps > 0 ? 3 : 1) + oz;
@@ -440,7 +440,8 @@ spdinv_status run_mixed(int64_t n, double* dA, int64_t lda, const spdinv_opts* o
     for (int s = 0; s < steps; ++s) {
         double* Xn = (Xc == X0) ? X1 : X0;
         if (emulated) {
-            e = ozaki_residual(n, dA, lda, Xc, R, ozws, kSlices, kLevels, stream, &launches);
+            e = ozaki_residual(n, dA, lda, Xc, R, ozws, kSlices, kLevels, o->residual == SPDINV_RESIDUAL_EMULATED,
+                               p.ctrl + 2, stream, &launches);
             if (e != cudaSuccess) return cuda_fail(e);
         } else {
             residual_kernel<<<(unsigned)((int64_t)rt * rt), kThreads, rsm, stream>>>(n, dA, lda, Xc, R, p.ctrl);
@@ -472,22 +473,24 @@ extern "C" SPDINV_API spdinv_status spdinv_inverse_residual(int64_t n, const dou
     if (lda < (n > 1 ? n : 1)) return SPDINV_ERR_LDA;
     if (n == 0) return SPDINV_OK;
     if (!dA || !dX || !dR) return SPDINV_ERR_NULL;
-    if (residual != SPDINV_RESIDUAL_EMULATED && residual != SPDINV_RESIDUAL_FP64) return SPDINV_ERR_UNSUPPORTED;
+    const bool emulated = residual == SPDINV_RESIDUAL_EMULATED || residual == SPDINV_RESIDUAL_EMULATED_MMA_SYNC;
+    if (!emulated && residual != SPDINV_RESIDUAL_FP64) return SPDINV_ERR_UNSUPPORTED;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_fail(e);
     DeviceState& ds = device_state(dev);
     std::lock_guard<std::mutex> lk(ds.mu);
     // status words (zero: no abort) + the slices
-    const size_t need = 256 + (residual == SPDINV_RESIDUAL_EMULATED ? ozaki_workspace_bytes(n, 7) : 0);
+    const size_t need = 256 + (emulated ? ozaki_workspace_bytes(n, 7) : 0);
     e = ds.ensure_workspace(need);
     if (e != cudaSuccess) return cuda_fail(e);
     int* ctrl = static_cast<int*>(ds.ws);
     e = cudaMemsetAsync(ctrl, 0, 256, stream);
     if (e != cudaSuccess) return cuda_fail(e);
     int launches = 0;
-    if (residual == SPDINV_RESIDUAL_EMULATED) {
-        e = ozaki_residual(n, dA, lda, dX, dR, static_cast<char*>(ds.ws) + 256, 7, 6, stream, &launches);
+    if (emulated) {
+        e = ozaki_residual(n, dA, lda, dX, dR, static_cast<char*>(ds.ws) + 256, 7, 6,
+                           residual == SPDINV_RESIDUAL_EMULATED, ctrl + 2, stream, &launches);
     } else {
         const int rt = (int)((n + RB - 1) / RB);
         const int rsm = 2 * RB * RB * (int)sizeof(double);

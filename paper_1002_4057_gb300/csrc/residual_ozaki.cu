@@ -317,14 +317,14 @@ __global__ void __launch_bounds__(THREADS, 1) ozaki_residual_kernel(const OzPara
 }  // namespace
 
 size_t ozaki_workspace_bytes(int64_t n, int S) {
-    const int64_t npad = (n + BM - 1) / BM * BM;
+    const int64_t npad = (n + 255) / 256 * 256;
     const size_t slices = 2 * (size_t)S * npad * npad * sizeof(__nv_bfloat16);
     return slices + 2 * (size_t)npad * sizeof(int) + 2 * (size_t)npad * sizeof(unsigned long long) + 1024;
 }
 
 cudaError_t ozaki_residual(int64_t n, const double* A, int64_t lda, const double* X, double* R, void* ws, int S,
-                           int L, cudaStream_t s, int* launches) {
-    const int64_t npad = (n + BM - 1) / BM * BM;
+                           int L, bool tc, int* errw, cudaStream_t s, int* launches) {
+    const int64_t npad = (n + 255) / 256 * 256;  // whole 256-deep chunks and 128-wide tiles
     char* w = static_cast<char*>(ws);
     __nv_bfloat16* Asl = reinterpret_cast<__nv_bfloat16*>(w);
     __nv_bfloat16* Xsl = Asl + (size_t)S * npad * npad;
@@ -363,6 +363,11 @@ cudaError_t ozaki_residual(int64_t n, const double* A, int64_t lda, const double
             }
         }
     p.npairs = np;
+    if (tc) {
+        err = ozaki_products_tc(n, npad, Asl, Xsl, S, p.ps, p.pt, np, e, f, R, errw, s);
+        if (launches) *launches += 7;
+        return err;
+    }
     const int sm = STAGES * (BM + BN) * LDS * (int)sizeof(__nv_bfloat16);
     err = cudaFuncSetAttribute(ozaki_residual_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     if (err != cudaSuccess) return err;

@@ -99,7 +99,7 @@ def test_mixed_full_size_sampled(gpu):
 
 
 @pytest.mark.parametrize("n", [1, 31, 127, 128, 129, 300, 1030])
-@pytest.mark.parametrize("residual", [0, 1])
+@pytest.mark.parametrize("residual", [0, 1, 2])
 def test_inverse_residual_vs_fp64(gpu, n, residual):
     """R = I - A X against the FP64 CPU product, for an X near A^{-1} (the
     case the correction meets): |R - R_ref| <= 1e-13 |A| |X| elementwise-max."""
@@ -121,7 +121,8 @@ def test_inverse_residual_vs_fp64(gpu, n, residual):
     assert np.max(np.abs(R - Rref)) <= 1e-13 * scale, np.max(np.abs(R - Rref)) / scale
 
 
-def test_inverse_residual_exact_integer_case(gpu):
+@pytest.mark.parametrize("residual", [0, 2])
+def test_inverse_residual_exact_integer_case(gpu, residual):
     """Integer A and its exact integer inverse: R must be exactly zero."""
     import torch
     from paper_1002_4057_gb300 import _lib as L
@@ -131,7 +132,7 @@ def test_inverse_residual_exact_integer_case(gpu):
     dA = to_dev(A, gpu)
     dX = torch.from_numpy(np.asfortranarray(X)).to(gpu)
     dR = torch.full((n, n), 7.0, dtype=torch.float64, device=gpu).t()
-    assert L.spdinv_inverse_residual(n, dA.data_ptr(), n, dX.data_ptr(), dR.data_ptr(), 0,
+    assert L.spdinv_inverse_residual(n, dA.data_ptr(), n, dX.data_ptr(), dR.data_ptr(), residual,
                                      torch.cuda.current_stream().cuda_stream) == 0
     torch.cuda.synchronize()
     assert np.array_equal(dR.cpu().numpy(), np.zeros((n, n)))
@@ -144,10 +145,10 @@ def test_mixed_emulated_matches_native_residual(gpu, n):
     M, _ = oracle.potri(A)
     ref = oracle.symmetrize_lower(M)
     errs = {}
-    for residual in (0, 1):
+    for residual in (0, 1, 2):
         dA = to_dev(A, gpu)
         info = T.potri_(dA, precision=MIXED, refine_steps=2, tile=64, residual=residual)
         assert int(info.item()) == 0
         errs[residual] = oracle.rel_frobenius(full_from_lower(lower_np(dA)), ref)
-    print("n=%d errors emulated %.2e native %.2e" % (n, errs[0], errs[1]))
-    assert errs[0] <= 1e-10 and errs[1] <= 1e-10
+    print("n=%d errors emulated(tcgen05) %.2e native %.2e emulated(mma.sync) %.2e" % (n, errs[0], errs[1], errs[2]))
+    assert errs[0] <= 1e-10 and errs[1] <= 1e-10 and errs[2] <= 1e-10
