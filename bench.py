@@ -46,7 +46,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="fp64",
-                    choices=["fp64", "batched64", "batched32", "backward64", "backward32", "mixed"],
+                    choices=["fp64", "batched64", "batched32", "backward64", "backward32", "mixed", "residual"],
                     help="fp64 (default, the headline line): one n x n FP64 inversion per step; "
                          "batched*: 4096 matrices n ~ U{16..256} per step, one graph-captured launch; "
                          "backward*: forward + backward of 256 matrices n = 512")
@@ -240,6 +240,30 @@ def run_mixed_study(args, dev, stream):
     print(json.dumps({"workload": "mixed", "metric": METRIC, "n": n, "summary": best}), flush=True)
 
 
+def run_residual(args, dev, stream):
+    """R = I - A X through spdinv_inverse_residual at order n: the emulated
+    FP64 product on tcgen05, the same on mma.sync, and native FP64; the
+    FP64-equivalent rate counts 2 n^3 per residual."""
+    import numpy as np
+    import torch
+
+    import spd_inputs as si
+    from paper_1002_4057_gb300 import _lib as L
+
+    n = args.n
+    A, _, _ = si.spectral_spd(n, 1e4, seed=si.SEED_BASE + 2, device=dev)
+    X = torch.linalg.inv(A.t().contiguous()).t().contiguous()  # input only (an approximate inverse)
+    R = torch.empty((n, n), dtype=torch.float64, device=dev)
+    out = {"workload": "residual", "n": n, "flops": 2.0 * n ** 3}
+    for name, mode in (("emulated_tcgen05", 0), ("emulated_mma_sync", 2), ("native_fp64", 1)):
+        def call():
+            st = L.spdinv_inverse_residual(n, A.data_ptr(), n, X.data_ptr(), R.data_ptr(), mode, stream.cuda_stream)
+            assert st == 0
+        ms = timed_steps(call, args.steps, args.warmup, stream)
+        out[name] = {"ms": round(ms, 2), "fp64_equiv_tflops": round(2.0 * n ** 3 / (ms * 1e-3) / 1e12, 2)}
+    print(json.dumps(out), flush=True)
+
+
 def run_secondary(args):
     """Measurement lines for the batched and backward workloads (not the
     headline line): Gflop/s with sum(n^3) per batch, or 3 n^3 per matrix for
@@ -256,6 +280,9 @@ def run_secondary(args):
     clk = ClockSampler(0)
     if args.workload == "mixed":
         run_mixed_study(args, dev, stream)
+        return
+    if args.workload == "residual":
+        run_residual(args, dev, stream)
         return
     if args.workload.startswith("batched"):
         dtype = torch.float64 if args.workload == "batched64" else torch.float32

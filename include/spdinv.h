@@ -148,8 +148,10 @@ SPDINV_API spdinv_status spdinv_potri_ex(int64_t n, double* dA, int64_t lda, con
  * correction; the paper has none): R = I - A X with A symmetric, given by the
  * lower triangle of dA (column-major, lda), X full n x n (leading dimension n)
  * and R full n x n (leading dimension n).  residual = SPDINV_RESIDUAL_EMULATED
- * forms the products from exact 8-bit slices on the BF16 tensor cores
- * (error about 1e-15 |A||X|; SPDINV_RESIDUAL_EMULATED_MMA_SYNC the same on the
+ * forms the products from 7 exact 8-bit slices of each operand on the BF16
+ * tensor cores, keeping the 34 slice products whose levels s + t are <= 7
+ * (error about 1e-16 |A||X|, like the native residual;
+ * SPDINV_RESIDUAL_EMULATED_MMA_SYNC the same on the
  * warp-level MMA); SPDINV_RESIDUAL_FP64 uses native FP64 MMA.
  * Uses the library workspace (may allocate on first use). */
 SPDINV_API spdinv_status spdinv_inverse_residual(int64_t n, const double* dA, int64_t lda, const double* dX,

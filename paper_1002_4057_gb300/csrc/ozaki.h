@@ -19,7 +19,12 @@ cudaError_t ozaki_residual(int64_t n, const double* A, int64_t lda, const double
 
 // The slice products with tcgen05 (residual_tc.cu).
 cudaError_t ozaki_products_tc(int64_t n, int64_t npad, const void* Asl, const void* Xsl, int S, const int* ps,
-                              const int* pt, int npairs, const int* e, const int* f, double* R, int* err,
-                              cudaStream_t s);
+                              const int* pt, int npairs, const int* e, const int* f, double* R, const double* base,
+                              double sign, int* err, cudaStream_t s);
+
+// Xn = X + X R on the tensor cores (X symmetric, stored full; R full; all ld
+// n): the same exact-slice products with S slices and pairs s + t <= L.
+cudaError_t ozaki_correction(int64_t n, const double* X, const double* R, double* Xn, void* ws, int S, int L,
+                             int* err, cudaStream_t s, int* launches);
 
 }  // namespace spdinv

@@ -398,7 +398,11 @@ spdinv_status run_mixed(int64_t n, double* dA, int64_t lda, const spdinv_opts* o
     const int steps = o->refine_steps;
     const bool emulated = o->residual == SPDINV_RESIDUAL_EMULATED || o->residual == SPDINV_RESIDUAL_EMULATED_MMA_SYNC;
     if (!emulated && o->residual != SPDINV_RESIDUAL_FP64) return SPDINV_ERR_UNSUPPORTED;
-    constexpr int kSlices = 7, kLevels = 6;
+    // 7 slices of 8 bits cover the 53-bit significands.  Products of slice
+    // levels s + t <= 6 (28 pairs) leave an error small enough for every step
+    // but the last, whose residual error stays in the result: it keeps the
+    // levels up to 7 (34 pairs), which matches the native FP64 residual.
+    constexpr int kSlices = 7, kLevels = 6, kLevelsLast = 7;
     const size_t oz = (steps > 0 && emulated) ? align(ozaki_workspace_bytes(n, kSlices)) : 0;
     const size_t total = ctrl_bytes + 2 * bytesBC + bytesD + nn * (steps > 0 ? 3 : 1) + oz;
     e = ds.ensure_workspace(total);
@@ -440,14 +444,20 @@ spdinv_status run_mixed(int64_t n, double* dA, int64_t lda, const spdinv_opts* o
     for (int s = 0; s < steps; ++s) {
         double* Xn = (Xc == X0) ? X1 : X0;
         if (emulated) {
-            e = ozaki_residual(n, dA, lda, Xc, R, ozws, kSlices, kLevels, o->residual == SPDINV_RESIDUAL_EMULATED,
-                               p.ctrl + 2, stream, &launches);
+            e = ozaki_residual(n, dA, lda, Xc, R, ozws, kSlices, s == steps - 1 ? kLevelsLast : kLevels,
+                               o->residual == SPDINV_RESIDUAL_EMULATED, p.ctrl + 2, stream, &launches);
             if (e != cudaSuccess) return cuda_fail(e);
         } else {
             residual_kernel<<<(unsigned)((int64_t)rt * rt), kThreads, rsm, stream>>>(n, dA, lda, Xc, R, p.ctrl);
             launches += 1;
         }
-        correct_kernel<<<(unsigned)((int64_t)rt * rt), kThreads, csm, stream>>>(n, Xc, R, Xn, p.ctrl);
+        if (o->residual == SPDINV_RESIDUAL_EMULATED) {  // X + X R from 5 exact slices (beyond FP32 accuracy)
+            e = ozaki_correction(n, Xc, R, Xn, ozws, 5, 4, p.ctrl + 2, stream, &launches);
+            if (e != cudaSuccess) return cuda_fail(e);
+            launches -= 1;
+        } else {
+            correct_kernel<<<(unsigned)((int64_t)rt * rt), kThreads, csm, stream>>>(n, Xc, R, Xn, p.ctrl);
+        }
         Xc = Xn;
         launches += 1;
     }
@@ -489,7 +499,7 @@ extern "C" SPDINV_API spdinv_status spdinv_inverse_residual(int64_t n, const dou
     if (e != cudaSuccess) return cuda_fail(e);
     int launches = 0;
     if (emulated) {
-        e = ozaki_residual(n, dA, lda, dX, dR, static_cast<char*>(ds.ws) + 256, 7, 6,
+        e = ozaki_residual(n, dA, lda, dX, dR, static_cast<char*>(ds.ws) + 256, 7, 7,
                            residual == SPDINV_RESIDUAL_EMULATED, ctrl + 2, stream, &launches);
     } else {
         const int rt = (int)((n + RB - 1) / RB);

@@ -364,7 +364,7 @@ cudaError_t ozaki_residual(int64_t n, const double* A, int64_t lda, const double
         }
     p.npairs = np;
     if (tc) {
-        err = ozaki_products_tc(n, npad, Asl, Xsl, S, p.ps, p.pt, np, e, f, R, errw, s);
+        err = ozaki_products_tc(n, npad, Asl, Xsl, S, p.ps, p.pt, np, e, f, R, nullptr, -1.0, errw, s);
         if (launches) *launches += 7;
         return err;
     }
@@ -374,6 +374,41 @@ cudaError_t ozaki_residual(int64_t n, const double* A, int64_t lda, const double
     ozaki_residual_kernel<<<dim3((unsigned)(npad / BN), (unsigned)(npad / BM)), THREADS, sm, s>>>(p);
     if (launches) *launches += 7;
     return cudaGetLastError();
+}
+
+}  // namespace spdinv
+
+namespace spdinv {
+
+cudaError_t ozaki_correction(int64_t n, const double* X, const double* R, double* Xn, void* ws, int S, int L,
+                             int* errw, cudaStream_t s, int* launches) {
+    const int64_t npad = (n + 255) / 256 * 256;
+    char* w = static_cast<char*>(ws);
+    __nv_bfloat16* Xsl = reinterpret_cast<__nv_bfloat16*>(w);  // A operand: X (symmetric: its columns are its rows)
+    __nv_bfloat16* Rsl = Xsl + (size_t)S * npad * npad;          // B operand: R, K-major per column
+    unsigned long long* xmax = reinterpret_cast<unsigned long long*>(Rsl + (size_t)S * npad * npad);
+    unsigned long long* rmax = xmax + npad;
+    int* e = reinterpret_cast<int*>(rmax + npad);
+    int* f = e + npad;
+    cudaError_t err = cudaMemsetAsync(Xsl, 0, 2 * (size_t)S * npad * npad * sizeof(__nv_bfloat16), s);
+    if (err != cudaSuccess) return err;
+    col_absmax_kernel<<<(unsigned)n, 256, 0, s>>>(n, X, xmax);
+    col_absmax_kernel<<<(unsigned)n, 256, 0, s>>>(n, R, rmax);
+    exponents_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, xmax, e);
+    exponents_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, rmax, f);
+    slice_X_kernel<<<(unsigned)n, 256, 0, s>>>(n, npad, X, e, S, Xsl);
+    slice_X_kernel<<<(unsigned)n, 256, 0, s>>>(n, npad, R, f, S, Rsl);
+    int ps[64], pt[64], np = 0;
+    for (int lv = 0; lv <= L; ++lv)
+        for (int a = 0; a <= lv; ++a)
+            if (a < S && lv - a < S && np < 64) {
+                ps[np] = a;
+                pt[np] = lv - a;
+                ++np;
+            }
+    err = ozaki_products_tc(n, npad, Xsl, Rsl, S, ps, pt, np, e, f, Xn, X, 1.0, errw, s);
+    if (launches) *launches += 8;
+    return err;
 }
 
 }  // namespace spdinv

@@ -2,17 +2,22 @@
 // fifth-generation tensor cores: tcgen05.mma (BF16 in, FP32 accumulator in
 // tensor memory), operands staged by TMA with 128-byte swizzle.
 //
-// One CTA computes a 128 x 128 tile of R = I - A X over all slice pairs:
+// One CTA computes a 128 x 128 tile of R = I - A X (or, for the correction
+// step, X + X R) over all slice pairs:
 //   warp 0    TMA producer: 64-deep K slices of A's and X's slice planes into
-//             a 4-stage shared-memory ring;
-//   warp 1    allocates 256 tensor-memory columns (two 128-column FP32
-//             accumulators) and issues the MMAs from one thread: 4 stages =
-//             one exact 256-deep chunk per accumulator, then a commit;
+//             a 6-stage shared-memory ring;
+//   warp 1    allocates all 512 tensor-memory columns and issues the MMAs
+//             from one thread into two 128-column FP32 accumulators: 4 stages
+//             = one exact 256-deep chunk per accumulator, then a commit;
 //   warps 2-9 epilogue: each thread owns half of one accumulator row (its
-//             warp's lane quarter, 64 columns), reads a finished chunk with
-//             tcgen05.ld, adds the exact FP32 integers into INT32 registers,
-//             releases the accumulator, and at the end of a slice pair adds
-//             -2^{e_i + f_j - 8(s+t+2)} * sum into R (FP64, global).
+//             warp's lane quarter, 64 columns).  Per chunk it reads the
+//             accumulator with tcgen05.ld, adds the exact FP32 integers into
+//             INT32 registers and releases the accumulator; per slice pair it
+//             adds those into INT64 level sums kept in tensor memory (columns
+//             256-511, lo/hi pairs); per level s + t -- all its pairs share
+//             the scale 2^{e_i + f_j - 8(s+t+2)} -- it adds the level once into
+//             R (FP64, global).  FP64 work, slow on this chip, thus happens 7
+//             times per tile instead of once per chunk or pair.
 // Every wait is bounded; on a timeout the CTA records an error, all roles
 // leave their loops, and the tensor memory is freed before exit.
 #include <cuda.h>
@@ -30,12 +35,13 @@ namespace spdinv {
 namespace {
 
 constexpr int TM = 128, TN = 128, TK = 64;  // output tile; K per stage = one 128-byte swizzle row of bf16
-constexpr int NSTAGE = 4;
+constexpr int NSTAGE = 6;  // 1.5 exact chunks in flight: the copies run ahead of the MMAs
 constexpr int A_BYTES = TM * TK * 2, B_BYTES = TN * TK * 2, STAGE_BYTES = A_BYTES + B_BYTES;
 constexpr int CHUNK_STAGES = 256 / TK;  // exact FP32 chunk: 256 products of 8-bit slices
-constexpr int FLUSH_CHUNKS = 128;       // INT32 headroom: 128 chunks x 256 x 255^2 < 2^31
-constexpr int TMEM_COLS = 256;          // two 128-column FP32 accumulators
+constexpr int TMEM_COLS = 512;          // two 128-column FP32 accumulators + INT64 level sums (256 columns)
+constexpr int LVL_COL = 256;            // first tensor-memory column of the INT64 level sums
 constexpr int NTHREADS = 320;          // warp 0 TMA, warp 1 MMA, warps 2-9 epilogue
+constexpr int EPI_WARPS = 8;
 constexpr int EPI_COLS = TN / 2;        // columns per epilogue thread (two warps per lane quarter)
 constexpr uint32_t IDESC = (1u << 4)                        // D: FP32
                            | (1u << 7) | (1u << 10)          // A, B: BF16
@@ -45,6 +51,9 @@ constexpr uint32_t IDESC = (1u << 4)                        // D: FP32
 struct TcParams {
     int64_t n, npad;
     int npairs;
+    int tiles;            // tiles per side
+    const double* base;   // output = base + sign * A X   (base == nullptr: the identity)
+    double sign;
     int ps[64], pt[64];
     const int* e;
     const int* f;
@@ -79,6 +88,9 @@ __device__ __forceinline__ void umma_commit(uint64_t* bar) {
                  : "memory");
 }
 
+// 2^x as a double, exactly, for |x| < 1022.
+__device__ __forceinline__ double pow2(int x) { return __longlong_as_double((long long)(x + 1023) << 52); }
+
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
@@ -93,6 +105,38 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
         : "r"(taddr)
         : "memory");
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
+        "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(taddr),
+        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]),
+        "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]), "r"(r[16]),
+        "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]), "r"(r[24]),
+        "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31])
+        : "memory");
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
+            taddr),
+        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]),
+        "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+        : "memory");
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
 
 // Bounded wait that ignores the abort flag (used while draining in-flight work).
@@ -126,7 +170,19 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     __shared__ volatile int s_abort;
     __shared__ int s_f[TN];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t m0 = (int64_t)blockIdx.y * TM, n0 = (int64_t)blockIdx.x * TN;
+    // Grouped raster: consecutive CTAs sweep GROUP_M row tiles before moving
+    // to the next column tile, so the CTAs resident at one time share both
+    // operands' slices in L2.
+    constexpr int GROUP_M = 16;
+    int tile_m, tile_n;
+    {
+        const int pid = blockIdx.x, per_group = GROUP_M * p.tiles;
+        const int first = (pid / per_group) * GROUP_M;
+        const int gm = min(p.tiles - first, GROUP_M);
+        tile_m = first + (pid % per_group) % gm;
+        tile_n = (pid % per_group) / gm;
+    }
+    const int64_t m0 = (int64_t)tile_m * TM, n0 = (int64_t)tile_n * TN;
     const int kstages = (int)(p.npad / TK);            // stages per slice pair
     const int chunks_per_pair = kstages / CHUNK_STAGES;
     const int total_stages = p.npairs * kstages;
@@ -139,7 +195,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&accf[b], 1);
-            mbar_init(&acce[b], 8);  // one arrival per epilogue warp
+            mbar_init(&acce[b], EPI_WARPS);  // one arrival per epilogue warp
         }
         mbar_init(&fin, 1);
         s_abort = 0;
@@ -202,51 +258,77 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             umma_commit(&fin);  // every MMA issued above has completed when this arrives
             drain_bar(&fin, 0, 2000000000LL);
         }
-    } else {  // ---- epilogue: warps 2..9, half an accumulator row per thread
+    } else {  // ---- epilogue: warps 2..17, a quarter of an accumulator row per thread
         const int quarter = warp & 3;
-        const int half = (warp - 2) >> 2;
+        const int half = (warp - 2) >> 2;  // which 32-column part of the row
         const int row = quarter * 32 + lane;
         const int64_t i = m0 + row;
         const int ei = (i < p.n) ? p.e[i] : 0;
+        const uint32_t trow = tmem + ((uint32_t)(quarter * 32) << 16);
+        const uint32_t tlvl = trow + (uint32_t)(LVL_COL + half * 2 * EPI_COLS);  // this thread's INT64 sums
         int acc[EPI_COLS];
 #pragma unroll
         for (int j = 0; j < EPI_COLS; ++j) acc[j] = 0;
-        bool first_flush = true;
+        bool first_flush = true, level_start = true;
         int pair = 0, cin = 0;  // chunk index within the pair
         for (int c = 0; c < total_chunks; ++c) {
             const int b = c & 1;
             if (!wait_bar(&accf[b], (c >> 1) & 1, &s_abort, p)) break;
             tc_fence_after();
 #pragma unroll
-            for (int cb = 0; cb < EPI_COLS / 32; ++cb) {
-                uint32_t r[32];
-                tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * TN + half * EPI_COLS + cb * 32), r);
+            for (int cb = 0; cb < EPI_COLS / 16; ++cb) {
+                uint32_t r[16];
+                tmem_ld16(trow + (uint32_t)(b * TN + half * EPI_COLS + cb * 16), r);
 #pragma unroll
-                for (int u = 0; u < 32; ++u) acc[cb * 32 + u] += __float2int_rn(__uint_as_float(r[u]));
+                for (int u = 0; u < 16; ++u) acc[cb * 16 + u] += __float2int_rn(__uint_as_float(r[u]));
             }
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&acce[b]);
-            ++cin;
-            const bool pair_end = cin == chunks_per_pair;
-            if (pair_end || (cin % FLUSH_CHUNKS) == 0) {
-                const int lvl = 8 * (p.ps[pair] + p.pt[pair] + 2);
+            if (++cin < chunks_per_pair) continue;
+            // ---- end of a slice pair: INT32 pair sums into the INT64 level sums
+            cin = 0;
+            const int lv = p.ps[pair] + p.pt[pair];
+            ++pair;
+            const bool level_end = !(pair < p.npairs && p.ps[pair] + p.pt[pair] == lv);
 #pragma unroll
-                for (int j = 0; j < EPI_COLS; ++j) {
-                    const int64_t jj = n0 + half * EPI_COLS + j;
-                    if (i < p.n && jj < p.n) {
-                        double* dst = &p.R[i + jj * p.n];
-                        const double v = scalbn((double)acc[j], ei + s_f[half * EPI_COLS + j] - lvl);
-                        *dst = (first_flush ? (i == jj ? 1.0 : 0.0) : *dst) - v;
-                    }
-                    acc[j] = 0;
+            for (int g = 0; g < EPI_COLS / 8; ++g) {  // 8 INT64 values = 16 columns per step
+                uint32_t r[16];
+                if (!level_start) tmem_ld16(tlvl + (uint32_t)(g * 16), r);
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    long long v = level_start ? 0ll
+                                              : (long long)(((unsigned long long)r[2 * u + 1] << 32) | r[2 * u]);
+                    v += (long long)acc[g * 8 + u];
+                    acc[g * 8 + u] = 0;
+                    r[2 * u] = (uint32_t)(unsigned long long)v;
+                    r[2 * u + 1] = (uint32_t)((unsigned long long)v >> 32);
                 }
-                first_flush = false;
+                tmem_st16(tlvl + (uint32_t)(g * 16), r);
             }
-            if (pair_end) {
-                ++pair;
-                cin = 0;
+            level_start = level_end;
+            if (!level_end) continue;
+            // ---- end of a level: R -= 2^{e_i + f_j - 8(lv+2)} * sum (exact scale, one FMA per entry)
+            const double ri = pow2(ei - 8 * (lv + 2));
+#pragma unroll 1
+            for (int g = 0; g < EPI_COLS / 16; ++g) {
+                uint32_t r[32];
+                tmem_ld32(tlvl + (uint32_t)(g * 32), r);
+                if (i >= p.n) continue;
+#pragma unroll
+                for (int u = 0; u < 16; ++u) {
+                    const long long v = (long long)(((unsigned long long)r[2 * u + 1] << 32) | r[2 * u]);
+                    const int j = half * EPI_COLS + g * 16 + u;
+                    const int64_t jj = n0 + j;
+                    if (jj < p.n) {
+                        double* dst = &p.R[i + jj * p.n];
+                        const double base =
+                            first_flush ? (p.base ? p.base[i + jj * p.n] : (i == jj ? 1.0 : 0.0)) : *dst;
+                        *dst = fma(p.sign * (double)v, ri * pow2(s_f[j]), base);
+                    }
+                }
             }
+            first_flush = false;
         }
     }
     tc_fence_before();
@@ -286,8 +368,8 @@ bool make_map(CUtensorMap* m, const void* base, int64_t npad, int S) {
 }  // namespace
 
 cudaError_t ozaki_products_tc(int64_t n, int64_t npad, const void* Asl, const void* Xsl, int S, const int* ps,
-                              const int* pt, int npairs, const int* e, const int* f, double* R, int* err,
-                              cudaStream_t s) {
+                              const int* pt, int npairs, const int* e, const int* f, double* R, const double* base,
+                              double sign, int* err, cudaStream_t s) {
     if (npad % TM != 0 || npad % 256 != 0 || npairs > 64) return cudaErrorInvalidValue;
     CUtensorMap ma, mb;
     if (!make_map(&ma, Asl, npad, S) || !make_map(&mb, Xsl, npad, S)) return cudaErrorInvalidValue;
@@ -302,12 +384,15 @@ cudaError_t ozaki_products_tc(int64_t n, int64_t npad, const void* Asl, const vo
     p.e = e;
     p.f = f;
     p.R = R;
+    p.base = base;
+    p.sign = sign;
+    p.tiles = (int)(npad / TM);
     p.err = err;
     p.timeout_ns = 20LL * 1000000000LL;
     const int sm = NSTAGE * STAGE_BYTES;
     cudaError_t rc = cudaFuncSetAttribute(ozaki_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     if (rc != cudaSuccess) return rc;
-    ozaki_tc_kernel<<<dim3((unsigned)(npad / TN), (unsigned)(npad / TM)), NTHREADS, sm, s>>>(ma, mb, p);
+    ozaki_tc_kernel<<<(unsigned)(p.tiles * p.tiles), NTHREADS, sm, s>>>(ma, mb, p);
     return cudaGetLastError();
 }
 
