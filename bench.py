@@ -46,10 +46,12 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="fp64",
-                    choices=["fp64", "batched64", "batched32", "backward64", "backward32", "mixed", "residual"],
+                    choices=["fp64", "batched64", "batched32", "backward64", "backward32", "mixed", "residual",
+                             "variants"],
                     help="fp64 (default, the headline line): one n x n FP64 inversion per step; "
                          "batched*: 4096 matrices n ~ U{16..256} per step, one graph-captured launch; "
-                         "backward*: forward + backward of 256 matrices n = 512")
+                         "backward*: forward + backward of 256 matrices n = 512; "
+                         "variants: pipelined vs step-by-step (barriered) execution and the tile size")
     return ap.parse_args()
 
 
@@ -200,7 +202,7 @@ def run_mixed_study(args, dev, stream):
     cols = np.array([0, n // 3, n - 1])
     flops = float(n) ** 3
     out = []
-    for cond, kmax in ((1e2, 2), (1e4, 2), (1e6, 3)):
+    for cond, kmax in ((1e2, 2), (1e4, 2), (1e6, 4)):
         A, Q, lam = si.spectral_spd(n, cond, seed=si.SEED_BASE + 2, device=dev)
         ref = cf.spectral_inverse_columns(Q.cpu().numpy(), lam, cols)
         del Q
@@ -264,6 +266,49 @@ def run_residual(args, dev, stream):
     print(json.dumps(out), flush=True)
 
 
+def run_variants(args, dev, stream):
+    """The execution-variant study of Sec. 3 on the GPU, FP64: the three
+    steps pipelined in one persistent launch (spdinv_potri) against the same
+    steps run one after another (spdinv_potrf, spdinv_trtri, spdinv_lauum:
+    every step waits for the previous one to finish), for tiles 32 and 64 at
+    n = 4096, 8192 and 16384; and the selected inverse diag(A^{-1})
+    (spdinv_potri_diag: Step 3 on the diagonal tiles only)."""
+    import torch
+
+    import spd_inputs as si
+    from paper_1002_4057_gb300 import torch_api as T
+
+    sizes = (4096, 8192, 16384) if args.n == 16384 else (args.n,)
+    for n in sizes:
+        A, _, _ = si.spectral_spd(n, 1e4, seed=si.SEED_BASE + 1, device=dev)
+        W = torch.empty_like(A)
+        info = torch.zeros(1, dtype=torch.int32, device=dev)
+        flops = float(n) ** 3
+        rec = {"workload": "variants", "n": n}
+        for b in (32, 64):
+            def piped():
+                W.copy_(A)
+                T.potri_(W, info=info, tile=b)
+            ms = timed_steps(piped, args.steps, args.warmup, stream)
+            rec["pipelined_b%d" % b] = {"ms": round(ms, 2), "gflops": round(flops / (ms * 1e-3) / 1e9, 1)}
+        ms_copy = timed_steps(lambda: W.copy_(A), args.steps, args.warmup, stream)
+
+        def stepwise():
+            W.copy_(A)
+            T.potrf_(W, info=info)
+            T.trtri_(W, info=info)
+            T.lauum_(W)
+        ms = timed_steps(stepwise, args.steps, args.warmup, stream)
+        assert int(info.item()) == 0
+        rec["stepwise_default_tile"] = {"ms": round(ms, 2), "gflops": round(flops / (ms * 1e-3) / 1e9, 1)}
+        ms_d = timed_steps(lambda: T.inverse_diag(A, info=info), args.steps, args.warmup, stream)
+        rec["selected_inverse_diag_default_tile"] = {"ms": round(ms_d, 2)}
+        rec["restore_copy_ms"] = round(ms_copy, 2)
+        print(json.dumps(rec), flush=True)
+        del A, W
+        torch.cuda.empty_cache()
+
+
 def run_secondary(args):
     """Measurement lines for the batched and backward workloads (not the
     headline line): Gflop/s with sum(n^3) per batch, or 3 n^3 per matrix for
@@ -283,6 +328,9 @@ def run_secondary(args):
         return
     if args.workload == "residual":
         run_residual(args, dev, stream)
+        return
+    if args.workload == "variants":
+        run_variants(args, dev, stream)
         return
     if args.workload.startswith("batched"):
         dtype = torch.float64 if args.workload == "batched64" else torch.float32

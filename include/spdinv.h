@@ -135,14 +135,31 @@ SPDINV_API spdinv_status spdinv_potri(int64_t n, double* dA, int64_t lda, int* d
  * steps, wait limit).  opts may be NULL (= all defaults).
  * Mixed precision (opts->precision == SPDINV_PREC_MIXED_FP32, tile 32 or 64):
  * the tile DAG runs with FP32 bulk updates and FP64 diagonal POTRF/TRTRI,
- * then refine_steps times R = I - A X (FP64; A read from its lower triangle,
- * intact until the end) and X <- X + X R (product in FP32, sum in FP64); the
- * lower triangle of A then holds X in FP64.  Accuracy after k steps is about
- * e^(2^k) for the FP32 result's error e (plus the FP32 rounding of X R), so
- * the step count needed for a target grows with cond(A).  The workspace
- * holds three n x n FP64 matrices when refine_steps > 0. */
+ * then refine_steps times R = I - A X (FP64-accurate; A read from its lower
+ * triangle, intact until the end) and X <- X + X R (sum in FP64); the lower
+ * triangle of A then holds X in FP64.  opts->residual selects how the two
+ * products are formed: by default from exact BF16 slices on the tensor cores
+ * (R to FP64 accuracy, X R to about 1e-10 relative, which the small
+ * correction term needs), or R with native FP64 MMA and X R in FP32.  The
+ * error after k steps is about cond(A)^(2^k - 1) e^(2^k) for the FP32
+ * result's error e, so the step count needed for a target grows with cond(A).
+ * The workspace holds three n x n FP64 matrices when refine_steps > 0, plus
+ * 14 n^2 BF16 slices with the emulated products. */
 SPDINV_API spdinv_status spdinv_potri_ex(int64_t n, double* dA, int64_t lda, const spdinv_opts* opts,
                               int* d_info, cudaStream_t stream);
+
+/* Selected inverse: the diagonal of A^{-1} (the variances in a
+ * variance-covariance matrix A^{-1}, the use the paper's introduction names
+ * for an explicit inverse; Sec. 1) without forming the rest
+ * of A^{-1}.  Steps 1 and 2 run in full; of Step 3 only the diagonal tiles'
+ * LAUUM + SYRK chains run (about n^2 b / 2 of its n^3 / 3 multiply-adds), all
+ * in the same persistent launch.  dA: lower triangle of the SPD matrix
+ * (column-major, lda >= n), only read.  d_diag: n doubles (device), receives
+ * diag(A^{-1}).  d_info (nullable device int): 0, or k > 0 if the leading
+ * minor of order k is not positive definite (d_diag is then unspecified).
+ * Argument errors return synchronously and launch nothing. */
+SPDINV_API spdinv_status spdinv_potri_diag(int64_t n, const double* dA, int64_t lda, double* d_diag, int* d_info,
+                                           cudaStream_t stream);
 
 /* Residual of an approximate inverse (used by the mixed-precision
  * correction; the paper has none): R = I - A X with A symmetric, given by the
@@ -275,7 +292,8 @@ SPDINV_API spdinv_status spdinv_dag_task_counts(int t, int64_t out[12]);
  * take them.  Each task is encoded as (kind << 28) | (i << 14) | j with kind
  * 0 = Step-1 diagonal, 1 = Step-1 off-diagonal, 2 = Step-2 diagonal,
  * 3 = Step-2 off-diagonal, 4 = Step-3 diagonal, 5 = Step-3 off-diagonal.
- * steps: 1 = potrf, 2 = trtri, 3 = lauum, 0 = potri (all three).
+ * steps: 1 = potrf, 2 = trtri, 3 = lauum, 0 = potri (all three),
+ * 4 = potri_diag (Steps 1 and 2, and Step 3's diagonal tiles only).
  * Writes at most cap tasks to out (NULL allowed when cap == 0), the task
  * count to *ntasks and the weighted critical path (in units of one b^3
  * multiply-add tile product) to *crit (nullable). */

@@ -58,6 +58,7 @@ SIGNATURES = {
     "spdinv_potri": (c_int, [c_int64, P, c_int64, P, P]),
     "spdinv_potri_ex": (c_int, [c_int64, P, c_int64, ctypes.POINTER(spdinv_opts), P, P]),
     "spdinv_potri_noalloc": (c_int, [c_int64, P, c_int64, P, P]),
+    "spdinv_potri_diag": (c_int, [c_int64, P, c_int64, P, P, P]),
     "spdinv_inverse_residual": (c_int, [c_int64, P, c_int64, P, P, c_int, P]),
     "spdinv_potri_batched": (c_int, [c_int, P, P, P, P, P]),
     "spdinv_spotri_batched": (c_int, [c_int, P, P, P, P, P]),
@@ -121,6 +122,10 @@ def spdinv_potri_ex(n, dA, lda, opts, d_info, stream):
 
 def spdinv_inverse_residual(n, dA, lda, dX, dR, residual, stream):
     return _call("spdinv_inverse_residual", n, dA, lda, dX, dR, residual, stream)
+
+
+def spdinv_potri_diag(n, dA, lda, d_diag, d_info, stream):
+    return _call("spdinv_potri_diag", n, dA, lda, d_diag, d_info, stream)
 
 
 def spdinv_potri_noalloc(n, dA, lda, d_info, stream):

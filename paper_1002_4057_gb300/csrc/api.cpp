@@ -95,10 +95,11 @@ static int default_tile(int64_t n) { return n >= 8192 ? 64 : 32; }
 
 // Shared body of potrf / trtri / lauum / potri (FP64).
 spdinv_status run_fp64(int64_t n, double* dA, int64_t lda, int steps, const spdinv_opts* o, int* d_info,
-                       cudaStream_t stream) {
+                       cudaStream_t stream, double* d_diag) {
     if (n < 0) return SPDINV_ERR_N;
     if (lda < (n > 1 ? n : 1)) return SPDINV_ERR_LDA;
     if (n > 0 && dA == nullptr) return SPDINV_ERR_NULL;
+    if (steps == STEPS_DIAG && n > 0 && d_diag == nullptr) return SPDINV_ERR_NULL;
     int b = (o && o->tile > 0) ? o->tile : default_tile(n);
     if (b != 32 && b != 64) return SPDINV_ERR_UNSUPPORTED;
     if (o && o->precision != SPDINV_PREC_FP64) return SPDINV_ERR_UNSUPPORTED;
@@ -142,6 +143,7 @@ spdinv_status run_fp64(int64_t n, double* dA, int64_t lda, int steps, const spdi
     p.Dw = reinterpret_cast<double*>(base + ctrl_bytes + bytesB + bytesC);
     p.timeout_ns = (long long)(wait_timeout_s(o) * 1e9);
     p.drop_task = (o && o->wait_timeout_s > 0 && o->fault_drop_task >= 0) ? o->fault_drop_task : -1;
+    p.diag = d_diag;
     e = ds.exec_plan(t, steps, &p.tasks, &p.ntasks);
     if (e != cudaSuccess) return cuda_fail(e);
 
@@ -184,6 +186,12 @@ spdinv_status spdinv_potri_ex(int64_t n, double* dA, int64_t lda, const spdinv_o
     return run_fp64(n, dA, lda, STEPS_ALL, opts, d_info, stream);
 }
 
+spdinv_status spdinv_potri_diag(int64_t n, const double* dA, int64_t lda, double* d_diag, int* d_info,
+                                cudaStream_t stream) {
+    // A is only read: Step 3 keeps just the diagonal of each diagonal tile.
+    return run_fp64(n, const_cast<double*>(dA), lda, STEPS_DIAG, nullptr, d_info, stream, d_diag);
+}
+
 spdinv_status spdinv_dag_critical_path(int t, int flags, int64_t out[4]) {
     if (t < 1 || t > 256) return SPDINV_ERR_N;
     if (!out) return SPDINV_ERR_NULL;
@@ -201,7 +209,7 @@ spdinv_status spdinv_dag_task_counts(int t, int64_t out[12]) {
 spdinv_status spdinv_plan_tasks(int64_t n, int b, int steps, uint32_t* out, int64_t cap, int64_t* ntasks,
                                 double* crit) {
     if (n < 1 || b < 1) return SPDINV_ERR_N;
-    if (steps < 0 || steps > 3) return SPDINV_ERR_UNSUPPORTED;
+    if (steps < 0 || steps > 4) return SPDINV_ERR_UNSUPPORTED;
     if (!ntasks || (cap > 0 && !out)) return SPDINV_ERR_NULL;
     const int64_t t = (n + b - 1) / b;
     if (t > 16383) return SPDINV_ERR_N;

@@ -31,8 +31,9 @@ struct DeviceState {
 DeviceState& device_state(int dev);
 void count_launches(int k);
 spdinv_status cuda_fail(cudaError_t e);
+// d_diag: STEPS_DIAG only, receives diag(A^{-1}).
 spdinv_status run_fp64(int64_t n, double* dA, int64_t lda, int steps, const spdinv_opts* o, int* d_info,
-                       cudaStream_t stream);
+                       cudaStream_t stream, double* d_diag = nullptr);
 spdinv_status run_mixed(int64_t n, double* dA, int64_t lda, const spdinv_opts* o, int* d_info,
                         cudaStream_t stream);
 

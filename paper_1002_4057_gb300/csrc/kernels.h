@@ -25,6 +25,7 @@ struct KParamsF64 {
     int* ctrl;            // [0] ticket, [1] abort, [2] error, [3] info
     long long timeout_ns; // limit of one dependency wait
     int drop_task;        // failure-injection hook (-1 = off)
+    double* diag;         // STEPS_DIAG: receives diag(A^{-1}) (n entries); A is not written
 };
 
 // Queues the FP64 persistent inversion (plus the stage-in copy for the

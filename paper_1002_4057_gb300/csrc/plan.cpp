@@ -176,9 +176,10 @@ ExecPlan build_exec_plan(int t, int steps) {
     ExecPlan p;
     p.t = t;
     p.steps = steps;
-    const bool s1 = steps == STEPS_ALL || steps == STEPS_POTRF;
-    const bool s2 = steps == STEPS_ALL || steps == STEPS_TRTRI;
-    const bool s3 = steps == STEPS_ALL || steps == STEPS_LAUUM;
+    const bool s1 = steps == STEPS_ALL || steps == STEPS_POTRF || steps == STEPS_DIAG;
+    const bool s2 = steps == STEPS_ALL || steps == STEPS_TRTRI || steps == STEPS_DIAG;
+    const bool s3 = steps == STEPS_ALL || steps == STEPS_LAUUM || steps == STEPS_DIAG;
+    const bool s3off = steps != STEPS_DIAG;
     const bool s2diag = steps == STEPS_TRTRI;  // in potri the Step-1 diagonal task inverts
 
     // Sequential (topological) order: Algorithm 1's loop nest.
@@ -195,7 +196,8 @@ ExecPlan build_exec_plan(int t, int steps) {
         }
     if (s3)
         for (int i = 0; i < t; ++i) {
-            for (int j = 0; j < i; ++j) seq.push_back(encode_task(K_S3_OFF, i, j));
+            if (s3off)
+                for (int j = 0; j < i; ++j) seq.push_back(encode_task(K_S3_OFF, i, j));
             seq.push_back(encode_task(K_S3_DIAG, i, i));
         }
     const size_t N = seq.size();

@@ -26,7 +26,9 @@ SPDINV_HD inline uint32_t task_kind(uint32_t e) { return e >> 28; }
 SPDINV_HD inline uint32_t task_i(uint32_t e) { return (e >> 14) & 0x3FFFu; }
 SPDINV_HD inline uint32_t task_j(uint32_t e) { return e & 0x3FFFu; }
 
-enum PlanSteps { STEPS_ALL = 0, STEPS_POTRF = 1, STEPS_TRTRI = 2, STEPS_LAUUM = 3 };
+// STEPS_DIAG: Steps 1 and 2 in full and, of Step 3, only the diagonal tiles
+// (the selected inverse diag(A^{-1})).
+enum PlanSteps { STEPS_ALL = 0, STEPS_POTRF = 1, STEPS_TRTRI = 2, STEPS_LAUUM = 3, STEPS_DIAG = 4 };
 
 struct ExecPlan {
     int t = 0;

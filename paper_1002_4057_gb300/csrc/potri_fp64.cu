@@ -112,7 +112,7 @@ __global__ void __launch_bounds__(kThreads) potri_fp64_persistent(const KParamsF
     int* const fL = p.flags;                  // [t*t]  B_ij holds L_ij
     int* const fX = p.flags + (int64_t)t * t; // [t*t]  C_ij holds X_ij
     int* const fD = p.flags + 2 * (int64_t)t * t;  // [t]  D_j holds X_jj
-    const bool from_A = p.steps == STEPS_ALL || p.steps == STEPS_POTRF;
+    const bool from_A = p.steps == STEPS_ALL || p.steps == STEPS_POTRF || p.steps == STEPS_DIAG;
     // D_i is staged before the launch for spdinv_lauum: nothing to wait for.
     auto dflag = [&](int q) -> const int* { return p.steps == STEPS_LAUUM ? nullptr : &fD[q]; };
 
@@ -222,7 +222,14 @@ __global__ void __launch_bounds__(kThreads) potri_fp64_persistent(const KParamsF
             cta_sync();
             acc_store<B>(acc, T0);
             cta_sync();
-            store_A_tile<B>(p, i, i, T0, true);
+            if (p.steps == STEPS_DIAG) {
+                for (int r = threadIdx.x; r < B; r += kThreads) {
+                    const int64_t g = (int64_t)i * B + r;
+                    if (g < p.n) p.diag[g] = T0[r * B + r];
+                }
+            } else {
+                store_A_tile<B>(p, i, i, T0, true);
+            }
         }
     }
 }

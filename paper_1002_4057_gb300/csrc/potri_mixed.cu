@@ -3,9 +3,15 @@
 // (GEMM, SYRK, TRMM) in FP32 while every diagonal-tile POTRF and TRTRI runs in
 // native FP64; then `refine_steps` residual corrections bring the result back
 // to FP64 accuracy:
-//      R = I - A X         (FP64, tensor-core MMA; A read from its lower triangle)
-//      X <- X + X R        (the small correction X R in FP32, added in FP64)
-// and the lower triangle of X is written into A.
+//      R = I - A X         (FP64-accurate; A read from its lower triangle)
+//      X <- X + X R        (the small correction X R, added in FP64)
+// and the lower triangle of X is written into A.  By default both products
+// run on the BF16 tensor cores as sums of exact slice products
+// (residual_ozaki.cu, residual_tc.cu): R from 7 slices per operand, 28 slice
+// pairs in every step but the last and 34 in the last one; X R from 5 slices,
+// 15 pairs, since the correction only needs ~1e-10 relative accuracy of a
+// term that is itself small.  SPDINV_RESIDUAL_FP64 forms R with native FP64
+// MMA and X R in FP32 on the CUDA cores instead.
 //
 // The persistent FP32 kernel follows the FP64 one task for task.  Its
 // renamed stores hold FP32 tiles padded to b x (b+1) -- the layout the

@@ -15,9 +15,11 @@
 //     are added exactly in INT32 and each pair in FP64 with its scale
 //     2^{e_i + f_j - 8(s+t+2)};
 //   * pairs with s + t > L are dropped.  Rows are scaled by their largest
-//     entry, so smaller entries keep fewer bits; S = 7 and L = 6 (28 pairs)
-//     bring the error to about 1e-15 relative to |A| |X| on the inversion's
-//     matrices, below what the corrections need.
+//     entry, so smaller entries keep fewer bits.  S = 7 with L = 6 (28 pairs)
+//     leaves an error of about 1e-15 relative to |A| |X|, enough for every
+//     correction step but the last; L = 7 (34 pairs) brings it to about
+//     1e-16, the accuracy of the native FP64 product, which the last step
+//     needs because its residual error stays in the result.
 // The slice products run on mma.sync m16n8k16 (BF16 in, FP32 out), fed from
 // shared memory by cp.async and ldmatrix.
 #include <cuda_bf16.h>

@@ -16,8 +16,9 @@
 //             adds those into INT64 level sums kept in tensor memory (columns
 //             256-511, lo/hi pairs); per level s + t -- all its pairs share
 //             the scale 2^{e_i + f_j - 8(s+t+2)} -- it adds the level once into
-//             R (FP64, global).  FP64 work, slow on this chip, thus happens 7
-//             times per tile instead of once per chunk or pair.
+//             R (FP64, global).  FP64 work, slow on this chip, thus happens
+//             once per level (L + 1 times per tile) instead of once per chunk
+//             or pair.
 // Every wait is bounded; on a timeout the CTA records an error, all roles
 // leave their loops, and the tensor memory is freed before exit.
 #include <cuda.h>

@@ -83,6 +83,18 @@ def potri_(A, info=None, stream=None, tile=0, ctas_per_sm=0, precision=0, refine
     return info
 
 
+def inverse_diag(A, info=None, stream=None):
+    """diag(A^{-1}) of an SPD matrix (column-major float64 CUDA tensor; only
+    its lower triangle is read, nothing is written) as a new length-n
+    tensor: Steps 1 and 2 and the diagonal tiles of Step 3."""
+    n, lda = _lda(A, torch.float64)
+    info = _info_buf(A.device) if info is None else info
+    d = torch.empty(n, dtype=torch.float64, device=A.device)
+    _check(L.spdinv_potri_diag(n, A.data_ptr(), lda, d.data_ptr(), info.data_ptr(), _stream(stream)),
+           "spdinv_potri_diag")
+    return d
+
+
 def mirror_lower(A):
     """Full symmetric matrix from the lower triangle (a new tensor)."""
     Lo = torch.tril(A)
