@@ -96,6 +96,10 @@ typedef struct {
                             SPDINV_RESIDUAL_FP64 (1): native FP64 tensor-core products;
                             SPDINV_RESIDUAL_EMULATED_MMA_SYNC (2): the slice products on the
                             warp-level mma.sync tensor-core path (for comparison). */
+    int refine_order;    /* mixed precision: order p of each correction,
+                            X <- X (I + R + R^2 + ... + R^{p-1}) with R = I - A X, whose new
+                            residual is R^p; 0 = 2 (Newton-Schulz).  2..8; p > 2 needs
+                            residual = SPDINV_RESIDUAL_EMULATED. */
 } spdinv_opts;
 
 #define SPDINV_RESIDUAL_EMULATED 0
@@ -132,19 +136,22 @@ SPDINV_API spdinv_status spdinv_lauum(int64_t n, double* dA, int64_t lda, cudaSt
 SPDINV_API spdinv_status spdinv_potri(int64_t n, double* dA, int64_t lda, int* d_info, cudaStream_t stream);
 
 /* spdinv_potri with options (tile size, residency, precision, correction
- * steps, wait limit).  opts may be NULL (= all defaults).
+ * steps and order, wait limit).  opts may be NULL (= all defaults).
  * Mixed precision (opts->precision == SPDINV_PREC_MIXED_FP32, tile 32 or 64):
  * the tile DAG runs with FP32 bulk updates and FP64 diagonal POTRF/TRTRI,
  * then refine_steps times R = I - A X (FP64-accurate; A read from its lower
- * triangle, intact until the end) and X <- X + X R (sum in FP64); the lower
- * triangle of A then holds X in FP64.  opts->residual selects how the two
- * products are formed: by default from exact BF16 slices on the tensor cores
- * (R to FP64 accuracy, X R to about 1e-10 relative, which the small
- * correction term needs), or R with native FP64 MMA and X R in FP32.  The
- * error after k steps is about cond(A)^(2^k - 1) e^(2^k) for the FP32
- * result's error e, so the step count needed for a target grows with cond(A).
- * The workspace holds three n x n FP64 matrices when refine_steps > 0, plus
- * 14 n^2 BF16 slices with the emulated products. */
+ * triangle, intact until the end) and X <- X + X R + ... + X R^{p-1} (p =
+ * refine_order; sums in FP64); the lower triangle of A then holds X in FP64.
+ * opts->residual selects how the products are formed: by default from exact
+ * BF16 slices on the tensor cores (R to FP64 accuracy, the terms X R^m to the
+ * relative accuracy their size calls for), or R with native FP64 MMA and X R
+ * in FP32 (p = 2 only).  A step of order p takes a residual R to about R^p,
+ * so the FP32 result's error e (about 1e-5 at cond 1e2, 1e-3 at cond 1e4 for
+ * n = 16384) falls to about e^p times a modest factor that grows with
+ * cond(A): one step of order 3 reaches 1e-10 at cond 1e2, one of order 4 at
+ * cond 1e4, two of order 3 at cond 1e6.  The workspace holds three n x n FP64
+ * matrices when refine_steps > 0, plus 23 n^2 BF16 slices with the emulated
+ * products. */
 SPDINV_API spdinv_status spdinv_potri_ex(int64_t n, double* dA, int64_t lda, const spdinv_opts* opts,
                               int* d_info, cudaStream_t stream);
 

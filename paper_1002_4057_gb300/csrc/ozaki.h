@@ -17,14 +17,27 @@ size_t ozaki_workspace_bytes(int64_t n, int S);
 cudaError_t ozaki_residual(int64_t n, const double* A, int64_t lda, const double* X, double* R, void* ws, int S,
                            int L, bool tc, int* err, cudaStream_t s, int* launches);
 
-// The slice products with tcgen05 (residual_tc.cu).
-cudaError_t ozaki_products_tc(int64_t n, int64_t npad, const void* Asl, const void* Xsl, int S, const int* ps,
-                              const int* pt, int npairs, const int* e, const int* f, double* R, const double* base,
-                              double sign, int* err, cudaStream_t s);
+// The slice products with tcgen05 (residual_tc.cu): output = base + sign *
+// sum of the pairs' products, where base is the given matrix, or the identity
+// (identity = true) or zero when base is nullptr.  SA / SB: slice planes held
+// by the two operands.  lower: only the 128 x 128 output tiles on and below
+// the diagonal (products known to be symmetric).
+cudaError_t ozaki_products_tc(int64_t n, int64_t npad, const void* Asl, int SA, const void* Xsl, int SB,
+                              const int* ps, const int* pt, int npairs, const int* e, const int* f, double* R,
+                              const double* base, bool identity, double sign, bool lower, int* err, cudaStream_t s);
 
-// Xn = X + X R on the tensor cores (X symmetric, stored full; R full; all ld
-// n): the same exact-slice products with S slices and pairs s + t <= L.
-cudaError_t ozaki_correction(int64_t n, const double* X, const double* R, double* Xn, void* ws, int S, int L,
-                             int* err, cudaStream_t s, int* launches);
+// Workspace bytes of ozaki_refine_step for order n.
+size_t ozaki_refine_workspace_bytes(int64_t n);
+
+// One correction step of order p (2 <= p <= 8) of the hyperpower family
+// X <- X (I + R + ... + R^{p-1}), R = I - A X, whose new residual is R^p:
+//   R = I - A X from 7 slices per operand, pairs with levels <= levelsR;
+//   X R, X R^2, ... as (X R^{m-1}) R, each symmetric, lower tiles only, with
+//   fewer slices as the terms shrink; each term is added into X.
+// X is symmetric, read from and updated in its lower triangle (ld n); R
+// (n x n) and Y (n x n, the current term) are scratch.  A (lower, lda) is
+// sliced only when slice_A (its slices are kept in ws between steps).
+cudaError_t ozaki_refine_step(int64_t n, const double* A, int64_t lda, double* X, double* R, double* Y, void* ws,
+                              int levelsR, int order, bool slice_A, int* err, cudaStream_t s, int* launches);
 
 }  // namespace spdinv

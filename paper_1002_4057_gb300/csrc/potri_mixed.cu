@@ -1,17 +1,20 @@
 // Mixed-precision inversion (an added form): the tile DAG of Algorithm 1
 // (Sec. 2) with renaming and pipelining (Sec. 3) runs with its bulk updates
 // (GEMM, SYRK, TRMM) in FP32 while every diagonal-tile POTRF and TRTRI runs in
-// native FP64; then `refine_steps` residual corrections bring the result back
-// to FP64 accuracy:
+// native FP64; then `refine_steps` residual corrections of order p bring the
+// result back to FP64 accuracy:
 //      R = I - A X         (FP64-accurate; A read from its lower triangle)
-//      X <- X + X R        (the small correction X R, added in FP64)
-// and the lower triangle of X is written into A.  By default both products
-// run on the BF16 tensor cores as sums of exact slice products
-// (residual_ozaki.cu, residual_tc.cu): R from 7 slices per operand, 28 slice
-// pairs in every step but the last and 34 in the last one; X R from 5 slices,
-// 15 pairs, since the correction only needs ~1e-10 relative accuracy of a
-// term that is itself small.  SPDINV_RESIDUAL_FP64 forms R with native FP64
-// MMA and X R in FP32 on the CUDA cores instead.
+//      X <- X + X R + X R^2 + ... + X R^{p-1}
+// (the hyperpower family of iterations for the inverse; p = 2 is the
+// Newton-Schulz step; the new residual is R^p), and the lower triangle of X
+// is written into A.  By default every product runs on the BF16 tensor cores
+// as a sum of exact slice products (residual_ozaki.cu, residual_tc.cu): R from
+// 7 slices per operand, 28 slice pairs in every step but the last and 34 in
+// the last one, whose residual error stays in the result; the terms X R^m are
+// formed as (X R^{m-1}) R, symmetric, so only their lower tiles, with 15, 10,
+// 6, ... pairs as the terms shrink.  SPDINV_RESIDUAL_FP64 (and the mma.sync
+// comparison path) forms R with native FP64 MMA (or mma.sync slices) and X R
+// in FP32 on the CUDA cores instead, for p = 2 only.
 //
 // The persistent FP32 kernel follows the FP64 one task for task.  Its
 // renamed stores hold FP32 tiles padded to b x (b+1) -- the layout the
@@ -380,6 +383,9 @@ spdinv_status run_mixed(int64_t n, double* dA, int64_t lda, const spdinv_opts* o
     const int b = o->tile > 0 ? o->tile : 64;
     if (b != 32 && b != 64) return SPDINV_ERR_UNSUPPORTED;
     if (o->refine_steps < 0 || o->refine_steps > 16) return SPDINV_ERR_UNSUPPORTED;
+    const int order = o->refine_order == 0 ? 2 : o->refine_order;
+    if (order < 2 || order > 8) return SPDINV_ERR_UNSUPPORTED;
+    if (order > 2 && o->residual != SPDINV_RESIDUAL_EMULATED) return SPDINV_ERR_UNSUPPORTED;
     const int64_t t64 = (n + b - 1) / b;
     if (t64 > 16383) return SPDINV_ERR_N;
     if (n == 0) {
@@ -409,7 +415,10 @@ spdinv_status run_mixed(int64_t n, double* dA, int64_t lda, const spdinv_opts* o
     // but the last, whose residual error stays in the result: it keeps the
     // levels up to 7 (34 pairs), which matches the native FP64 residual.
     constexpr int kSlices = 7, kLevels = 6, kLevelsLast = 7;
-    const size_t oz = (steps > 0 && emulated) ? align(ozaki_workspace_bytes(n, kSlices)) : 0;
+    const bool chain = o->residual == SPDINV_RESIDUAL_EMULATED;  // order-p step on tcgen05
+    const size_t oz = (steps > 0 && emulated)
+                          ? align(chain ? ozaki_refine_workspace_bytes(n) : ozaki_workspace_bytes(n, kSlices))
+                          : 0;
     const size_t total = ctrl_bytes + 2 * bytesBC + bytesD + nn * (steps > 0 ? 3 : 1) + oz;
     e = ds.ensure_workspace(total);
     if (e != cudaSuccess) return cuda_fail(e);
@@ -447,7 +456,13 @@ spdinv_status run_mixed(int64_t n, double* dA, int64_t lda, const spdinv_opts* o
     if (e == cudaSuccess) e = cudaFuncSetAttribute(correct_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, csm);
     if (e != cudaSuccess) return cuda_fail(e);
     double* Xc = X0;
-    for (int s = 0; s < steps; ++s) {
+    for (int s = 0; s < steps && chain; ++s) {
+        // X (lower triangle) is updated in place; X1 holds the current term.
+        e = ozaki_refine_step(n, dA, lda, X0, R, X1, ozws, s == steps - 1 ? kLevelsLast : kLevels, order, s == 0,
+                              p.ctrl + 2, stream, &launches);
+        if (e != cudaSuccess) return cuda_fail(e);
+    }
+    for (int s = 0; s < steps && !chain; ++s) {
         double* Xn = (Xc == X0) ? X1 : X0;
         if (emulated) {
             e = ozaki_residual(n, dA, lda, Xc, R, ozws, kSlices, s == steps - 1 ? kLevelsLast : kLevels,
@@ -457,13 +472,7 @@ spdinv_status run_mixed(int64_t n, double* dA, int64_t lda, const spdinv_opts* o
             residual_kernel<<<(unsigned)((int64_t)rt * rt), kThreads, rsm, stream>>>(n, dA, lda, Xc, R, p.ctrl);
             launches += 1;
         }
-        if (o->residual == SPDINV_RESIDUAL_EMULATED) {  // X + X R from 5 exact slices (beyond FP32 accuracy)
-            e = ozaki_correction(n, Xc, R, Xn, ozws, 5, 4, p.ctrl + 2, stream, &launches);
-            if (e != cudaSuccess) return cuda_fail(e);
-            launches -= 1;
-        } else {
-            correct_kernel<<<(unsigned)((int64_t)rt * rt), kThreads, csm, stream>>>(n, Xc, R, Xn, p.ctrl);
-        }
+        correct_kernel<<<(unsigned)((int64_t)rt * rt), kThreads, csm, stream>>>(n, Xc, R, Xn, p.ctrl);
         Xc = Xn;
         launches += 1;
     }

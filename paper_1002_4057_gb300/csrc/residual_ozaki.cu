@@ -341,11 +341,10 @@ cudaError_t ozaki_residual(int64_t n, const double* A, int64_t lda, const double
     col_absmax_kernel<<<(unsigned)n, 256, 0, s>>>(n, X, cmax);
     exponents_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, rmax, e);
     exponents_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, cmax, f);
-    // padding rows/columns of the slices must be zero
-    err = cudaMemsetAsync(Asl, 0, 2 * (size_t)S * npad * npad * sizeof(__nv_bfloat16), s);
-    if (err != cudaSuccess) return err;
-    slice_A_kernel<<<dim3((unsigned)t32, (unsigned)t32), dim3(32, 8), 0, s>>>(n, npad, A, lda, e, S, Asl);
-    slice_X_kernel<<<(unsigned)n, 256, 0, s>>>(n, npad, X, f, S, Xsl);
+    // the slicing grids cover the padded planes, writing zeros past n
+    const unsigned tp = (unsigned)(npad / 32);
+    slice_A_kernel<<<dim3(tp, tp), dim3(32, 8), 0, s>>>(n, npad, A, lda, e, S, Asl);
+    slice_X_kernel<<<(unsigned)npad, 256, 0, s>>>(n, npad, X, f, S, Xsl);
     OzParams p{};
     p.n = n;
     p.npad = npad;
@@ -366,7 +365,7 @@ cudaError_t ozaki_residual(int64_t n, const double* A, int64_t lda, const double
         }
     p.npairs = np;
     if (tc) {
-        err = ozaki_products_tc(n, npad, Asl, Xsl, S, p.ps, p.pt, np, e, f, R, nullptr, -1.0, errw, s);
+        err = ozaki_products_tc(n, npad, Asl, S, Xsl, S, p.ps, p.pt, np, e, f, R, nullptr, true, -1.0, false, errw, s);
         if (launches) *launches += 7;
         return err;
     }
@@ -381,36 +380,131 @@ cudaError_t ozaki_residual(int64_t n, const double* A, int64_t lda, const double
 }  // namespace spdinv
 
 namespace spdinv {
+namespace {
 
-cudaError_t ozaki_correction(int64_t n, const double* X, const double* R, double* Xn, void* ws, int S, int L,
-                             int* errw, cudaStream_t s, int* launches) {
-    const int64_t npad = (n + 255) / 256 * 256;
-    char* w = static_cast<char*>(ws);
-    __nv_bfloat16* Xsl = reinterpret_cast<__nv_bfloat16*>(w);  // A operand: X (symmetric: its columns are its rows)
-    __nv_bfloat16* Rsl = Xsl + (size_t)S * npad * npad;          // B operand: R, K-major per column
-    unsigned long long* xmax = reinterpret_cast<unsigned long long*>(Rsl + (size_t)S * npad * npad);
-    unsigned long long* rmax = xmax + npad;
-    int* e = reinterpret_cast<int*>(rmax + npad);
-    int* f = e + npad;
-    cudaError_t err = cudaMemsetAsync(Xsl, 0, 2 * (size_t)S * npad * npad * sizeof(__nv_bfloat16), s);
+// Slices of a symmetric matrix given by its lower triangle (ld): row maxima,
+// exponents and S planes, laid out as rows (equal to the columns).
+cudaError_t slice_symmetric(int64_t n, int64_t npad, const double* M, int64_t ld, int S, __nv_bfloat16* planes,
+                            unsigned long long* mx, int* ex, cudaStream_t s, int* launches) {
+    cudaError_t err = cudaMemsetAsync(mx, 0, sizeof(unsigned long long) * npad, s);
     if (err != cudaSuccess) return err;
-    col_absmax_kernel<<<(unsigned)n, 256, 0, s>>>(n, X, xmax);
-    col_absmax_kernel<<<(unsigned)n, 256, 0, s>>>(n, R, rmax);
-    exponents_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, xmax, e);
-    exponents_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, rmax, f);
-    slice_X_kernel<<<(unsigned)n, 256, 0, s>>>(n, npad, X, e, S, Xsl);
-    slice_X_kernel<<<(unsigned)n, 256, 0, s>>>(n, npad, R, f, S, Rsl);
-    int ps[64], pt[64], np = 0;
+    const unsigned t32 = (unsigned)((n + 31) / 32), tp = (unsigned)(npad / 32);
+    row_absmax_kernel<<<dim3(t32, t32), dim3(32, 8), 0, s>>>(n, M, ld, mx);
+    exponents_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, mx, ex);
+    slice_A_kernel<<<dim3(tp, tp), dim3(32, 8), 0, s>>>(n, npad, M, ld, ex, S, planes);
+    *launches += 3;
+    return cudaGetLastError();
+}
+
+// Slices of a full matrix (ld n) by columns: column maxima, exponents and S
+// planes laid out K-major per column.
+cudaError_t slice_columns(int64_t n, int64_t npad, const double* M, int S, __nv_bfloat16* planes,
+                          unsigned long long* mx, int* ex, cudaStream_t s, int* launches) {
+    col_absmax_kernel<<<(unsigned)n, 256, 0, s>>>(n, M, mx);
+    exponents_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, mx, ex);
+    slice_X_kernel<<<(unsigned)npad, 256, 0, s>>>(n, npad, M, ex, S, planes);
+    *launches += 3;
+    return cudaGetLastError();
+}
+
+// Lower triangle: X += Y (both ld n).
+__global__ void add_lower_kernel(int64_t n, double* X, const double* Y) {
+    const int64_t j = blockIdx.x;
+    for (int64_t i = j + threadIdx.x; i < n; i += blockDim.x) X[i + j * n] += Y[i + j * n];
+}
+
+// Slice pairs (s, t), s < SA, t < SB, by increasing level s + t <= L.
+int level_pairs(int SA, int SB, int L, int* ps, int* pt) {
+    int np = 0;
     for (int lv = 0; lv <= L; ++lv)
         for (int a = 0; a <= lv; ++a)
-            if (a < S && lv - a < S && np < 64) {
+            if (a < SA && lv - a < SB && np < 64) {
                 ps[np] = a;
                 pt[np] = lv - a;
                 ++np;
             }
-    err = ozaki_products_tc(n, npad, Xsl, Rsl, S, ps, pt, np, e, f, Xn, X, 1.0, errw, s);
-    if (launches) *launches += 8;
-    return err;
+    return np;
+}
+
+constexpr int kResSlices = 7;                        // slices of A and X for R
+constexpr int kChainLevels[7] = {4, 3, 2, 2, 1, 1, 1};  // level limit of X R^m, m = 1..7
+constexpr int kRSlices = 5;                          // slices of R (kChainLevels[0] + 1)
+constexpr int kYSlices = 4;                          // slices of X R^m (kChainLevels[1] + 1)
+
+struct RefineWs {
+    __nv_bfloat16 *Asl, *Xsl, *Rsl, *Ysl;
+    unsigned long long* mx;
+    int *eA, *eX, *fR, *eY;
+};
+
+RefineWs refine_layout(int64_t n, void* ws) {
+    const int64_t npad = (n + 255) / 256 * 256;
+    const size_t plane = (size_t)npad * npad;
+    RefineWs w;
+    w.Asl = static_cast<__nv_bfloat16*>(ws);
+    w.Xsl = w.Asl + kResSlices * plane;
+    w.Rsl = w.Xsl + kResSlices * plane;
+    w.Ysl = w.Rsl + kRSlices * plane;
+    w.mx = reinterpret_cast<unsigned long long*>(w.Ysl + kYSlices * plane);
+    w.eA = reinterpret_cast<int*>(w.mx + npad);
+    w.eX = w.eA + npad;
+    w.fR = w.eX + npad;
+    w.eY = w.fR + npad;
+    return w;
+}
+
+}  // namespace
+
+size_t ozaki_refine_workspace_bytes(int64_t n) {
+    const int64_t npad = (n + 255) / 256 * 256;
+    const size_t plane = (size_t)npad * npad;
+    return (2 * kResSlices + kRSlices + kYSlices) * plane * sizeof(__nv_bfloat16) +
+           (size_t)npad * (sizeof(unsigned long long) + 4 * sizeof(int)) + 1024;
+}
+
+cudaError_t ozaki_refine_step(int64_t n, const double* A, int64_t lda, double* X, double* R, double* Y, void* ws,
+                              int levelsR, int order, bool slice_A, int* errw, cudaStream_t s, int* launches) {
+    if (order < 2 || order > 8) return cudaErrorInvalidValue;
+    const int64_t npad = (n + 255) / 256 * 256;
+    const RefineWs w = refine_layout(n, ws);
+    cudaError_t err = cudaSuccess;
+    if (slice_A) {  // A does not change between steps
+        err = slice_symmetric(n, npad, A, lda, kResSlices, w.Asl, w.mx, w.eA, s, launches);
+        if (err != cudaSuccess) return err;
+    }
+    // X is symmetric: its row slices are also its column slices.
+    err = slice_symmetric(n, npad, X, n, kResSlices, w.Xsl, w.mx, w.eX, s, launches);
+    if (err != cudaSuccess) return err;
+    int ps[64], pt[64];
+    int np = level_pairs(kResSlices, kResSlices, levelsR, ps, pt);
+    err = ozaki_products_tc(n, npad, w.Asl, kResSlices, w.Xsl, kResSlices, ps, pt, np, w.eA, w.eX, R, nullptr, true,
+                            -1.0, false, errw, s);  // R = I - A X, every tile
+    if (err != cudaSuccess) return err;
+    err = slice_columns(n, npad, R, kRSlices, w.Rsl, w.mx, w.fR, s, launches);
+    if (err != cudaSuccess) return err;
+    *launches += 1;
+    // X R^m = (X R^{m-1}) R is symmetric: only its lower tiles are formed.
+    const __nv_bfloat16* left = w.Xsl;
+    int left_slices = kResSlices;
+    const int* eleft = w.eX;
+    for (int m = 1; m < order; ++m) {
+        const int L = kChainLevels[m - 1];
+        np = level_pairs(L + 1, kRSlices, L, ps, pt);
+        err = ozaki_products_tc(n, npad, left, left_slices, w.Rsl, kRSlices, ps, pt, np, eleft, w.fR, Y, nullptr,
+                                false, 1.0, true, errw, s);
+        if (err != cudaSuccess) return err;
+        *launches += 1;
+        if (m + 1 < order) {
+            err = slice_symmetric(n, npad, Y, n, kYSlices, w.Ysl, w.mx, w.eY, s, launches);
+            if (err != cudaSuccess) return err;
+            left = w.Ysl;
+            left_slices = kYSlices;
+            eleft = w.eY;
+        }
+        add_lower_kernel<<<(unsigned)n, 256, 0, s>>>(n, X, Y);
+        *launches += 1;
+    }
+    return cudaGetLastError();
 }
 
 }  // namespace spdinv

@@ -53,7 +53,9 @@ struct TcParams {
     int64_t n, npad;
     int npairs;
     int tiles;            // tiles per side
-    const double* base;   // output = base + sign * A X   (base == nullptr: the identity)
+    int lower;            // 1: only the output tiles on and below the diagonal (symmetric products)
+    int identity;         // with base == nullptr: 1 = start from the identity, 0 = from zero
+    const double* base;   // output = base + sign * A X   (base == nullptr: identity or zero)
     double sign;
     int ps[64], pt[64];
     const int* e;
@@ -176,12 +178,37 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     // operands' slices in L2.
     constexpr int GROUP_M = 16;
     int tile_m, tile_n;
-    {
+    if (!p.lower) {
         const int pid = blockIdx.x, per_group = GROUP_M * p.tiles;
         const int first = (pid / per_group) * GROUP_M;
         const int gm = min(p.tiles - first, GROUP_M);
         tile_m = first + (pid % per_group) % gm;
         tile_n = (pid % per_group) / gm;
+    } else {
+        // Lower tiles only, the same grouped raster: in the group of row
+        // tiles [first, first + gm), column tile c holds the rows r >= c.
+        int pid = blockIdx.x, first = 0;
+        for (;;) {
+            const int gm = min(p.tiles - first, GROUP_M);
+            const int cnt = first * gm + gm * (gm + 1) / 2;
+            if (pid < cnt || first + gm >= p.tiles) break;
+            pid -= cnt;
+            first += gm;
+        }
+        const int gm = min(p.tiles - first, GROUP_M);
+        if (pid < first * gm) {
+            tile_n = pid / gm;
+            tile_m = first + pid % gm;
+        } else {
+            pid -= first * gm;
+            int c = 0;
+            while (pid >= gm - c) {
+                pid -= gm - c;
+                ++c;
+            }
+            tile_n = first + c;
+            tile_m = tile_n + pid;
+        }
     }
     const int64_t m0 = (int64_t)tile_m * TM, n0 = (int64_t)tile_n * TN;
     const int kstages = (int)(p.npad / TK);            // stages per slice pair
@@ -324,7 +351,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     if (jj < p.n) {
                         double* dst = &p.R[i + jj * p.n];
                         const double base =
-                            first_flush ? (p.base ? p.base[i + jj * p.n] : (i == jj ? 1.0 : 0.0)) : *dst;
+                            first_flush ? (p.base ? p.base[i + jj * p.n] : (p.identity && i == jj ? 1.0 : 0.0))
+                                        : *dst;
                         *dst = fma(p.sign * (double)v, ri * pow2(s_f[j]), base);
                     }
                 }
@@ -368,12 +396,14 @@ bool make_map(CUtensorMap* m, const void* base, int64_t npad, int S) {
 
 }  // namespace
 
-cudaError_t ozaki_products_tc(int64_t n, int64_t npad, const void* Asl, const void* Xsl, int S, const int* ps,
-                              const int* pt, int npairs, const int* e, const int* f, double* R, const double* base,
-                              double sign, int* err, cudaStream_t s) {
+cudaError_t ozaki_products_tc(int64_t n, int64_t npad, const void* Asl, int SA, const void* Xsl, int SB,
+                              const int* ps, const int* pt, int npairs, const int* e, const int* f, double* R,
+                              const double* base, bool identity, double sign, bool lower, int* err, cudaStream_t s) {
     if (npad % TM != 0 || npad % 256 != 0 || npairs > 64) return cudaErrorInvalidValue;
+    for (int q = 0; q < npairs; ++q)  // every pair must address planes that the maps cover
+        if (ps[q] < 0 || ps[q] >= SA || pt[q] < 0 || pt[q] >= SB) return cudaErrorInvalidValue;
     CUtensorMap ma, mb;
-    if (!make_map(&ma, Asl, npad, S) || !make_map(&mb, Xsl, npad, S)) return cudaErrorInvalidValue;
+    if (!make_map(&ma, Asl, npad, SA) || !make_map(&mb, Xsl, npad, SB)) return cudaErrorInvalidValue;
     TcParams p{};
     p.n = n;
     p.npad = npad;
@@ -386,14 +416,17 @@ cudaError_t ozaki_products_tc(int64_t n, int64_t npad, const void* Asl, const vo
     p.f = f;
     p.R = R;
     p.base = base;
+    p.identity = identity ? 1 : 0;
     p.sign = sign;
+    p.lower = lower ? 1 : 0;
     p.tiles = (int)(npad / TM);
     p.err = err;
     p.timeout_ns = 20LL * 1000000000LL;
     const int sm = NSTAGE * STAGE_BYTES;
     cudaError_t rc = cudaFuncSetAttribute(ozaki_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     if (rc != cudaSuccess) return rc;
-    ozaki_tc_kernel<<<(unsigned)(p.tiles * p.tiles), NTHREADS, sm, s>>>(ma, mb, p);
+    const int grid = lower ? p.tiles * (p.tiles + 1) / 2 : p.tiles * p.tiles;
+    ozaki_tc_kernel<<<(unsigned)grid, NTHREADS, sm, s>>>(ma, mb, p);
     return cudaGetLastError();
 }
 

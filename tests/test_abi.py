@@ -59,6 +59,15 @@ def test_unsupported_tile(lib):
     assert L.spdinv_potri_ex(100, 8, 100, o, None, None) == L.SPDINV_ERR_UNSUPPORTED
 
 
+@pytest.mark.parametrize("order,residual", [(1, 0), (9, 0), (-2, 0), (3, 1), (3, 2)])
+def test_unsupported_refine_order(lib, order, residual):
+    """Correction orders outside 2..8, and orders above 2 on the residual
+    paths that have only the Newton-Schulz step, are rejected before any
+    device work (the pointer is never touched)."""
+    o = L.spdinv_opts(64, 0, 1, 1, 0.0, -1, residual, order)
+    assert L.spdinv_potri_ex(100, 8, 100, o, None, None) == L.SPDINV_ERR_UNSUPPORTED
+
+
 def test_planner_queries_need_no_gpu(lib):
     st, cp = L.spdinv_dag_critical_path(4, 0)
     assert st == 0 and cp[:3] == [10, 9, 10]

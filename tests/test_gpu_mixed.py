@@ -1,7 +1,8 @@
 """Mixed precision: FP32 bulk tile updates, FP64 diagonal tiles and FP64
 residual corrections, against the FP64 oracle.  The error is stated for every
-result; the 1e-10 gate applies with the number of correction steps the
-conditioning needs (one at cond 1e2, two at 1e4)."""
+result; the 1e-10 gate applies with the number of correction steps and the
+order the conditioning needs (order 2: one step at cond 1e2, two at 1e4;
+one step of order 3 at cond 1e2 and of order 4 at cond 1e4)."""
 import numpy as np
 import pytest
 
@@ -15,9 +16,9 @@ pytestmark = pytest.mark.gpu
 MIXED = 1
 
 
-def _run(T, A, gpu, steps, tile=64):
+def _run(T, A, gpu, steps, tile=64, order=0):
     dA = to_dev(A, gpu)
-    info = T.potri_(dA, precision=MIXED, refine_steps=steps, tile=tile)
+    info = T.potri_(dA, precision=MIXED, refine_steps=steps, tile=tile, refine_order=order)
     import torch
     torch.cuda.synchronize()
     return dA, int(info.item())
@@ -47,10 +48,47 @@ def test_mixed_integer_case_exact(gpu):
     from paper_1002_4057_gb300 import torch_api as T
     n = 700
     A, s = si.bidiag_integer_spd(n, seed=3)
-    for steps in (0, 1):
-        dA, info = _run(T, A, gpu, steps)
+    for steps, order in ((0, 0), (1, 0), (1, 4), (2, 3)):
+        dA, info = _run(T, A, gpu, steps, order=order)
         assert info == 0
         assert np.array_equal(lower_np(dA), np.tril(cf.bidiag_inverse(s)))
+
+
+@pytest.mark.parametrize("n", [1, 64, 129, 256, 513, 1000])
+def test_mixed_one_step_of_higher_order(gpu, n):
+    """One correction of order p: R = I - A X, then X + X R + ... + X R^{p-1}
+    with the terms formed as symmetric lower-tile products.  Order 3 at cond
+    1e2 and order 4 at cond 1e4 reach the 1e-10 gate in one step; a higher
+    order is never worse than order 2 with the same single residual."""
+    from paper_1002_4057_gb300 import torch_api as T
+    for cond, order in ((1e2, 3), (1e4, 4)):
+        A, _, _ = si.spectral_spd(n, cond, seed=si.SEED_BASE + 5 + n)
+        M, _ = oracle.potri(A)
+        ref = oracle.symmetrize_lower(M)
+        errs = {}
+        for p in (2, order, 8):
+            dA, info = _run(T, A, gpu, 1, order=p)
+            assert info == 0
+            errs[p] = oracle.rel_frobenius(full_from_lower(lower_np(dA)), ref)
+        print("n=%d cond=%.0e one step, error by order: %s" % (n, cond, {k: "%.2e" % v for k, v in errs.items()}))
+        assert errs[order] <= 1e-10 and errs[8] <= 1e-10
+        assert errs[order] <= max(errs[2], 1e-13)
+
+
+def test_mixed_two_steps_order3_cond1e6(gpu):
+    """cond 1e6: two steps of order 3, against the spectral definition
+    Q diag(1/lam) Q^T (the FP64 oracle's own error is ~1e-10 here)."""
+    from paper_1002_4057_gb300 import torch_api as T
+    n = 700
+    A, Q, lam = si.spectral_spd(n, 1e6, seed=si.SEED_BASE + 6)
+    ref = (Q / lam) @ Q.T
+    dA, info = _run(T, A, gpu, 2, order=3)
+    assert info == 0
+    err = oracle.rel_frobenius(full_from_lower(lower_np(dA)), ref)
+    M, _ = oracle.potri(A)
+    e64 = oracle.rel_frobenius(oracle.symmetrize_lower(M), ref)
+    print("n=%d cond=1e6 two order-3 steps: error %.2e (FP64 oracle %.2e)" % (n, err, e64))
+    assert err <= max(1e-10, 2 * e64)
 
 
 def test_mixed_info(gpu):
@@ -61,38 +99,41 @@ def test_mixed_info(gpu):
     assert info == 151
 
 
-def test_mixed_upper_untouched(gpu):
+@pytest.mark.parametrize("order", [0, 4])
+def test_mixed_upper_untouched(gpu, order):
     from paper_1002_4057_gb300 import torch_api as T
     n = 130
     A, _, _ = si.spectral_spd(n, 1e2, seed=8)
     B = A.copy(order="F")
     iu = np.triu_indices(n, 1)
     B[iu] = -3.5
-    dA, info = _run(T, B, gpu, 1)
+    dA, info = _run(T, B, gpu, 1, order=order)
     assert info == 0
     assert np.all(dA.cpu().numpy()[iu] == -3.5)
 
 
 @pytest.mark.slow
 def test_mixed_full_size_sampled(gpu):
-    """n = 16384, cond 1e2: sampled columns against the spectral definition
-    Q diag(1/lam) Q^T.  At this size the FP32 result's error is ~1e-5, so one
-    correction reaches ~7e-10 and two reach the 1e-10 gate."""
+    """n = 16384: sampled columns against the spectral definition
+    Q diag(1/lam) Q^T.  At this size the FP32 result's error is ~1e-5 at cond
+    1e2 and ~6e-4 at cond 1e4: one order-2 correction reaches ~7e-10 at cond
+    1e2 and two reach the 1e-10 gate, as does one of order 3; at cond 1e4 one
+    step of order 4 does."""
     import torch
     from paper_1002_4057_gb300 import torch_api as T
     n = 16384
     cols = np.array([0, 7777, 16383])
-    for cond, steps in ((1e2, 2),):
+    for cond, steps, order in ((1e2, 2, 2), (1e2, 1, 3), (1e4, 1, 4)):
         A, Q, lam = si.spectral_spd(n, cond, seed=si.SEED_BASE + 2, device=gpu)
         ref = cf.spectral_inverse_columns(Q.cpu().numpy(), lam, cols)
         del Q
         W = A.clone()
-        info = T.potri_(W, precision=MIXED, refine_steps=steps, tile=64)
+        info = T.potri_(W, precision=MIXED, refine_steps=steps, tile=64, refine_order=order)
         assert int(info.item()) == 0
         Lo = torch.tril(W)
         Xc = (Lo[:, cols] + torch.tril(Lo, -1).t()[:, cols]).cpu().numpy()
         err = np.linalg.norm(Xc - ref) / np.linalg.norm(ref)
-        print("n=16384 cond=%.0e steps=%d sampled error %.2e" % (cond, steps, err))
+        print("n=16384 cond=%.0e steps=%d order=%d sampled error %.2e" % (cond, steps, order, err))
         assert err <= 1e-10
         del A, W, Lo
         torch.cuda.empty_cache()
