@@ -6,14 +6,14 @@
 // multiplication by using fast routines of matrix multiplication and its
 // applications", Numer. Algorithms 59 (2012)):
 //   * every row i of A (symmetric, read from its lower triangle) is scaled by
-//     2^-e_i with 2^e_i > max_k |A_ik|, every column j of X by 2^-f_j;
-//   * each scaled entry u in (-1, 1) is cut into S slices of 8 bits,
-//     u = sum_s a_s 2^{-8(s+1)} + rest, a_s integers in [-255, 255] -- exact
-//     in BF16 (8 significant bits);
+//     2^-e_i with 2^e_i > 2 max_k |A_ik|, every column j of X by 2^-f_j;
+//   * each scaled entry u in (-1/2, 1/2) is cut into S balanced digits of
+//     base 256, u = sum_s a_s 2^{-8(s+1)} + rest with a_s = round(256 u_s),
+//     integers in [-128, 128] -- exact in BF16 (8 significant bits);
 //   * for a slice pair (s, t) the product sum_k a_s(i,k) x_t(k,j) has terms
-//     below 2^16 and is exact in FP32 over k-chunks of 256 (< 2^24); chunks
-//     are added exactly in INT32 and each pair in FP64 with its scale
-//     2^{e_i + f_j - 8(s+t+2)};
+//     of at most 2^14 and is exact in FP32 over k-chunks of up to 1024
+//     (<= 2^24); chunks are added exactly in INT32 and each pair in FP64
+//     with its scale 2^{e_i + f_j - 8(s+t+2)};
 //   * pairs with s + t > L are dropped.  Rows are scaled by their largest
 //     entry, so smaller entries keep fewer bits.  S = 7 with L = 6 (28 pairs)
 //     leaves an error of about 1e-15 relative to |A| |X|, enough for every
@@ -35,7 +35,7 @@ namespace {
 constexpr int BM = 128, BN = 64, BK = 32, STAGES = 4, THREADS = 256;
 constexpr int LDS = BK + 8;  // shared row stride (bf16): 80 bytes, conflict-free ldmatrix
 constexpr int CHUNK_TILES = 256 / BK;  // exact FP32 sums of 8-bit slice products
-constexpr int FLUSH_TILES = 128 * CHUNK_TILES;  // INT32 headroom: 128 chunks of 256 x 255^2 < 2^31
+constexpr int FLUSH_TILES = 128 * CHUNK_TILES;  // INT32 headroom: 128 chunks of 256 x 128^2 = 2^29
 
 // Positive doubles order like their bit patterns, so the maxima are kept as
 // 64-bit integers updated with atomicMax.
@@ -83,22 +83,28 @@ __global__ void col_absmax_kernel(int64_t n, const double* X, unsigned long long
     }
 }
 
-// Exponent e with 2^e > m (m = 0 -> 0).
+// Exponent e with 2^e > 2 m (m = 0 -> 0).
 __global__ void exponents_kernel(int64_t n, const unsigned long long* maxbits, int* expo) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const double m = __longlong_as_double((long long)maxbits[i]);
         int e = 0;
-        if (m > 0.0) frexp(m, &e);  // m = f 2^e, f in [0.5, 1)
+        if (m > 0.0) {
+            frexp(m, &e);  // m = f 2^e, f in [0.5, 1)
+            ++e;
+        }
         expo[i] = e;
     }
 }
 
-// The S slices of u = v 2^-e in (-1, 1).
+// The S balanced base-256 digits of u = v 2^-e in (-1/2, 1/2): each step
+// takes a = round(256 u) in [-128, 128] and keeps the remainder, again in
+// [-1/2, 1/2].  Every operation is exact (scaling by powers of two and
+// subtracting the integer part of a double).
 __device__ __forceinline__ void cut(double v, int e, int S, __nv_bfloat16* out, int64_t stride) {
     double u = scalbn(v, -e);
     for (int s = 0; s < S; ++s) {
         u *= 256.0;
-        const double a = trunc(u);
+        const double a = rint(u);
         u -= a;
         out[s * stride] = __float2bfloat16_rn((float)a);
     }

@@ -2,13 +2,14 @@
 // fifth-generation tensor cores: tcgen05.mma (BF16 in, FP32 accumulator in
 // tensor memory), operands staged by TMA with 128-byte swizzle.
 //
-// One CTA computes a 128 x 128 tile of R = I - A X (or, for the correction
-// step, X + X R) over all slice pairs:
+// One CTA computes a 128 x 128 tile of R = I - A X (or of a correction term
+// X R^m) over all slice pairs:
 //   warp 0    TMA producer: 64-deep K slices of A's and X's slice planes into
 //             a 6-stage shared-memory ring;
 //   warp 1    allocates all 512 tensor-memory columns and issues the MMAs
-//             from one thread into two 128-column FP32 accumulators: 4 stages
-//             = one exact 256-deep chunk per accumulator, then a commit;
+//             from one thread into two 128-column FP32 accumulators: 16
+//             stages = one exact 1024-deep chunk per accumulator, then a
+//             commit;
 //   warps 2-9 epilogue: each thread owns half of one accumulator row (its
 //             warp's lane quarter, 64 columns).  Per chunk it reads the
 //             accumulator with tcgen05.ld, adds the exact FP32 integers into
@@ -26,6 +27,8 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <cstdlib>
+#include <map>
 #include <mutex>
 
 #include "api_internal.h"
@@ -38,7 +41,7 @@ namespace {
 constexpr int TM = 128, TN = 128, TK = 64;  // output tile; K per stage = one 128-byte swizzle row of bf16
 constexpr int NSTAGE = 6;  // 1.5 exact chunks in flight: the copies run ahead of the MMAs
 constexpr int A_BYTES = TM * TK * 2, B_BYTES = TN * TK * 2, STAGE_BYTES = A_BYTES + B_BYTES;
-constexpr int CHUNK_STAGES = 256 / TK;  // exact FP32 chunk: 256 products of 8-bit slices
+constexpr int CHUNK_STAGES = 1024 / TK;  // exact FP32 chunk: 1024 products of balanced 8-bit digits (<= 2^24)
 constexpr int TMEM_COLS = 512;          // two 128-column FP32 accumulators + INT64 level sums (256 columns)
 constexpr int LVL_COL = 256;            // first tensor-memory column of the INT64 level sums
 constexpr int NTHREADS = 320;          // warp 0 TMA, warp 1 MMA, warps 2-9 epilogue
@@ -91,6 +94,52 @@ __device__ __forceinline__ void umma_commit(uint64_t* bar) {
                  : "memory");
 }
 
+// ---- thread-block clusters: operand tiles shared by TMA multicast ----------
+// A cluster of CM x CN CTAs computes a CM x CN block of output tiles.  The CN
+// CTAs of one block row need the same A tile: each loads 1/CN of its rows
+// and multicasts them to all CN.  Likewise the CM CTAs of one block column
+// share the B tile, 1/CM of its rows each.  A stage of a CTA's ring is thus
+// written by CM + CN - 1 CTAs (itself included), and each of them may reuse
+// the stage only after this CTA's MMAs have read it: the MMA issuer's commit
+// arrives on the `empty` barrier of every one of those CTAs.
+
+__device__ __forceinline__ uint32_t cluster_ctarank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+// Every thread of every CTA in the cluster; orders the CTAs' shared-memory
+// writes (barrier initialisation) before the peers' later accesses.
+__device__ __forceinline__ void cluster_sync_all() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_mbarrier_init_cluster() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// TMA load whose bytes land, and count, at the same shared-memory offsets in
+// every CTA of `mask`.
+__device__ __forceinline__ void tma_load_2d_mc(void* dst, const CUtensorMap* tm, int x, int y, uint64_t* bar,
+                                               uint16_t mask) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster"
+        " [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(tm)), "r"(x), "r"(y), "r"(smem_u32(bar)), "h"(mask)
+        : "memory");
+}
+
+// Arrive on the mbarrier at this offset in every CTA of `mask` once the MMAs
+// issued so far have completed.
+__device__ __forceinline__ void umma_commit_mc(uint64_t* bar, uint16_t mask) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+            smem_u32(bar)),
+        "h"(mask)
+        : "memory");
+}
+
 // 2^x as a double, exactly, for |x| < 1022.
 __device__ __forceinline__ double pow2(int x) { return __longlong_as_double((long long)(x + 1023) << 52); }
 
@@ -109,6 +158,20 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
         : "memory");
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
+
+// The same load without its wait: several loads in flight, then one wait.
+__device__ __forceinline__ void tmem_ld32_async(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr)
+        : "memory");
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
     asm volatile(
@@ -164,62 +227,77 @@ __device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity, volatil
     }
 }
 
+// Block (bm, bn) of a tb_m x tb_n block grid for launch index `pid`, in a
+// grouped raster: GROUP block rows are swept column by column, so the
+// clusters resident at one time share both operands' slices in L2.  With
+// `lower` only the blocks with bm >= bn (tb_m == tb_n): in the group of rows
+// [first, first + gm), column c holds the rows r >= c.
+__device__ __forceinline__ void block_of(int pid, int tb_m, int tb_n, bool lower, int& bm, int& bn) {
+    constexpr int GROUP = 16;
+    if (!lower) {
+        const int per_group = GROUP * tb_n;
+        const int first = (pid / per_group) * GROUP;
+        const int gm = min(tb_m - first, GROUP);
+        bm = first + (pid % per_group) % gm;
+        bn = (pid % per_group) / gm;
+        return;
+    }
+    int first = 0;
+    for (;;) {
+        const int gm = min(tb_m - first, GROUP);
+        const int cnt = first * gm + gm * (gm + 1) / 2;
+        if (pid < cnt || first + gm >= tb_m) break;
+        pid -= cnt;
+        first += gm;
+    }
+    const int gm = min(tb_m - first, GROUP);
+    if (pid < first * gm) {
+        bn = pid / gm;
+        bm = first + pid % gm;
+    } else {
+        pid -= first * gm;
+        int c = 0;
+        while (pid >= gm - c) {
+            pid -= gm - c;
+            ++c;
+        }
+        bn = first + c;
+        bm = bn + pid;
+    }
+}
+
+template <int CM, int CN>
 __global__ void __launch_bounds__(NTHREADS, 1)
     ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                     const TcParams p) {
+    constexpr int CL = CM * CN;
+    constexpr int A_PART = A_BYTES / CN, B_PART = B_BYTES / CM;  // bytes each CTA loads per stage
     unsigned char* smem = dynamic_smem();  // 1024-byte aligned (swizzled operand tiles)
     __shared__ __align__(8) uint64_t full[NSTAGE], empty[NSTAGE], accf[2], acce[2], fin;
     __shared__ uint32_t tmem_slot;
     __shared__ volatile int s_abort;
     __shared__ int s_f[TN];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // Grouped raster: consecutive CTAs sweep GROUP_M row tiles before moving
-    // to the next column tile, so the CTAs resident at one time share both
-    // operands' slices in L2.
-    constexpr int GROUP_M = 16;
-    int tile_m, tile_n;
-    if (!p.lower) {
-        const int pid = blockIdx.x, per_group = GROUP_M * p.tiles;
-        const int first = (pid / per_group) * GROUP_M;
-        const int gm = min(p.tiles - first, GROUP_M);
-        tile_m = first + (pid % per_group) % gm;
-        tile_n = (pid % per_group) / gm;
-    } else {
-        // Lower tiles only, the same grouped raster: in the group of row
-        // tiles [first, first + gm), column tile c holds the rows r >= c.
-        int pid = blockIdx.x, first = 0;
-        for (;;) {
-            const int gm = min(p.tiles - first, GROUP_M);
-            const int cnt = first * gm + gm * (gm + 1) / 2;
-            if (pid < cnt || first + gm >= p.tiles) break;
-            pid -= cnt;
-            first += gm;
-        }
-        const int gm = min(p.tiles - first, GROUP_M);
-        if (pid < first * gm) {
-            tile_n = pid / gm;
-            tile_m = first + pid % gm;
-        } else {
-            pid -= first * gm;
-            int c = 0;
-            while (pid >= gm - c) {
-                pid -= gm - c;
-                ++c;
-            }
-            tile_n = first + c;
-            tile_m = tile_n + pid;
-        }
-    }
+    // This CTA's place (dm, dn) in its cluster's CM x CN block of tiles.
+    const int rank = CL > 1 ? (int)cluster_ctarank() : 0;
+    const int dm = rank % CM, dn = rank / CM;
+    uint16_t maskA = 0, maskB = 0;  // the CTAs sharing this CTA's A tile (its block row) / B tile
+    for (int q = 0; q < CN; ++q) maskA |= (uint16_t)(1u << (dm + CM * q));
+    for (int q = 0; q < CM; ++q) maskB |= (uint16_t)(1u << (q + CM * dn));
+    const uint16_t maskE = maskA | maskB;  // the CTAs whose copies land in this CTA's ring
+    int bm, bn;
+    block_of((int)(blockIdx.x / CL), p.tiles / CM, p.tiles / CN, p.lower != 0, bm, bn);
+    const int tile_m = bm * CM + dm, tile_n = bn * CN + dn;
     const int64_t m0 = (int64_t)tile_m * TM, n0 = (int64_t)tile_n * TN;
     const int kstages = (int)(p.npad / TK);            // stages per slice pair
-    const int chunks_per_pair = kstages / CHUNK_STAGES;
+    const int chunks_per_pair = (kstages + CHUNK_STAGES - 1) / CHUNK_STAGES;  // the last one may be shorter
     const int total_stages = p.npairs * kstages;
     const int total_chunks = p.npairs * chunks_per_pair;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < NSTAGE; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&empty[s], 1);
+            mbar_init(&empty[s], CM + CN - 1);  // one release per CTA that writes into this ring
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&accf[b], 1);
@@ -228,6 +306,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         mbar_init(&fin, 1);
         s_abort = 0;
         fence_proxy_async_shared();
+        if (CL > 1) fence_mbarrier_init_cluster();
     }
     for (int j = threadIdx.x; j < TN; j += NTHREADS) s_f[j] = (n0 + j < p.n) ? p.f[n0 + j] : 0;
     if (warp == 1) {
@@ -238,6 +317,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     }
     tc_fence_before();
     cta_sync();
+    if (CL > 1) cluster_sync_all();  // the peers' barriers exist before any copy or release targets them
     tc_fence_after();
     const uint32_t tmem = tmem_slot;
 
@@ -249,13 +329,20 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 if (!wait_bar(&empty[s], ((it / NSTAGE) & 1) ^ 1, &s_abort, p)) break;
                 const int pair = it / kstages, kt = it - pair * kstages;
                 unsigned char* st = smem + s * STAGE_BYTES;
-                mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
-                tma_load_2d(st, &tmA, kt * TK, (int)(p.ps[pair] * p.npad + m0), &full[s]);
-                tma_load_2d(st + A_BYTES, &tmB, kt * TK, (int)(p.pt[pair] * p.npad + n0), &full[s]);
+                mbar_arrive_expect_tx(&full[s], STAGE_BYTES);  // the whole stage, whoever copies it
+                const int ya = (int)(p.ps[pair] * p.npad + m0) + dn * (TM / CN);
+                const int yb = (int)(p.pt[pair] * p.npad + n0) + dm * (TN / CM);
+                if (CN > 1) tma_load_2d_mc(st + dn * A_PART, &tmA, kt * TK, ya, &full[s], maskA);
+                else tma_load_2d(st, &tmA, kt * TK, ya, &full[s]);
+                if (CM > 1) tma_load_2d_mc(st + A_BYTES + dm * B_PART, &tmB, kt * TK, yb, &full[s], maskB);
+                else tma_load_2d(st + A_BYTES, &tmB, kt * TK, yb, &full[s]);
             }
             if (s_abort)  // let the copies already issued land before the CTA leaves
                 for (int k = it - NSTAGE > 0 ? it - NSTAGE : 0; k < it; ++k)
                     drain_bar(&full[k % NSTAGE], (k / NSTAGE) & 1, 200000000LL);
+            if (CL > 1)  // every CTA that shares this ring has released its last stages
+                for (int k = it; k < it + NSTAGE; ++k)
+                    drain_bar(&empty[k % NSTAGE], ((k / NSTAGE) & 1) ^ 1, 200000000LL);
         }
     } else if (warp == 1) {
         if (lane == 0) {  // ---- MMA issuer
@@ -265,8 +352,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 if (!wait_bar(&acce[b], ((c >> 1) & 1) ^ 1, &s_abort, p)) break;
                 tc_fence_after();
                 const uint32_t d = tmem + (uint32_t)(b * TN);
+                const int q0 = (c % chunks_per_pair) * CHUNK_STAGES;
+                const int nq = min(CHUNK_STAGES, kstages - q0);
                 bool ok = true;
-                for (int q = 0; q < CHUNK_STAGES; ++q, ++it) {
+                for (int q = 0; q < nq; ++q, ++it) {
                     const int s = it % NSTAGE;
                     if (!wait_bar(&full[s], (it / NSTAGE) & 1, &s_abort, p)) {
                         ok = false;
@@ -278,7 +367,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll
                     for (int k = 0; k < TK / 16; ++k)  // +32 bytes per K=16 inside the swizzle row
                         umma_bf16(d, da + 2 * k, db + 2 * k, (q | k) != 0);
-                    umma_commit(&empty[s]);
+                    if (CL > 1) umma_commit_mc(&empty[s], maskE);
+                    else umma_commit(&empty[s]);
                 }
                 if (!ok) break;
                 umma_commit(&accf[b]);
@@ -303,12 +393,16 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             const int b = c & 1;
             if (!wait_bar(&accf[b], (c >> 1) & 1, &s_abort, p)) break;
             tc_fence_after();
+            {  // both 32-column loads in flight, one wait; the sums are exact integers <= 2^24
+                uint32_t r0[32], r1[32];
+                tmem_ld32_async(trow + (uint32_t)(b * TN + half * EPI_COLS), r0);
+                tmem_ld32_async(trow + (uint32_t)(b * TN + half * EPI_COLS + 32), r1);
+                tmem_wait_ld();
 #pragma unroll
-            for (int cb = 0; cb < EPI_COLS / 16; ++cb) {
-                uint32_t r[16];
-                tmem_ld16(trow + (uint32_t)(b * TN + half * EPI_COLS + cb * 16), r);
-#pragma unroll
-                for (int u = 0; u < 16; ++u) acc[cb * 16 + u] += __float2int_rn(__uint_as_float(r[u]));
+                for (int u = 0; u < 32; ++u) {
+                    acc[u] += __float2int_rn(__uint_as_float(r0[u]));
+                    acc[32 + u] += __float2int_rn(__uint_as_float(r1[u]));
+                }
             }
             tc_fence_before();
             __syncwarp();
@@ -362,6 +456,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     }
     tc_fence_before();
     cta_sync();
+    if (CL > 1) cluster_sync_all();  // no peer copies into, or releases on, a CTA that has left
     tc_fence_after();
     if (warp == 1) {
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
@@ -381,17 +476,81 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
-// 2D map over S slice planes stacked as (S*npad) rows of npad bf16, box 64 x 128.
-bool make_map(CUtensorMap* m, const void* base, int64_t npad, int S) {
+// 2D map over S slice planes stacked as (S*npad) rows of npad bf16, box 64
+// (K, one 128-byte swizzle row) x rows.
+bool make_map(CUtensorMap* m, const void* base, int64_t npad, int S, int rows) {
     auto fn = encode_fn();
     if (!fn) return false;
     cuuint64_t dims[2] = {(cuuint64_t)npad, (cuuint64_t)(S * npad)};
     cuuint64_t strides[1] = {(cuuint64_t)(npad * 2)};
-    cuuint32_t box[2] = {(cuuint32_t)TK, 128u};
+    cuuint32_t box[2] = {(cuuint32_t)TK, (cuuint32_t)rows};
     cuuint32_t estr[2] = {1u, 1u};
     return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int CM, int CN>
+cudaLaunchConfig_t tc_config(const TcParams& p, bool lower, cudaStream_t s, cudaLaunchAttribute* attr) {
+    const int tbm = p.tiles / CM, tbn = p.tiles / CN;
+    const int blocks = lower ? tbm * (tbm + 1) / 2 : tbm * tbn;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(blocks * CM * CN));
+    cfg.blockDim = dim3(NTHREADS);
+    cfg.dynamicSmemBytes = NSTAGE * STAGE_BYTES;
+    cfg.stream = s;
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CM * CN;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = CM * CN > 1 ? 1 : 0;
+    return cfg;
+}
+
+template <int CM, int CN>
+cudaError_t launch_tc(const TcParams& p, const void* Asl, int SA, const void* Xsl, int SB, bool lower, cudaStream_t s) {
+    CUtensorMap ma, mb;
+    if (!make_map(&ma, Asl, p.npad, SA, TM / CN) || !make_map(&mb, Xsl, p.npad, SB, TN / CM))
+        return cudaErrorInvalidValue;
+    auto k = ozaki_tc_kernel<CM, CN>;
+    cudaError_t rc = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, NSTAGE * STAGE_BYTES);
+    if (rc != cudaSuccess) return rc;
+    cudaLaunchAttribute attr[1];
+    const cudaLaunchConfig_t cfg = tc_config<CM, CN>(p, lower, s, attr);
+    return cudaLaunchKernelEx(&cfg, k, ma, mb, p);
+}
+
+// Cluster shape per device: single CTAs by default; SPDINV_TC_CLUSTER=4
+// selects 2 x 2 clusters (each operand tile read from L2 once per two CTAs)
+// where at least 7/8 of the SMs can then hold a CTA (clusters must fit in
+// one GPC).
+bool use_clusters() {
+    static std::mutex mu;
+    static std::map<int, bool> choice;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return false;
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = choice.find(dev);
+    if (it != choice.end()) return it->second;
+    const char* env = std::getenv("SPDINV_TC_CLUSTER");
+    bool ok = env && std::atoi(env) == 4;
+    int sms = 0;
+    if (ok && cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) ok = false;
+    if (ok) {
+        auto k = ozaki_tc_kernel<2, 2>;
+        int clusters = 0;
+        TcParams q{};
+        q.tiles = 64;
+        cudaLaunchAttribute attr[1];
+        const cudaLaunchConfig_t cfg = tc_config<2, 2>(q, false, nullptr, attr);
+        ok = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, NSTAGE * STAGE_BYTES) ==
+                 cudaSuccess &&
+             cudaOccupancyMaxActiveClusters(&clusters, k, &cfg) == cudaSuccess && clusters * 4 * 8 >= sms * 7;
+        cudaGetLastError();  // a refused query is not an error of the caller's
+    }
+    choice[dev] = ok;
+    return ok;
 }
 
 }  // namespace
@@ -399,11 +558,9 @@ bool make_map(CUtensorMap* m, const void* base, int64_t npad, int S) {
 cudaError_t ozaki_products_tc(int64_t n, int64_t npad, const void* Asl, int SA, const void* Xsl, int SB,
                               const int* ps, const int* pt, int npairs, const int* e, const int* f, double* R,
                               const double* base, bool identity, double sign, bool lower, int* err, cudaStream_t s) {
-    if (npad % TM != 0 || npad % 256 != 0 || npairs > 64) return cudaErrorInvalidValue;
+    if (npad % 256 != 0 || npairs > 64) return cudaErrorInvalidValue;  // an even number of 128-row tiles
     for (int q = 0; q < npairs; ++q)  // every pair must address planes that the maps cover
         if (ps[q] < 0 || ps[q] >= SA || pt[q] < 0 || pt[q] >= SB) return cudaErrorInvalidValue;
-    CUtensorMap ma, mb;
-    if (!make_map(&ma, Asl, npad, SA) || !make_map(&mb, Xsl, npad, SB)) return cudaErrorInvalidValue;
     TcParams p{};
     p.n = n;
     p.npad = npad;
@@ -422,12 +579,7 @@ cudaError_t ozaki_products_tc(int64_t n, int64_t npad, const void* Asl, int SA, 
     p.tiles = (int)(npad / TM);
     p.err = err;
     p.timeout_ns = 20LL * 1000000000LL;
-    const int sm = NSTAGE * STAGE_BYTES;
-    cudaError_t rc = cudaFuncSetAttribute(ozaki_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    if (rc != cudaSuccess) return rc;
-    const int grid = lower ? p.tiles * (p.tiles + 1) / 2 : p.tiles * p.tiles;
-    ozaki_tc_kernel<<<(unsigned)grid, NTHREADS, sm, s>>>(ma, mb, p);
-    return cudaGetLastError();
+    return use_clusters() ? launch_tc<2, 2>(p, Asl, SA, Xsl, SB, lower, s) : launch_tc<1, 1>(p, Asl, SA, Xsl, SB, lower, s);
 }
 
 }  // namespace spdinv
