@@ -45,6 +45,9 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-timed", action="store_true",
+                    help="bracket the timed region with cudaProfilerStart/Stop, for "
+                         "ncu --profile-from-start off (warm-up, tuning and set-up launches are then not captured)")
     ap.add_argument("--workload", default="fp64",
                     choices=["fp64", "batched64", "batched32", "backward64", "backward32", "mixed", "residual",
                              "variants"],
@@ -172,6 +175,17 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+PROFILE_TIMED = False
+
+
+def profiler(on):
+    """cudaProfilerStart/Stop around a timed region (--profile-timed)."""
+    if PROFILE_TIMED:
+        import torch
+        torch.cuda.synchronize()
+        (torch.cuda.cudart().cudaProfilerStart if on else torch.cuda.cudart().cudaProfilerStop)()
+
+
 def timed_steps(fn, steps, warmup, stream):
     import torch
     for _ in range(max(warmup, 3)):
@@ -179,11 +193,13 @@ def timed_steps(fn, steps, warmup, stream):
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    profiler(True)
     e0.record(stream)
     for _ in range(steps):
         fn()
     e1.record(stream)
     torch.cuda.synchronize()
+    profiler(False)
     return e0.elapsed_time(e1) / steps
 
 
@@ -413,7 +429,9 @@ def run_secondary(args):
 
 
 def main():
+    global PROFILE_TIMED
     args = parse()
+    PROFILE_TIMED = args.profile_timed
     rank, world, local = dist_env()
     if args.impl == "reference":
         run_reference(args, rank, world)
@@ -470,6 +488,7 @@ def main():
     torch.cuda.synchronize()
     t_start = torch.cuda.Event(enable_timing=True)
     t_end = torch.cuda.Event(enable_timing=True)
+    profiler(True)
     t_start.record(stream)
     for k in range(args.steps):
         A.copy_(A0)
@@ -478,6 +497,7 @@ def main():
         ev[k][1].record(stream)
     t_end.record(stream)
     torch.cuda.synchronize()
+    profiler(False)
     barrier()
     launches = L.spdinv_kernel_launches() - launches0
     clocks = clk.stop()

@@ -222,9 +222,13 @@ SPDINV_API spdinv_status spdinv_potri_noalloc(int64_t n, double* dA, int64_t lda
  *   d_Aptrs           device array of batch device pointers;
  *   d_info            device int[batch] (nullable): per-matrix info as above.
  * The per-size plan (queue order, tile choice) is cached by the exact size
- * list: the first call with a size list uploads it (and may allocate); a
- * later call with the same list queues only the kernel launch and can be
- * captured in a CUDA graph. */
+ * list.  The first call with a size list builds it: it takes the per-class
+ * table of spdinv_batched_tiles capped at each tile size (one kernel holds
+ * the largest tile any matrix uses, which sets the occupancy of all), times
+ * each capped table on a synthetic batch of the same sizes (skipped above
+ * 2 GiB), keeps the fastest and uploads it; this call allocates and
+ * synchronises.  A later call with the same list queues only the kernel
+ * launch and can be captured in a CUDA graph. */
 SPDINV_API spdinv_status spdinv_potri_batched(int batch, const int* h_n, double* const* d_Aptrs,
                                    const int* h_lda, int* d_info, cudaStream_t stream);
 

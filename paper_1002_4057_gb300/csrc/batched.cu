@@ -280,10 +280,15 @@ struct BatchPlan {
     int bmax = 16;
 };
 
+constexpr int kCands = 3;  // candidate tiles 16, 32, 64 (64: FP32 only)
+constexpr int kCandTile[kCands] = {16, 32, 64};
+
 struct BatchState {
     std::mutex mu;
     bool tuned[2] = {false, false};
+    bool forced[2] = {false, false};        // one tile from SPDINV_BATCHED_TILE
     int tiles[2][kClasses];
+    float ms[2][kClasses][kCands];          // per-class timings of each candidate (1e30: not run)
     std::map<std::vector<int>, BatchPlan> plans[2];
 };
 
@@ -316,6 +321,7 @@ cudaError_t autotune(BatchState& bs, int num_sms, int* tiles) {
         if (b == 16 || b == 32 || (b == 64 && fp == 1)) {
             for (int c = 0; c < kClasses; ++c) bs.tiles[fp][c] = b;
             bs.tuned[fp] = true;
+            bs.forced[fp] = true;
             std::memcpy(tiles, bs.tiles[fp], sizeof(int) * kClasses);
             return cudaSuccess;
         }
@@ -345,6 +351,7 @@ cudaError_t autotune(BatchState& bs, int num_sms, int* tiles) {
         e = cudaMemcpy(ptrs, hp.data(), sizeof(T*) * count, cudaMemcpyHostToDevice);
         float best = 1e30f;
         int bestb = cands[0];
+        for (int k = 0; k < kCands; ++k) bs.ms[fp][c][k] = 1e30f;
         for (int b : cands) {
             if (e != cudaSuccess) break;
             for (int q = 0; q < count; ++q) hints[3 * count + q] = b;
@@ -363,6 +370,7 @@ cudaError_t autotune(BatchState& bs, int num_sms, int* tiles) {
                 cudaEventElapsedTime(&ms, e0, e1);
                 if (rep > 0) ms_min = std::min(ms_min, ms);
             }
+            bs.ms[fp][c][b == 16 ? 0 : (b == 32 ? 1 : 2)] = ms_min;
             if (ms_min < best) {
                 best = ms_min;
                 bestb = b;
@@ -379,6 +387,116 @@ cudaError_t autotune(BatchState& bs, int num_sms, int* tiles) {
     bs.tuned[fp] = true;
     std::memcpy(tiles, bs.tiles[fp], sizeof(int) * kClasses);
     return cudaSuccess;
+}
+
+// Fills matrix k of a batch (order n[k], leading dimension n[k]) with a
+// diagonally dominant (hence SPD) test matrix, one CTA per matrix.
+template <typename T>
+__global__ void fill_tuning_mats(T* const* ptrs, const int* n, int batch) {
+    for (int k = blockIdx.x; k < batch; k += gridDim.x) {
+        const int m = n[k];
+        T* A = ptrs[k];
+        for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+            const int r = e % m, c = e / m;
+            uint32_t h = (uint32_t)(min(r, c) * 73856093u) ^ (uint32_t)(max(r, c) * 19349663u) ^ (uint32_t)k;
+            h ^= h >> 13;
+            h *= 0x5bd1e995u;
+            h ^= h >> 15;
+            A[e] = r == c ? (T)m : (T)((h & 0xFFFF) / 65536.0 - 0.5);
+        }
+    }
+}
+
+// The per-class table when every tile is at most `cap`: the fastest tile of
+// each class among those (one persistent kernel holds the largest tile any
+// matrix uses, and its shared memory and registers set the occupancy of all).
+int capped_tiles(const BatchState& bs, int fp, int cap, int* out) {
+    int bmax = 16;
+    for (int c = 0; c < kClasses; ++c) {
+        if (bs.forced[fp]) {
+            out[c] = bs.tiles[fp][c];
+        } else {
+            int best = 0;
+            for (int k = 1; k < kCands; ++k)
+                if (kCandTile[k] <= cap && bs.ms[fp][c][k] < bs.ms[fp][c][best]) best = k;
+            out[c] = kCandTile[best];
+        }
+        bmax = std::max(bmax, out[c]);
+    }
+    return bmax;
+}
+
+// Whole-batch plan tuning: the per-class tables capped at 64, 32 and 16 are
+// each timed on a synthetic batch with the caller's sizes; the fastest wins.
+// Returns the chosen table in `tiles`.  Skipped (first table kept) when the
+// synthetic copy would exceed 2 GiB.
+template <typename T>
+cudaError_t tune_plan(const BatchState& bs, int fp, int batch, const int* h_n, const std::vector<int>& order,
+                      int num_sms, int* tiles) {
+    std::vector<std::vector<int>> tables;
+    for (int cap : {64, 32, 16}) {
+        if (fp == 0 && cap == 64) continue;
+        std::vector<int> t(kClasses);
+        capped_tiles(bs, fp, cap, t.data());
+        if (std::find(tables.begin(), tables.end(), t) == tables.end()) tables.push_back(t);
+    }
+    std::copy(tables[0].begin(), tables[0].end(), tiles);
+    size_t elems = 0;
+    for (int k = 0; k < batch; ++k) elems += (size_t)h_n[k] * h_n[k];
+    if (tables.size() < 2 || elems * sizeof(T) > (size_t(2) << 30)) return cudaSuccess;
+    T* data = nullptr;
+    T** ptrs = nullptr;
+    int* ints = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaMalloc(&data, sizeof(T) * std::max<size_t>(elems, 1));
+    if (e == cudaSuccess) e = cudaMalloc(&ptrs, sizeof(T*) * batch);
+    if (e == cudaSuccess) e = cudaMalloc(&ints, sizeof(int) * (4 * (size_t)batch + 1));
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    std::vector<T*> hp(batch);
+    std::vector<int> h(4 * (size_t)batch);
+    size_t off = 0;
+    for (int k = 0; k < batch; ++k) {
+        hp[k] = data + off;
+        off += (size_t)h_n[k] * h_n[k];
+        h[k] = h_n[k];
+        h[batch + k] = std::max(h_n[k], 1);
+        h[2 * batch + k] = order[k];
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(ptrs, hp.data(), sizeof(T*) * batch, cudaMemcpyHostToDevice);
+    float best = 1e30f;
+    for (const auto& t : tables) {
+        if (e != cudaSuccess) break;
+        int bmax = 16;
+        for (int k = 0; k < batch; ++k) {
+            h[3 * batch + k] = t[size_class(h_n[k])];
+            bmax = std::max(bmax, h[3 * batch + k]);
+        }
+        e = cudaMemcpy(ints, h.data(), sizeof(int) * 4 * batch, cudaMemcpyHostToDevice);
+        BatchParams<T> p{batch, ints + 2 * batch, ints, ints + batch, ints + 3 * batch, ptrs, nullptr, ints + 4 * batch};
+        float ms_min = 1e30f;
+        for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
+            fill_tuning_mats<T><<<std::min(batch, 4 * num_sms), 256>>>(ptrs, ints, batch);
+            cudaMemset(ints + 4 * batch, 0, sizeof(int));
+            cudaEventRecord(e0);
+            e = launch_batched<T>(p, bmax, num_sms, 0);
+            cudaEventRecord(e1);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            ms_min = std::min(ms_min, ms);
+        }
+        if (e == cudaSuccess && ms_min < best) {
+            best = ms_min;
+            std::copy(t.begin(), t.end(), tiles);
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(data);
+    cudaFree(ptrs);
+    cudaFree(ints);
+    return e;
 }
 
 template <typename T>
@@ -409,6 +527,8 @@ spdinv_status run_batched(int batch, const int* h_n, T* const* d_Aptrs, const in
         std::vector<int> order(batch);
         std::iota(order.begin(), order.end(), 0);
         std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return h_n[a] > h_n[b]; });
+        e = tune_plan<T>(bs, fp, batch, h_n, order, num_sms, tiles);
+        if (e != cudaSuccess) return cuda_fail(e);
         int bmax = 16;
         for (int k = 0; k < batch; ++k) {
             h[k] = h_n[k];

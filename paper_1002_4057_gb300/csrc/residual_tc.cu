@@ -27,8 +27,6 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
-#include <cstdlib>
-#include <map>
 #include <mutex>
 
 #include "api_internal.h"
@@ -39,7 +37,7 @@ namespace spdinv {
 namespace {
 
 constexpr int TM = 128, TN = 128, TK = 64;  // output tile; K per stage = one 128-byte swizzle row of bf16
-constexpr int NSTAGE = 6;  // 1.5 exact chunks in flight: the copies run ahead of the MMAs
+constexpr int NSTAGE = 6;  // 1.5 exact 256-deep chunks' worth of copies run ahead of the MMAs
 constexpr int A_BYTES = TM * TK * 2, B_BYTES = TN * TK * 2, STAGE_BYTES = A_BYTES + B_BYTES;
 constexpr int CHUNK_STAGES = 1024 / TK;  // exact FP32 chunk: 1024 products of balanced 8-bit digits (<= 2^24)
 constexpr int TMEM_COLS = 512;          // two 128-column FP32 accumulators + INT64 level sums (256 columns)
@@ -92,52 +90,6 @@ __device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t da, uint64_t
 __device__ __forceinline__ void umma_commit(uint64_t* bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                  : "memory");
-}
-
-// ---- thread-block clusters: operand tiles shared by TMA multicast ----------
-// A cluster of CM x CN CTAs computes a CM x CN block of output tiles.  The CN
-// CTAs of one block row need the same A tile: each loads 1/CN of its rows
-// and multicasts them to all CN.  Likewise the CM CTAs of one block column
-// share the B tile, 1/CM of its rows each.  A stage of a CTA's ring is thus
-// written by CM + CN - 1 CTAs (itself included), and each of them may reuse
-// the stage only after this CTA's MMAs have read it: the MMA issuer's commit
-// arrives on the `empty` barrier of every one of those CTAs.
-
-__device__ __forceinline__ uint32_t cluster_ctarank() {
-    uint32_t r;
-    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-    return r;
-}
-
-// Every thread of every CTA in the cluster; orders the CTAs' shared-memory
-// writes (barrier initialisation) before the peers' later accesses.
-__device__ __forceinline__ void cluster_sync_all() {
-    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-
-__device__ __forceinline__ void fence_mbarrier_init_cluster() {
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-
-// TMA load whose bytes land, and count, at the same shared-memory offsets in
-// every CTA of `mask`.
-__device__ __forceinline__ void tma_load_2d_mc(void* dst, const CUtensorMap* tm, int x, int y, uint64_t* bar,
-                                               uint16_t mask) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster"
-        " [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(smem_u32(dst)),
-        "l"(reinterpret_cast<uint64_t>(tm)), "r"(x), "r"(y), "r"(smem_u32(bar)), "h"(mask)
-        : "memory");
-}
-
-// Arrive on the mbarrier at this offset in every CTA of `mask` once the MMAs
-// issued so far have completed.
-__device__ __forceinline__ void umma_commit_mc(uint64_t* bar, uint16_t mask) {
-    asm volatile(
-        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
-            smem_u32(bar)),
-        "h"(mask)
-        : "memory");
 }
 
 // 2^x as a double, exactly, for |x| < 1022.
@@ -227,10 +179,10 @@ __device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity, volatil
     }
 }
 
-// Block (bm, bn) of a tb_m x tb_n block grid for launch index `pid`, in a
-// grouped raster: GROUP block rows are swept column by column, so the
-// clusters resident at one time share both operands' slices in L2.  With
-// `lower` only the blocks with bm >= bn (tb_m == tb_n): in the group of rows
+// Tile (bm, bn) of a tb_m x tb_n tile grid for launch index `pid`, in a
+// grouped raster: GROUP tile rows are swept column by column, so the CTAs
+// resident at one time share both operands' slices in L2.  With `lower`
+// only the tiles with bm >= bn (tb_m == tb_n): in the group of rows
 // [first, first + gm), column c holds the rows r >= c.
 __device__ __forceinline__ void block_of(int pid, int tb_m, int tb_n, bool lower, int& bm, int& bn) {
     constexpr int GROUP = 16;
@@ -266,28 +218,18 @@ __device__ __forceinline__ void block_of(int pid, int tb_m, int tb_n, bool lower
     }
 }
 
-template <int CM, int CN>
 __global__ void __launch_bounds__(NTHREADS, 1)
     ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                    const TcParams p) {
-    constexpr int CL = CM * CN;
-    constexpr int A_PART = A_BYTES / CN, B_PART = B_BYTES / CM;  // bytes each CTA loads per stage
+                    const __grid_constant__ TcParams p) {
     unsigned char* smem = dynamic_smem();  // 1024-byte aligned (swizzled operand tiles)
     __shared__ __align__(8) uint64_t full[NSTAGE], empty[NSTAGE], accf[2], acce[2], fin;
     __shared__ uint32_t tmem_slot;
     __shared__ volatile int s_abort;
     __shared__ int s_f[TN];
+    __shared__ int s_ya[64], s_yb[64];  // per pair: row of the A and X slice planes' tiles
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // This CTA's place (dm, dn) in its cluster's CM x CN block of tiles.
-    const int rank = CL > 1 ? (int)cluster_ctarank() : 0;
-    const int dm = rank % CM, dn = rank / CM;
-    uint16_t maskA = 0, maskB = 0;  // the CTAs sharing this CTA's A tile (its block row) / B tile
-    for (int q = 0; q < CN; ++q) maskA |= (uint16_t)(1u << (dm + CM * q));
-    for (int q = 0; q < CM; ++q) maskB |= (uint16_t)(1u << (q + CM * dn));
-    const uint16_t maskE = maskA | maskB;  // the CTAs whose copies land in this CTA's ring
-    int bm, bn;
-    block_of((int)(blockIdx.x / CL), p.tiles / CM, p.tiles / CN, p.lower != 0, bm, bn);
-    const int tile_m = bm * CM + dm, tile_n = bn * CN + dn;
+    int tile_m, tile_n;
+    block_of((int)blockIdx.x, p.tiles, p.tiles, p.lower != 0, tile_m, tile_n);
     const int64_t m0 = (int64_t)tile_m * TM, n0 = (int64_t)tile_n * TN;
     const int kstages = (int)(p.npad / TK);            // stages per slice pair
     const int chunks_per_pair = (kstages + CHUNK_STAGES - 1) / CHUNK_STAGES;  // the last one may be shorter
@@ -297,7 +239,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     if (threadIdx.x == 0) {
         for (int s = 0; s < NSTAGE; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&empty[s], CM + CN - 1);  // one release per CTA that writes into this ring
+            mbar_init(&empty[s], 1);
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&accf[b], 1);
@@ -306,9 +248,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         mbar_init(&fin, 1);
         s_abort = 0;
         fence_proxy_async_shared();
-        if (CL > 1) fence_mbarrier_init_cluster();
     }
     for (int j = threadIdx.x; j < TN; j += NTHREADS) s_f[j] = (n0 + j < p.n) ? p.f[n0 + j] : 0;
+    for (int q = threadIdx.x; q < p.npairs; q += NTHREADS) {
+        s_ya[q] = (int)(p.ps[q] * p.npad + m0);
+        s_yb[q] = (int)(p.pt[q] * p.npad + n0);
+    }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
                      "r"(TMEM_COLS)
@@ -317,7 +262,6 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     }
     tc_fence_before();
     cta_sync();
-    if (CL > 1) cluster_sync_all();  // the peers' barriers exist before any copy or release targets them
     tc_fence_after();
     const uint32_t tmem = tmem_slot;
 
@@ -329,20 +273,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 if (!wait_bar(&empty[s], ((it / NSTAGE) & 1) ^ 1, &s_abort, p)) break;
                 const int pair = it / kstages, kt = it - pair * kstages;
                 unsigned char* st = smem + s * STAGE_BYTES;
-                mbar_arrive_expect_tx(&full[s], STAGE_BYTES);  // the whole stage, whoever copies it
-                const int ya = (int)(p.ps[pair] * p.npad + m0) + dn * (TM / CN);
-                const int yb = (int)(p.pt[pair] * p.npad + n0) + dm * (TN / CM);
-                if (CN > 1) tma_load_2d_mc(st + dn * A_PART, &tmA, kt * TK, ya, &full[s], maskA);
-                else tma_load_2d(st, &tmA, kt * TK, ya, &full[s]);
-                if (CM > 1) tma_load_2d_mc(st + A_BYTES + dm * B_PART, &tmB, kt * TK, yb, &full[s], maskB);
-                else tma_load_2d(st + A_BYTES, &tmB, kt * TK, yb, &full[s]);
+                mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
+                tma_load_2d(st, &tmA, kt * TK, s_ya[pair], &full[s]);
+                tma_load_2d(st + A_BYTES, &tmB, kt * TK, s_yb[pair], &full[s]);
             }
             if (s_abort)  // let the copies already issued land before the CTA leaves
                 for (int k = it - NSTAGE > 0 ? it - NSTAGE : 0; k < it; ++k)
                     drain_bar(&full[k % NSTAGE], (k / NSTAGE) & 1, 200000000LL);
-            if (CL > 1)  // every CTA that shares this ring has released its last stages
-                for (int k = it; k < it + NSTAGE; ++k)
-                    drain_bar(&empty[k % NSTAGE], ((k / NSTAGE) & 1) ^ 1, 200000000LL);
         }
     } else if (warp == 1) {
         if (lane == 0) {  // ---- MMA issuer
@@ -367,8 +304,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll
                     for (int k = 0; k < TK / 16; ++k)  // +32 bytes per K=16 inside the swizzle row
                         umma_bf16(d, da + 2 * k, db + 2 * k, (q | k) != 0);
-                    if (CL > 1) umma_commit_mc(&empty[s], maskE);
-                    else umma_commit(&empty[s]);
+                    umma_commit(&empty[s]);
                 }
                 if (!ok) break;
                 umma_commit(&accf[b]);
@@ -456,7 +392,6 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     }
     tc_fence_before();
     cta_sync();
-    if (CL > 1) cluster_sync_all();  // no peer copies into, or releases on, a CTA that has left
     tc_fence_after();
     if (warp == 1) {
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
@@ -490,75 +425,12 @@ bool make_map(CUtensorMap* m, const void* base, int64_t npad, int S, int rows) {
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int CM, int CN>
-cudaLaunchConfig_t tc_config(const TcParams& p, bool lower, cudaStream_t s, cudaLaunchAttribute* attr) {
-    const int tbm = p.tiles / CM, tbn = p.tiles / CN;
-    const int blocks = lower ? tbm * (tbm + 1) / 2 : tbm * tbn;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)(blocks * CM * CN));
-    cfg.blockDim = dim3(NTHREADS);
-    cfg.dynamicSmemBytes = NSTAGE * STAGE_BYTES;
-    cfg.stream = s;
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = CM * CN;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = CM * CN > 1 ? 1 : 0;
-    return cfg;
-}
-
-template <int CM, int CN>
-cudaError_t launch_tc(const TcParams& p, const void* Asl, int SA, const void* Xsl, int SB, bool lower, cudaStream_t s) {
-    CUtensorMap ma, mb;
-    if (!make_map(&ma, Asl, p.npad, SA, TM / CN) || !make_map(&mb, Xsl, p.npad, SB, TN / CM))
-        return cudaErrorInvalidValue;
-    auto k = ozaki_tc_kernel<CM, CN>;
-    cudaError_t rc = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, NSTAGE * STAGE_BYTES);
-    if (rc != cudaSuccess) return rc;
-    cudaLaunchAttribute attr[1];
-    const cudaLaunchConfig_t cfg = tc_config<CM, CN>(p, lower, s, attr);
-    return cudaLaunchKernelEx(&cfg, k, ma, mb, p);
-}
-
-// Cluster shape per device: single CTAs by default; SPDINV_TC_CLUSTER=4
-// selects 2 x 2 clusters (each operand tile read from L2 once per two CTAs)
-// where at least 7/8 of the SMs can then hold a CTA (clusters must fit in
-// one GPC).
-bool use_clusters() {
-    static std::mutex mu;
-    static std::map<int, bool> choice;
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return false;
-    std::lock_guard<std::mutex> lk(mu);
-    auto it = choice.find(dev);
-    if (it != choice.end()) return it->second;
-    const char* env = std::getenv("SPDINV_TC_CLUSTER");
-    bool ok = env && std::atoi(env) == 4;
-    int sms = 0;
-    if (ok && cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) ok = false;
-    if (ok) {
-        auto k = ozaki_tc_kernel<2, 2>;
-        int clusters = 0;
-        TcParams q{};
-        q.tiles = 64;
-        cudaLaunchAttribute attr[1];
-        const cudaLaunchConfig_t cfg = tc_config<2, 2>(q, false, nullptr, attr);
-        ok = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, NSTAGE * STAGE_BYTES) ==
-                 cudaSuccess &&
-             cudaOccupancyMaxActiveClusters(&clusters, k, &cfg) == cudaSuccess && clusters * 4 * 8 >= sms * 7;
-        cudaGetLastError();  // a refused query is not an error of the caller's
-    }
-    choice[dev] = ok;
-    return ok;
-}
-
 }  // namespace
 
 cudaError_t ozaki_products_tc(int64_t n, int64_t npad, const void* Asl, int SA, const void* Xsl, int SB,
                               const int* ps, const int* pt, int npairs, const int* e, const int* f, double* R,
                               const double* base, bool identity, double sign, bool lower, int* err, cudaStream_t s) {
-    if (npad % 256 != 0 || npairs > 64) return cudaErrorInvalidValue;  // an even number of 128-row tiles
+    if (npad % 256 != 0 || npairs < 1 || npairs > 64) return cudaErrorInvalidValue;  // whole 256-deep chunks
     for (int q = 0; q < npairs; ++q)  // every pair must address planes that the maps cover
         if (ps[q] < 0 || ps[q] >= SA || pt[q] < 0 || pt[q] >= SB) return cudaErrorInvalidValue;
     TcParams p{};
@@ -579,7 +451,14 @@ cudaError_t ozaki_products_tc(int64_t n, int64_t npad, const void* Asl, int SA, 
     p.tiles = (int)(npad / TM);
     p.err = err;
     p.timeout_ns = 20LL * 1000000000LL;
-    return use_clusters() ? launch_tc<2, 2>(p, Asl, SA, Xsl, SB, lower, s) : launch_tc<1, 1>(p, Asl, SA, Xsl, SB, lower, s);
+    CUtensorMap ma, mb;
+    if (!make_map(&ma, Asl, npad, SA, TM) || !make_map(&mb, Xsl, npad, SB, TN)) return cudaErrorInvalidValue;
+    const int sm = NSTAGE * STAGE_BYTES;
+    cudaError_t rc = cudaFuncSetAttribute(ozaki_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    if (rc != cudaSuccess) return rc;
+    const int grid = lower ? p.tiles * (p.tiles + 1) / 2 : p.tiles * p.tiles;
+    ozaki_tc_kernel<<<(unsigned)grid, NTHREADS, sm, s>>>(ma, mb, p);
+    return cudaGetLastError();
 }
 
 }  // namespace spdinv

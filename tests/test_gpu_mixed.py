@@ -3,8 +3,6 @@ residual corrections, against the FP64 oracle.  The error is stated for every
 result; the 1e-10 gate applies with the number of correction steps and the
 order the conditioning needs (order 2: one step at cond 1e2, two at 1e4;
 one step of order 3 at cond 1e2 and of order 4 at cond 1e4)."""
-import os
-
 import numpy as np
 import pytest
 
@@ -14,8 +12,6 @@ import spd_inputs as si
 from gpu_util import full_from_lower, lower_np, to_dev
 
 pytestmark = pytest.mark.gpu
-
-ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 MIXED = 1
 
@@ -198,40 +194,3 @@ def test_mixed_emulated_matches_native_residual(gpu, n):
     print("n=%d errors emulated(tcgen05) %.2e native %.2e emulated(mma.sync) %.2e" % (n, errs[0], errs[1], errs[2]))
     assert errs[0] <= 1e-10 and errs[1] <= 1e-10 and errs[2] <= 1e-10
 
-
-def test_clustered_slice_products_are_bitwise_equal(gpu):
-    """The 2 x 2 cluster arrangement of the tcgen05 slice products (operand
-    tiles shared by TMA multicast; opted into with SPDINV_TC_CLUSTER=4) runs
-    every output tile's arithmetic in the same order as single CTAs, so R is
-    bitwise the same.  Run in child processes: the shape is chosen once per
-    process and device."""
-    import subprocess
-    import sys
-    import tempfile
-    code = r'''
-import sys, numpy as np, torch
-sys.path.insert(0, %r)
-import spd_inputs as si
-from paper_1002_4057_gb300 import _lib as L
-n = 1000
-A, _, _ = si.spectral_spd(n, 1e3, seed=77)
-X = np.linalg.inv(A).astype(np.float32).astype(np.float64)
-X = 0.5 * (X + X.T)
-dA = torch.from_numpy(np.asfortranarray(A)).cuda()
-dX = torch.from_numpy(np.asfortranarray(X)).cuda()
-dR = torch.zeros((n, n), dtype=torch.float64, device="cuda").t()
-assert L.spdinv_inverse_residual(n, dA.data_ptr(), n, dX.data_ptr(), dR.data_ptr(), 0,
-                                 torch.cuda.current_stream().cuda_stream) == 0
-torch.cuda.synchronize()
-np.save(sys.argv[1], dR.cpu().numpy())
-''' % ROOT
-    outs = []
-    with tempfile.TemporaryDirectory() as d:
-        for shape in ("1", "4"):
-            path = "%s/r%s.npy" % (d, shape)
-            env = dict(os.environ, SPDINV_TC_CLUSTER=shape)
-            r = subprocess.run([sys.executable, "-c", code, path], env=env, capture_output=True, text=True,
-                               timeout=600)
-            assert r.returncode == 0, r.stderr[-2000:]
-            outs.append(np.load(path))
-    assert np.array_equal(outs[0], outs[1])
