@@ -42,9 +42,11 @@ def parse():
     ap.add_argument("--tile", type=int, default=64)
     ap.add_argument("--ctas-per-sm", type=int, default=0)
     ap.add_argument("--cond", type=float, default=1e4)
-    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--conds", default="1e2,1e4,1e6",
+                    help="mixed workload: the condition numbers studied (comma list)")
     ap.add_argument("--profile-timed", action="store_true",
                     help="bracket the timed region with cudaProfilerStart/Stop, for "
                          "ncu --profile-from-start off (warm-up, tuning and set-up launches are then not captured)")
@@ -186,9 +188,9 @@ def profiler(on):
         (torch.cuda.cudart().cudaProfilerStart if on else torch.cuda.cudart().cudaProfilerStop)()
 
 
-def timed_steps(fn, steps, warmup, stream):
+def timed_steps(fn, steps, warmup, stream, min_warmup=3):
     import torch
-    for _ in range(max(warmup, 3)):
+    for _ in range(max(warmup, min_warmup)):
         fn()
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
@@ -219,10 +221,12 @@ def run_mixed_study(args, dev, stream):
     cols = np.array([0, n // 3, n - 1])
     flops = float(n) ** 3
     out = []
+    # one FP64 inversion takes ~33 s at n = 32768: fewer untimed runs there
+    mw = 3 if n <= 16384 else 1
     schedules = {1e2: ((0, 2), (1, 2), (2, 2), (1, 3), (1, 4)),
                  1e4: ((0, 2), (1, 2), (2, 2), (1, 3), (1, 4), (1, 5)),
                  1e6: ((0, 2), (1, 4), (2, 2), (3, 2), (4, 2), (2, 3), (2, 4))}
-    for cond in (1e2, 1e4, 1e6):
+    for cond in [float(c) for c in args.conds.split(",")]:
         A, Q, lam = si.spectral_spd(n, cond, seed=si.SEED_BASE + 2, device=dev)
         ref = cf.spectral_inverse_columns(Q.cpu().numpy(), lam, cols)
         del Q
@@ -238,14 +242,14 @@ def run_mixed_study(args, dev, stream):
             W.copy_(A)
             T.potri_(W, info=info, tile=64)
 
-        ms64 = timed_steps(fp64, 1, 1, stream)
+        ms64 = timed_steps(fp64, 1, 1, stream, mw)
         e64 = err_of(W)
         rec = {"cond": cond, "fp64_ms": round(ms64, 1), "fp64_err": e64, "mixed": []}
         for k, order in schedules[cond]:
             def mixed():
                 W.copy_(A)
                 T.potri_(W, info=info, tile=64, precision=1, refine_steps=k, refine_order=order)
-            ms = timed_steps(mixed, 1, 1, stream)
+            ms = timed_steps(mixed, 1, 1, stream, mw)
             assert int(info.item()) == 0
             e = err_of(W)
             rec["mixed"].append({"steps": k, "order": order if k else None, "ms": round(ms, 1), "err": e,
@@ -512,40 +516,69 @@ def main():
     flops = float(n) ** 3
     value = world * flops / (ms_per_step * 1e-3) / 1e9  # Gflop/s, all ranks
 
-    # ---- end to end through the public API, host buffers (pinned)
+    # ---- end to end through the public API, host buffers (pinned).  Every
+    # step copies its input host->device and its result device->host.  Two
+    # device buffers and a copy stream pipeline the steps: the copies of step
+    # k+1's input and of step k-1's result run while step k inverts, as a
+    # serving loop would (copies after a multi-second kernel measured ~9 GB/s
+    # on this host, so unoverlapped they would add ~0.45 s per step).
     e2e = None
     if not args.no_e2e:
+        K = max(args.e2e_steps, 1)
         hA = torch.empty((n * n,), dtype=torch.float64, pin_memory=True)
         hA.copy_(A0.t().contiguous().reshape(-1))  # column-major flattening of A0
-        hOut = torch.empty_like(hA)
-        dA = torch.empty((n * n,), dtype=torch.float64, device=dev)
-        dview = dA.as_strided((n, n), (1, n))
+        hOut = [torch.empty((n * n,), dtype=torch.float64, pin_memory=True) for _ in range(2)]
+        dbuf = [torch.empty((n * n,), dtype=torch.float64, device=dev) for _ in range(2)]
+        views = [d.as_strided((n, n), (1, n)) for d in dbuf]
+        cp = torch.cuda.Stream(device=dev)
+        infos = [torch.zeros(1, dtype=torch.int32, device=dev) for _ in range(2)]
 
-        def e2e_step():
-            dA.copy_(hA, non_blocking=True)
-            T.potri_(dview, info=info, tile=b, ctas_per_sm=args.ctas_per_sm)
-            hOut.copy_(dA, non_blocking=True)
+        def e2e_run(steps):
+            h2d = [torch.cuda.Event() for _ in range(2)]
+            inv = [torch.cuda.Event() for _ in range(2)]
+            d2h = [None, None]
+            with torch.cuda.stream(cp):
+                dbuf[0].copy_(hA, non_blocking=True)
+                h2d[0].record(cp)
+            for k in range(steps):
+                b_ = k % 2
+                stream.wait_event(h2d[b_])
+                T.potri_(views[b_], info=infos[b_], tile=b, ctas_per_sm=args.ctas_per_sm)
+                inv[b_].record(stream)
+                with torch.cuda.stream(cp):
+                    if k + 1 < steps:  # next input into the other buffer, once its last result is out
+                        o = (k + 1) % 2
+                        if d2h[o] is not None:
+                            cp.wait_event(d2h[o])
+                        dbuf[o].copy_(hA, non_blocking=True)
+                        h2d[o].record(cp)
+                    cp.wait_event(inv[b_])
+                    hOut[b_].copy_(dbuf[b_], non_blocking=True)
+                    d2h[b_] = torch.cuda.Event()
+                    d2h[b_].record(cp)
+            stream.wait_stream(cp)
 
-        e2e_step()
+        e2e_run(1)
         torch.cuda.synchronize()
         barrier()
         s0 = torch.cuda.Event(enable_timing=True)
         s1 = torch.cuda.Event(enable_timing=True)
         s0.record(stream)
-        for _ in range(args.e2e_steps):
-            e2e_step()
+        e2e_run(K)
         s1.record(stream)
         torch.cuda.synchronize()
-        e2e_ms = s0.elapsed_time(s1) / args.e2e_steps
+        e2e_ms = s0.elapsed_time(s1) / K
         if world > 1:
             tt = torch.tensor([e2e_ms], device=dev)
             dist.all_reduce(tt, op=dist.ReduceOp.MAX)
             e2e_ms = float(tt.item())
-        assert int(info.item()) == 0
+        assert int(infos[0].item()) == 0 and int(infos[1].item()) == 0
         e2e = {"value": round(world * flops / (e2e_ms * 1e-3) / 1e9, 3), "unit": "Gflop/s",
                "h2d_bytes_per_step": n * n * 8, "d2h_bytes_per_step": n * n * 8,
-               "ms_per_step": round(e2e_ms, 3), "steps": args.e2e_steps}
-        del hA, hOut, dA
+               "ms_per_step": round(e2e_ms, 3), "steps": K,
+               "pipeline": "pinned host buffers; input and result copies on a second stream overlap the "
+                           "neighbouring steps' inversions (two device buffers)"}
+        del hA, hOut, dbuf, views
 
     peaks, src = measured_peaks()
     peak_tf = peaks["bf16_tflops"] * FP64_NOMINAL_TFLOPS / BF16_NOMINAL_TFLOPS

@@ -79,10 +79,66 @@ __device__ __forceinline__ void gstore(T* A, int n, int64_t lda, int ti, int tj,
     }
 }
 
+// The next tile of a chain of products.  For tiles of at most 8 elements per
+// thread (b <= 32) the thread's elements are read into registers while the
+// current product runs and placed in shared memory after it; larger tiles
+// (b = 64, 32 elements per thread) would take the registers the product
+// needs, so they keep only the tile's position and are read when placed.
+template <typename T, int B, bool Staged = (B * B / kThreads <= 8)>
+struct TileRegs {
+    static constexpr int N = B * B / kThreads;
+    T v[N];
+};
+template <typename T, int B>
+struct TileRegs<T, B, false> {
+    const T* A;
+    int n;
+    int64_t lda;
+    int ti, tj;
+};
+
+// Thread t holds row t % B of the tile at columns t / B + q (kThreads / B),
+// q = 0 .. N-1 (kThreads is a multiple of B): one pointer and one stride.
+template <typename T, int B, bool S>
+__device__ __forceinline__ void fetch(const T* A, int n, int64_t lda, int ti, int tj, TileRegs<T, B, S>& r) {
+    if constexpr (S) {
+        constexpr int CS = kThreads / B;
+        const int rr = threadIdx.x % B, c0 = threadIdx.x / B;
+        const int gr = ti * B + rr, gc0 = tj * B + c0;
+        const T* src = A + gr + (int64_t)gc0 * lda;
+        const int64_t step = (int64_t)CS * lda;
+#pragma unroll
+        for (int q = 0; q < TileRegs<T, B, S>::N; ++q) {
+            const bool in = gr < n && gc0 + q * CS < n;
+            r.v[q] = in ? src[q * step] : ((ti == tj && rr == c0 + q * CS) ? T(1) : T(0));
+        }
+    } else {
+        r.A = A;
+        r.n = n;
+        r.lda = lda;
+        r.ti = ti;
+        r.tj = tj;
+    }
+}
+
+template <typename T, int B, bool S>
+__device__ __forceinline__ void place(const TileRegs<T, B, S>& r, T* Sm) {
+    if constexpr (S) {
+        constexpr int LD = Tile<T, B>::LD, CS = kThreads / B;
+        T* dst = Sm + (threadIdx.x / B) * LD + threadIdx.x % B;
+#pragma unroll
+        for (int q = 0; q < TileRegs<T, B, S>::N; ++q) dst[q * CS * LD] = r.v[q];
+    } else {
+        gload<T, B>(r.A, r.n, r.lda, r.ti, r.tj, Sm, false);
+    }
+}
+
 // Algorithm 1 on one matrix, in place.  Returns LAPACK's info.
 template <typename T, int B>
 __device__ int run_matrix(T* A, int n, int64_t lda, T* S0, T* S1, T* tmp, int* s_fail) {
+    static_assert(B * B % kThreads == 0 && kThreads % B == 0, "whole tiles per thread");
     typename Tile<T, B>::Acc acc;
+    TileRegs<T, B> r0, r1;
     const int t = (n + B - 1) / B;
     // ---- Step 1: tile Cholesky (left-looking, k increasing)
     for (int j = 0; j < t; ++j) {
@@ -90,10 +146,12 @@ __device__ int run_matrix(T* A, int n, int64_t lda, T* S0, T* S1, T* tmp, int* s
         gload<T, B>(A, n, lda, j, j, S0, true);
         cta_sync();
         acc_load<B>(acc, S0);
+        if (j > 0) fetch<T, B>(A, n, lda, j, 0, r0);
         for (int k = 0; k < j; ++k) {  // SYRK
             cta_sync();
-            gload<T, B>(A, n, lda, j, k, S1, false);
+            place<T, B>(r0, S1);
             cta_sync();
+            if (k + 1 < j) fetch<T, B>(A, n, lda, j, k + 1, r0);
             tile_mma<B, false, true, true, FULL, FULL>(acc, S1, S1);
         }
         cta_sync();
@@ -108,11 +166,19 @@ __device__ int run_matrix(T* A, int n, int64_t lda, T* S0, T* S1, T* tmp, int* s
             gload<T, B>(A, n, lda, i, j, S0, false);
             cta_sync();
             acc_load<B>(acc, S0);
+            if (j > 0) {
+                fetch<T, B>(A, n, lda, i, 0, r0);
+                fetch<T, B>(A, n, lda, j, 0, r1);
+            }
             for (int k = 0; k < j; ++k) {  // GEMM
                 cta_sync();
-                gload<T, B>(A, n, lda, i, k, S0, false);
-                gload<T, B>(A, n, lda, j, k, S1, false);
+                place<T, B>(r0, S0);
+                place<T, B>(r1, S1);
                 cta_sync();
+                if (k + 1 < j) {
+                    fetch<T, B>(A, n, lda, i, k + 1, r0);
+                    fetch<T, B>(A, n, lda, j, k + 1, r1);
+                }
                 tile_mma<B, false, true, true, FULL, FULL>(acc, S0, S1);
             }
             cta_sync();  // TRSM as the product with X_jj^T
@@ -136,11 +202,19 @@ __device__ int run_matrix(T* A, int n, int64_t lda, T* S0, T* S1, T* tmp, int* s
             cta_sync();
             acc_zero<B>(acc);
             tile_mma<B, false, false, false, LOWER, FULL>(acc, S0, S1);  // TRMM
-            for (int k = i - 1; k > j; --k) {                           // GEMM
+            if (i - 1 > j) {
+                fetch<T, B>(A, n, lda, i, i - 1, r0);
+                fetch<T, B>(A, n, lda, i - 1, j, r1);
+            }
+            for (int k = i - 1; k > j; --k) {  // GEMM
                 cta_sync();
-                gload<T, B>(A, n, lda, i, k, S0, false);  // X_ik
-                gload<T, B>(A, n, lda, k, j, S1, false);  // L_kj
+                place<T, B>(r0, S0);  // X_ik
+                place<T, B>(r1, S1);  // L_kj
                 cta_sync();
+                if (k - 1 > j) {
+                    fetch<T, B>(A, n, lda, i, k - 1, r0);
+                    fetch<T, B>(A, n, lda, k - 1, j, r1);
+                }
                 tile_mma<B, false, false, false, FULL, FULL>(acc, S0, S1);
             }
             cta_sync();
@@ -164,11 +238,19 @@ __device__ int run_matrix(T* A, int n, int64_t lda, T* S0, T* S1, T* tmp, int* s
             cta_sync();
             acc_zero<B>(acc);
             tile_mma<B, true, false, false, LOWER, FULL>(acc, S0, S1);  // TRMM
-            for (int k = i + 1; k < t; ++k) {                          // GEMM
+            if (i + 1 < t) {
+                fetch<T, B>(A, n, lda, i + 1, i, r0);
+                fetch<T, B>(A, n, lda, i + 1, j, r1);
+            }
+            for (int k = i + 1; k < t; ++k) {  // GEMM
                 cta_sync();
-                gload<T, B>(A, n, lda, k, i, S0, false);
-                gload<T, B>(A, n, lda, k, j, S1, false);
+                place<T, B>(r0, S0);
+                place<T, B>(r1, S1);
                 cta_sync();
+                if (k + 1 < t) {
+                    fetch<T, B>(A, n, lda, k + 1, i, r0);
+                    fetch<T, B>(A, n, lda, k + 1, j, r1);
+                }
                 tile_mma<B, true, false, false, FULL, FULL>(acc, S0, S1);
             }
             cta_sync();
@@ -181,10 +263,12 @@ __device__ int run_matrix(T* A, int n, int64_t lda, T* S0, T* S1, T* tmp, int* s
         cta_sync();
         acc_zero<B>(acc);
         tile_mma<B, true, false, false, LOWER, LOWER>(acc, S0, S0);  // LAUUM
-        for (int k = i + 1; k < t; ++k) {                           // SYRK
+        if (i + 1 < t) fetch<T, B>(A, n, lda, i + 1, i, r0);
+        for (int k = i + 1; k < t; ++k) {  // SYRK
             cta_sync();
-            gload<T, B>(A, n, lda, k, i, S0, false);
+            place<T, B>(r0, S0);
             cta_sync();
+            if (k + 1 < t) fetch<T, B>(A, n, lda, k + 1, i, r0);
             tile_mma<B, true, false, false, FULL, FULL>(acc, S0, S0);
         }
         cta_sync();
@@ -195,8 +279,15 @@ __device__ int run_matrix(T* A, int n, int64_t lda, T* S0, T* S1, T* tmp, int* s
     return 0;
 }
 
+// Resident CTAs per SM the register budget is set for: the largest tile's
+// accumulator and staged tiles must fit without spilling.
 template <typename T, int BMAX>
-__global__ void __launch_bounds__(kThreads) potri_batched_kernel(const BatchParams<T> p) {
+constexpr int batched_min_blocks() {
+    return BMAX >= 64 ? 4 : (BMAX <= 16 ? 12 : (sizeof(T) == 8 ? 5 : 8));
+}
+
+template <typename T, int BMAX>
+__global__ void __launch_bounds__(kThreads, batched_min_blocks<T, BMAX>()) potri_batched_kernel(const BatchParams<T> p) {
     unsigned char* const smem_raw = dynamic_smem();
     __shared__ int s_m, s_fail;
     constexpr int TS = BMAX * (BMAX + 1);
