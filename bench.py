@@ -1,7 +1,7 @@
-"""Benchmark: FP64 tiled SPD inversion (POTRI) on one GB300, n = 16384, tile 64.
+"""Benchmark: FP64 tiled SPD inversion (POTRI) on one GB300, n = 16384, tile 32.
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                [--n 16384] [--tile 64] [--cond 1e4] [--no-e2e] [--no-cpu-baseline]
+                [--n 16384] [--tile 32] [--cond 1e4] [--no-e2e] [--no-cpu-baseline]
 
 One step = restore A from a pristine device copy (0.6 ms) + one full
 inversion through the C-ABI (spdinv_potri_ex).  The metric counts n^3 flops
@@ -39,7 +39,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=16384)
-    ap.add_argument("--tile", type=int, default=64)
+    ap.add_argument("--tile", type=int, default=32)
     ap.add_argument("--ctas-per-sm", type=int, default=0)
     ap.add_argument("--cond", type=float, default=1e4)
     ap.add_argument("--e2e-steps", type=int, default=3)
@@ -240,7 +240,7 @@ def run_mixed_study(args, dev, stream):
 
         def fp64():
             W.copy_(A)
-            T.potri_(W, info=info, tile=64)
+            T.potri_(W, info=info)  # the library's default tile
 
         ms64 = timed_steps(fp64, 1, 1, stream, mw)
         e64 = err_of(W)
@@ -587,7 +587,7 @@ def main():
     roofline = {
         "bound": "tensor", "achieved": round(achieved_tf, 4), "peak": round(peak_tf, 4), "unit": "TFLOP/s",
         "frac": round(achieved_tf / peak_tf, 4), "traffic": None,
-        "kernel": "potri_fp64_persistent<64> (FP64 DMMA m8n8k4)",
+        "kernel": "potri_fp64_persistent<%d> (FP64 DMMA m8n8k4)" % b,
         "peak_note": "FP64 peak = bf16_tflops (%s) x nominal FP64/bf16 ratio 1.25/2250; "
                      "DMMA microbenchmark on this GPU: 1.04 TFLOP/s" % src,
     }

@@ -91,7 +91,10 @@ static double wait_timeout_s(const spdinv_opts* o) {
     return 60.0;
 }
 
-static int default_tile(int64_t n) { return n >= 8192 ? 64 : 32; }
+// Tile 32 measured faster than 64 at every size (n = 4096, 8192, 16384: 6
+// resident CTAs per SM instead of 3, and fewer wasted flops in the diagonal
+// tiles), so it is the default.
+static int default_tile(int64_t) { return 32; }
 
 // Shared body of potrf / trtri / lauum / potri (FP64).
 spdinv_status run_fp64(int64_t n, double* dA, int64_t lda, int steps, const spdinv_opts* o, int* d_info,
