@@ -54,7 +54,8 @@ def parse():
                     choices=["fp64", "batched64", "batched32", "backward64", "backward32", "mixed", "residual",
                              "variants"],
                     help="fp64 (default, the headline line): one n x n FP64 inversion per step; "
-                         "batched*: 4096 matrices n ~ U{16..256} per step, one graph-captured launch; "
+                         "batched*: 4096 matrices per GPU, n ~ U{16..256}, one graph-captured launch per step "
+                         "(with N GPUs the 4096 N matrices are split by spdinv_batch_shard); "
                          "backward*: forward + backward of 256 matrices n = 512; "
                          "variants: pipelined vs step-by-step (barriered) execution and the tile size")
     return ap.parse_args()
@@ -335,6 +336,89 @@ def run_variants(args, dev, stream):
         torch.cuda.empty_cache()
 
 
+def run_batched_bench(args, rank, world, local):
+    """The batched workload: 4096 matrices per GPU, n ~ U{16..256}.  With N
+    GPUs (torchrun) the global batch is 4096 N matrices, split across the
+    ranks by spdinv_batch_shard (balanced n^3, no collective on the data
+    path); each rank restores and inverts its share with one graph replay per
+    step.  value = the whole batch's sum(n^3) / the slowest rank's step time."""
+    import torch
+    import torch.distributed as dist
+
+    import spd_inputs as si
+    from paper_1002_4057_gb300 import _lib as L
+    from paper_1002_4057_gb300 import torch_api as T
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    stream = torch.cuda.current_stream()
+    clk = ClockSampler(local)
+    dtype = torch.float64 if args.workload == "batched64" else torch.float32
+    seed = si.SEED_BASE + 3
+    sizes = si.batch_sizes(4096 * world, 16, 256, seed=seed)
+    st, owner, load = L.spdinv_batch_shard([int(v) for v in sizes], world)
+    assert st == 0
+    mine = [k for k in range(len(sizes)) if owner[k] == rank]
+    # the same per-matrix streams as si.wishart_batch(sizes, 0.1, seed)
+    hs = [si.wishart_spd(int(sizes[k]), 0.1, seed * 100003 + k) for k in mine]
+    total = int(sum(a.shape[0] ** 2 for a in hs))
+    pool = torch.empty(total, dtype=dtype, device=dev)
+    mats, off = [], 0
+    for a in hs:
+        n = a.shape[0]
+        v = pool[off:off + n * n].as_strided((n, n), (1, n))
+        v.copy_(torch.from_numpy(a).to(dtype))
+        mats.append(v)
+        off += n * n
+    pristine = pool.clone()
+    pb = T.PreparedBatch(mats)
+    pb.run()
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        pb.run()
+
+    def step():
+        pool.copy_(pristine)
+        g.replay()
+
+    def slowest(ms):
+        if world > 1:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms
+
+    if world > 1:
+        dist.barrier()
+    clk.start()
+    ms = slowest(timed_steps(step, args.steps, args.warmup, stream))
+    clocks = clk.stop()
+    assert int(pb.info.abs().sum().item()) == 0
+    flops = float(sum(int(n) ** 3 for n in sizes))
+    if world > 1:
+        dist.barrier()
+    e_inv = slowest(timed_steps(lambda: g.replay(), args.steps, 1, stream))
+    st, tiles = L.spdinv_batched_tiles(1 if dtype == torch.float32 else 0)
+    if rank == 0:
+        line = {"workload": args.workload, "metric": METRIC, "value": round(flops / (ms * 1e-3) / 1e9, 3),
+                "unit": "Gflop/s", "n_gpus": world, "scaling": "weak", "ms_per_step": round(ms, 4),
+                "ms_per_batch_launch": round(e_inv, 4),
+                "value_launch_only": round(flops / (e_inv * 1e-3) / 1e9, 3),
+                "dtype": "f64" if dtype == torch.float64 else "f32", "flops_per_step": flops,
+                "config": {"matrices": 4096 * world, "n": "U{16..256}", "generator": "B B^T/n + 0.1 I",
+                           "split": "spdinv_batch_shard (longest processing time first on n^3); max/mean rank "
+                                    "load %.4f" % (max(load) / (sum(load) / world)),
+                           "step": "restore the batch (device copy) + one graph replay of spdinv_*potri_batched",
+                           "autotuned_tiles_by_32_class": tiles},
+                "clocks": clocks}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
 def run_secondary(args):
     """Measurement lines for the batched and backward workloads (not the
     headline line): Gflop/s with sum(n^3) per batch, or 3 n^3 per matrix for
@@ -359,46 +443,7 @@ def run_secondary(args):
         run_variants(args, dev, stream)
         return
     if args.workload.startswith("batched"):
-        dtype = torch.float64 if args.workload == "batched64" else torch.float32
-        sizes = si.batch_sizes(4096, 16, 256, seed=si.SEED_BASE + 3)
-        hs = si.wishart_batch(sizes, 0.1, si.SEED_BASE + 3)
-        total = int(sum(a.shape[0] ** 2 for a in hs))
-        pool = torch.empty(total, dtype=dtype, device=dev)
-        mats, off = [], 0
-        for a in hs:
-            n = a.shape[0]
-            v = pool[off:off + n * n].as_strided((n, n), (1, n))
-            v.copy_(torch.from_numpy(a).to(dtype))
-            mats.append(v)
-            off += n * n
-        pristine = pool.clone()
-        pb = T.PreparedBatch(mats)
-        pb.run()
-        torch.cuda.synchronize()
-        g = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(g):
-            pb.run()
-
-        def step():
-            pool.copy_(pristine)
-            g.replay()
-
-        launches0 = L.spdinv_kernel_launches()
-        clk.start()
-        ms = timed_steps(step, args.steps, args.warmup, stream)
-        clocks = clk.stop()
-        assert int(pb.info.abs().sum().item()) == 0
-        flops = float(sum(int(n) ** 3 for n in sizes))
-        e_inv = timed_steps(lambda: g.replay(), args.steps, 1, stream)
-        st, tiles = L.spdinv_batched_tiles(1 if dtype == torch.float32 else 0)
-        line = {"workload": args.workload, "metric": METRIC, "value": round(flops / (ms * 1e-3) / 1e9, 3),
-                "unit": "Gflop/s", "ms_per_step": round(ms, 4), "ms_per_batch_launch": round(e_inv, 4),
-                "value_launch_only": round(flops / (e_inv * 1e-3) / 1e9, 3),
-                "dtype": "f64" if dtype == torch.float64 else "f32", "flops_per_step": flops,
-                "config": {"matrices": 4096, "n": "U{16..256}", "generator": "B B^T/n + 0.1 I",
-                           "step": "restore the batch (device copy) + one graph replay of spdinv_*potri_batched",
-                           "autotuned_tiles_by_32_class": tiles},
-                "clocks": clocks, "gpu_launches_per_step": (L.spdinv_kernel_launches() - launches0)}
+        raise AssertionError("batched workloads run through run_batched_bench")
     else:
         dtype = torch.float64 if args.workload == "backward64" else torch.float32
         n, b = 512, 256
@@ -439,6 +484,9 @@ def main():
     rank, world, local = dist_env()
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.workload.startswith("batched"):
+        run_batched_bench(args, rank, world, local)
         return
     if args.workload != "fp64":
         if rank == 0:

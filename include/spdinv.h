@@ -256,6 +256,19 @@ SPDINV_API spdinv_status spdinv_spotri_backward(int batch, int64_t n, const floa
                                      float* dGrad, int64_t ldgrad, int64_t stride_grad,
                                      cudaStream_t stream);
 
+/* Split of a batch across `world` GPUs (one process per GPU; no counterpart
+ * in the paper, whose unit of work is one matrix).  The matrices are
+ * independent, so a multi-GPU batch needs no collective: rank r inverts the
+ * matrices with owner[k] == r through spdinv_potri_batched.  The split
+ * balances the work (n^3 per matrix) by longest processing time first:
+ * matrices by decreasing n, each to the rank with the least total so far,
+ * ties to the lower index and the lower rank; every rank's total is within
+ * 4/3 of the best possible split.  Deterministic and host-only (no GPU).
+ *   h_n[batch]     host: orders of the matrices (>= 0);
+ *   owner[batch]   host, out: rank in [0, world) of each matrix;
+ *   load[world]    host, out (nullable): each rank's total n^3. */
+SPDINV_API spdinv_status spdinv_batch_shard(int batch, const int* h_n, int world, int* owner, double* load);
+
 /* The autotuner's tile choice for spdinv_potri_batched (fp32 == 0) or
  * spdinv_spotri_batched (fp32 != 0): tiles[c] is the tile order used for
  * matrices with 32c < n <= 32(c+1) (c = 7 also for n > 256).  The first call

@@ -68,6 +68,7 @@ SIGNATURES = {
     "spdinv_spotri_backward": (c_int, [c_int, c_int64, P, c_int64, c_int64, P, c_int64, c_int64,
                                        P, c_int64, c_int64, P]),
     "spdinv_batched_tiles": (c_int, [c_int, P]),
+    "spdinv_batch_shard": (c_int, [c_int, P, c_int, P, P]),
     "spdinv_mirror_lower": (c_int, [c_int, c_int64, P, c_int64, c_int64, P]),
     "spdinv_smirror_lower": (c_int, [c_int, c_int64, P, c_int64, c_int64, P]),
     "spdinv_dag_critical_path": (c_int, [c_int, c_int, P]),
@@ -153,6 +154,18 @@ def spdinv_batched_tiles(fp32):
     out = (ctypes.c_int * 8)()
     st = _call("spdinv_batched_tiles", int(fp32), ctypes.addressof(out))
     return st, list(out)
+
+
+def spdinv_batch_shard(sizes, world):
+    """(status, owner per matrix, total n^3 per rank) of the split of a batch
+    with orders `sizes` across `world` ranks."""
+    n = len(sizes)
+    hn = (ctypes.c_int * max(n, 1))(*[int(v) for v in sizes])
+    owner = (ctypes.c_int * max(n, 1))()
+    load = (ctypes.c_double * max(int(world), 1))()
+    st = _call("spdinv_batch_shard", n, ctypes.addressof(hn), int(world), ctypes.addressof(owner),
+               ctypes.addressof(load))
+    return st, list(owner)[:n], list(load)[:max(int(world), 0)]
 
 
 def spdinv_mirror_lower(batch, n, dA, lda, stride, stream):

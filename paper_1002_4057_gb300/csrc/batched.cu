@@ -669,6 +669,31 @@ SPDINV_API spdinv_status spdinv_spotri_batched(int batch, const int* h_n, float*
     return run_batched<float>(batch, h_n, d_Aptrs, h_lda, d_info, stream);
 }
 
+SPDINV_API spdinv_status spdinv_batch_shard(int batch, const int* h_n, int world, int* owner, double* load) {
+    if (batch < 0) return SPDINV_ERR_N;
+    if (world < 1) return SPDINV_ERR_UNSUPPORTED;
+    if (batch > 0 && (!h_n || !owner)) return SPDINV_ERR_NULL;
+    for (int k = 0; k < batch; ++k)
+        if (h_n[k] < 0) return SPDINV_ERR_N;
+    // Longest processing time first: matrices by decreasing n (ties: lower
+    // index first), each to the rank with the least n^3 so far (ties: lower
+    // rank).  Deterministic, so every rank computes the same split.
+    std::vector<int> order(batch);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return h_n[a] > h_n[b]; });
+    std::vector<double> sum(world, 0.0);
+    for (int k : order) {
+        int r = 0;
+        for (int q = 1; q < world; ++q)
+            if (sum[q] < sum[r]) r = q;
+        owner[k] = r;
+        sum[r] += (double)h_n[k] * h_n[k] * h_n[k];
+    }
+    if (load)
+        for (int q = 0; q < world; ++q) load[q] = sum[q];
+    return SPDINV_OK;
+}
+
 SPDINV_API spdinv_status spdinv_batched_tiles(int fp32, int tiles[8]) {
     if (!tiles) return SPDINV_ERR_NULL;
     int dev = 0;
