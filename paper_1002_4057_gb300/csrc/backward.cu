@@ -2,7 +2,8 @@
 // method): for f(A) with X = A^{-1} and incoming gradient G = df/dX,
 //   d(A^{-1}) = -X dA X   =>   grad_A = -X sym(G) X,   sym(G) = (G + G^T)/2,
 // which is -sym(X G X) for symmetric X.  Two tiled products per matrix:
-//   phase 0:  Y = X sym(G)              (sym(G) formed while staging G's tiles)
+//   sym:      Gs = sym(G)               (a coalesced tiled transpose, once)
+//   phase 0:  Y = X Gs
 //   phase 1:  grad = -Y X, lower tiles only, each written to (i, j) and,
 //             transposed, to (j, i); the diagonal tiles are averaged with
 //             their transpose, so grad is exactly symmetric.
@@ -41,9 +42,8 @@ struct BwdParams {
     int t;
     const T* X;
     int64_t ldx, sx;
-    const T* G;
-    int64_t ldg, sg;
-    T* Y;  // workspace, n x n per matrix, ld n
+    const T* Gs;  // workspace: sym(G), n x n per matrix, ld n
+    T* Y;         // workspace, n x n per matrix, ld n
     T* grad;
     int64_t ldr, sr;
 };
@@ -59,14 +59,33 @@ __device__ __forceinline__ void load_tile(const T* M, int64_t n, int64_t ld, int
     }
 }
 
-// Tile (ti, tj) of sym(G) = (G + G^T)/2.
+// Gs = sym(G) = (G + G^T)/2 (ld n, matrix k at k n^2), formed once before
+// the products so that they read plain tiles: each CTA reads the 32 x 32
+// tiles (bi, bj) and (bj, bi), bi >= bj, with coalesced loads, transposes
+// through shared memory, and writes both halves with coalesced stores.
 template <typename T>
-__device__ __forceinline__ void load_sym_tile(const T* G, int64_t n, int64_t ld, int ti, int tj, T* S) {
-    constexpr int LD = BwdTile<T>::LD;
-    for (int idx = threadIdx.x; idx < BB * BB; idx += kThreads) {
-        const int r = idx % BB, c = idx / BB;
-        const int64_t gr = (int64_t)ti * BB + r, gc = (int64_t)tj * BB + c;
-        S[c * LD + r] = (gr < n && gc < n) ? T(0.5) * (G[gr + gc * ld] + G[gc + gr * ld]) : T(0);
+__global__ void __launch_bounds__(256) sym_kernel(int64_t n, const T* G, int64_t ldg, int64_t sg, T* Gs) {
+    __shared__ T a[32][33], b[32][33];
+    const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+    const int64_t k = blockIdx.y;
+    int bi = (int)((sqrt(8.0 * blockIdx.x + 1.0) - 1.0) / 2.0);
+    while ((bi + 1) * (bi + 2) / 2 <= (int)blockIdx.x) ++bi;
+    while (bi * (bi + 1) / 2 > (int)blockIdx.x) --bi;
+    const int bj = blockIdx.x - bi * (bi + 1) / 2;
+    const T* g = G + k * sg;
+    T* o = Gs + k * n * n;
+    for (int c = ty; c < 32; c += 8) {  // a[c][r] = G(bi*32 + r, bj*32 + c), b[c][r] = G(bj*32 + r, bi*32 + c)
+        const int64_t r0 = (int64_t)bi * 32 + tx, c0 = (int64_t)bj * 32 + c;
+        const int64_t r1 = (int64_t)bj * 32 + tx, c1 = (int64_t)bi * 32 + c;
+        a[c][tx] = (r0 < n && c0 < n) ? g[r0 + c0 * ldg] : T(0);
+        b[c][tx] = (r1 < n && c1 < n) ? g[r1 + c1 * ldg] : T(0);
+    }
+    cta_sync();
+    for (int c = ty; c < 32; c += 8) {
+        const int64_t r0 = (int64_t)bi * 32 + tx, c0 = (int64_t)bj * 32 + c;  // Gs(r0, c0) = (a[c][tx] + b[tx][c]) / 2
+        if (r0 < n && c0 < n) o[r0 + c0 * n] = T(0.5) * (a[c][tx] + b[tx][c]);
+        const int64_t r1 = (int64_t)bj * 32 + tx, c1 = (int64_t)bi * 32 + c;  // Gs(r1, c1) = (b[c][tx] + a[tx][c]) / 2
+        if (bi != bj && r1 < n && c1 < n) o[r1 + c1 * n] = T(0.5) * (b[c][tx] + a[tx][c]);
     }
 }
 
@@ -88,7 +107,7 @@ __global__ void __launch_bounds__(kThreads) backward_kernel(const BwdParams<T> p
         tj = blockIdx.x - ti * (ti + 1) / 2;
     }
     const T* X = p.X + mat * p.sx;
-    const T* G = p.G + mat * p.sg;
+    const T* G = p.Gs + mat * p.n * p.n;
     T* Y = p.Y + mat * p.n * p.n;
     typename BwdTile<T>::Acc acc;
     acc_zero<BB>(acc);
@@ -96,7 +115,7 @@ __global__ void __launch_bounds__(kThreads) backward_kernel(const BwdParams<T> p
         cta_sync();
         if (PHASE == 0) {
             load_tile<T>(X, p.n, p.ldx, ti, kt, S0);
-            load_sym_tile<T>(G, p.n, p.ldg, kt, tj, S1);
+            load_tile<T>(G, p.n, p.n, kt, tj, S1);  // sym(G), formed by sym_kernel
         } else {
             load_tile<T>(Y, p.n, p.n, ti, kt, S0);
             load_tile<T>(X, p.n, p.ldx, kt, tj, S1);
@@ -166,7 +185,7 @@ spdinv_status run_backward(int batch, int64_t n, const T* dX, int64_t ldx, int64
     if (e != cudaSuccess) return cuda_fail(e);
     BwdState& st = bwd_state(dev);
     std::lock_guard<std::mutex> lk(st.mu);
-    const size_t need = sizeof(T) * (size_t)n * n * batch;
+    const size_t need = 2 * sizeof(T) * (size_t)n * n * batch;  // Y and sym(G)
     if (need > st.bytes) {
         if (st.ws) {
             e = cudaDeviceSynchronize();
@@ -179,18 +198,23 @@ spdinv_status run_backward(int batch, int64_t n, const T* dX, int64_t ldx, int64
         if (e != cudaSuccess) return cuda_fail(e);
         st.bytes = need;
     }
-    BwdParams<T> p{n, (int)t, dX, ldx, sx, dG, ldg, sg, static_cast<T*>(st.ws), dGrad, ldr, sr};
+    T* Ys = static_cast<T*>(st.ws);
+    BwdParams<T> p{n, (int)t, dX, ldx, sx, Ys + (size_t)n * n * batch, Ys, dGrad, ldr, sr};
+    T* Gs = Ys + (size_t)n * n * batch;
     const int sm = 2 * BB * BwdTile<T>::LD * (int)sizeof(T);
     auto k0 = backward_kernel<T, 0>;
     auto k1 = backward_kernel<T, 1>;
     e = cudaFuncSetAttribute(k0, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     if (e != cudaSuccess) return cuda_fail(e);
+    const int64_t t32 = (n + 31) / 32;
+    sym_kernel<T><<<dim3((unsigned)(t32 * (t32 + 1) / 2), (unsigned)batch), dim3(32, 8), 0, stream>>>(n, dG, ldg, sg,
+                                                                                                    Gs);
     k0<<<dim3((unsigned)(t * t), (unsigned)batch), kThreads, sm, stream>>>(p);
     k1<<<dim3((unsigned)(t * (t + 1) / 2), (unsigned)batch), kThreads, sm, stream>>>(p);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e);
-    count_launches(2);
+    count_launches(3);
     return SPDINV_OK;
 }
 
