@@ -10,7 +10,11 @@
 // of L_jj from Step 1 on; nothing after Step 1 reads L_jj.
 //
 // The tile size of each matrix comes from the autotuner's table for its size
-// class.  FP64 uses the tensor-core MMA tile products, FP32 the CUDA-core ones.
+// class, capped per batch by plan tuning (one kernel holds the largest tile
+// any matrix uses, and that sets every CTA's occupancy).  Inside each chain of
+// products the next tiles are read into registers while the current product
+// runs.  FP64 uses the tensor-core MMA tile products, FP32 the CUDA-core ones.
+// spdinv_batch_shard splits a batch across GPUs (host only).
 #include <cuda_runtime.h>
 
 #include <algorithm>

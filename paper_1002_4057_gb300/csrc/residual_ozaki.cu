@@ -12,16 +12,20 @@
 //     integers in [-128, 128] -- exact in BF16 (8 significant bits);
 //   * for a slice pair (s, t) the product sum_k a_s(i,k) x_t(k,j) has terms
 //     of at most 2^14 and is exact in FP32 over k-chunks of up to 1024
-//     (<= 2^24); chunks are added exactly in INT32 and each pair in FP64
-//     with its scale 2^{e_i + f_j - 8(s+t+2)};
+//     (<= 2^24); chunks are added exactly in INT32, and into R in FP64 with
+//     the pair's scale 2^{e_i + f_j - 8(s+t+2)};
 //   * pairs with s + t > L are dropped.  Rows are scaled by their largest
 //     entry, so smaller entries keep fewer bits.  S = 7 with L = 6 (28 pairs)
 //     leaves an error of about 1e-15 relative to |A| |X|, enough for every
 //     correction step but the last; L = 7 (34 pairs) brings it to about
 //     1e-16, the accuracy of the native FP64 product, which the last step
 //     needs because its residual error stays in the result.
-// The slice products run on mma.sync m16n8k16 (BF16 in, FP32 out), fed from
-// shared memory by cp.async and ldmatrix.
+// The slice products run on the tcgen05 tensor cores (residual_tc.cu) or, as
+// the comparison path, on mma.sync m16n8k16 here (BF16 in, FP32 out, fed from
+// shared memory by cp.async and ldmatrix).  This file also holds the slicing
+// kernels and the order-p correction step built on them (ozaki_refine_step).
+// The mma.sync path adds each flush of its INT32 chunk sums into R in FP64;
+// the tcgen05 path first sums each level's pairs exactly in INT64.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 

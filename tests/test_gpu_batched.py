@@ -120,6 +120,36 @@ def test_autotuner_table(gpu):
         assert all(t in allowed for t in tiles), tiles
 
 
+
+@pytest.mark.parametrize("dtype_name,tol", [("float64", 1e-12), ("float32", 1e-5)])
+def test_sharded_batch_matches_whole_batch(gpu, dtype_name, tol):
+    """The multi-GPU path on one GPU, rank after rank: spdinv_batch_shard
+    splits the batch for two ranks, each share goes through its own batched
+    call, and every matrix matches the whole-batch call (a share may get a
+    different tile plan, so the comparison is by tolerance) and the oracle."""
+    import torch
+    from paper_1002_4057_gb300 import _lib as L
+    from paper_1002_4057_gb300 import torch_api as T
+    dtype = getattr(torch, dtype_name)
+    sizes = si.batch_sizes(120, 16, 256, seed=17)
+    hs, whole = _mats(sizes, dtype, gpu, 23)
+    assert int(T.potri_batched_(whole).abs().sum().item()) == 0
+    st, owner, load = L.spdinv_batch_shard([int(v) for v in sizes], 2)
+    assert st == 0 and sorted(set(owner)) == [0, 1]
+    got = [None] * len(sizes)
+    for rank in (0, 1):
+        mine = [k for k in range(len(sizes)) if owner[k] == rank]
+        share = [to_dev(hs[k], gpu).to(dtype) for k in mine]  # .to keeps the column-major strides
+        assert int(T.potri_batched_(share).abs().sum().item()) == 0
+        for d, k in zip(share, mine):
+            got[k] = d
+    torch.cuda.synchronize()
+    for k in range(len(sizes)):
+        a = full_from_lower(np.tril(got[k].double().cpu().numpy()))
+        b = full_from_lower(np.tril(whole[k].double().cpu().numpy()))
+        assert oracle.rel_frobenius(a, b) <= tol, (k, sizes[k])
+    _check(hs, got, 1e-10 if dtype == torch.float64 else 2e-4)
+
 @pytest.mark.slow
 def test_batched_config_4096_sampled(gpu):
     """The 4096-matrix workload (n ~ U{16..256}, A = B B^T/n + 0.1 I): every
