@@ -121,7 +121,10 @@ __global__ void __launch_bounds__(kThreads) backward_kernel(const BwdParams<T> p
             load_tile<T>(X, p.n, p.ldx, kt, tj, S1);
         }
         cta_sync();
-        tile_mma<BB, false, false, PHASE == 1, FULL, FULL>(acc, S0, S1);
+        if constexpr (sizeof(T) == 4)
+            tile_mma<BB, false, false, PHASE == 1, FULL, FULL, true>(acc, S0, S1);  // packed FP32 FMA
+        else
+            tile_mma<BB, false, false, PHASE == 1, FULL, FULL>(acc, S0, S1);
     }
     cta_sync();
     acc_store<BB>(acc, S0);
