@@ -295,13 +295,18 @@ SPDINV_API spdinv_status spdinv_smirror_lower(int batch, int64_t n, float* dA, i
 #define SPDINV_DAG_RENAME_DIAG  2  /* also keep the inverted diagonal tiles in their own store D */
 #define SPDINV_DAG_UUU          4  /* all innermost GEMM loops increasing (default: U, D, U) */
 #define SPDINV_DAG_PIPELINE     8  /* one DAG across the three steps (else a barrier between steps) */
+#define SPDINV_DAG_TREE        16  /* each commutative update chain of m products reduced as a tree:
+                                      m independent products into temporaries, a pairwise sum, one
+                                      update (the associative reduction Sec. 3 names for shortening
+                                      the critical path; analysis only: the GPU kernel runs chains) */
+#define SPDINV_DAG_TREE_STEP3  32  /* the same for the chains of Step 3 only */
 
 /* Critical path, in tasks of unit weight (tile copies weigh 0), of the
  * fine-grained task DAG of Algorithm 1 (Sec. 2) or its variants (Sec. 3)
  * for t x t tiles: out[0..2] = each step's own DAG, out[3] = the whole
  * inversion (pipelined or with barriers, per SPDINV_DAG_PIPELINE).
  * Table 1 of the paper gives out[0..2] for the in-place and out-of-place
- * cases.  1 <= t <= 256. */
+ * cases.  1 <= t <= 256 (with a tree flag, t <= 128). */
 SPDINV_API spdinv_status spdinv_dag_critical_path(int t, int flags, int64_t out[4]);
 
 /* Number of tasks of each kind in Algorithm 1 for t x t tiles, in the order

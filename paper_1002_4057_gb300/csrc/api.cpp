@@ -196,7 +196,7 @@ spdinv_status spdinv_potri_diag(int64_t n, const double* dA, int64_t lda, double
 }
 
 spdinv_status spdinv_dag_critical_path(int t, int flags, int64_t out[4]) {
-    if (t < 1 || t > 256) return SPDINV_ERR_N;
+    if (t < 1 || t > 256 || ((flags & (SPDINV_DAG_TREE | SPDINV_DAG_TREE_STEP3)) && t > 128)) return SPDINV_ERR_N;
     if (!out) return SPDINV_ERR_NULL;
     dag_critical_path(t, flags, out);
     return SPDINV_OK;

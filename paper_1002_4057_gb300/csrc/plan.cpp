@@ -23,6 +23,7 @@
 #include <algorithm>
 #include <cstring>
 #include <numeric>
+#include <vector>
 
 #include "../../include/spdinv.h"
 
@@ -66,28 +67,75 @@ void dag_critical_path(int t, int flags, int64_t out[4]) {
     const bool rdiag = flags & SPDINV_DAG_RENAME_DIAG;
     const bool uuu = flags & SPDINV_DAG_UUU;
     const bool pipe = flags & SPDINV_DAG_PIPELINE;
+    const bool tree_all = flags & SPDINV_DAG_TREE, tree3 = tree_all || (flags & SPDINV_DAG_TREE_STEP3);
+    bool tree = false;  // the current step's chains are tree-reduced
     const int64_t T = t;
-    // address spaces: A(i,j), B(i,j), C(i,j), D(j)
+    // address spaces: A(i,j), B(i,j), C(i,j), D(j), then one fresh temporary
+    // per product of a tree-reduced chain
     auto A = [&](int64_t i, int64_t j) { return i * T + j; };
     auto B = [&](int64_t i, int64_t j) { return T * T + i * T + j; };
     auto C = [&](int64_t i, int64_t j) { return 2 * T * T + i * T + j; };
     auto D = [&](int64_t j) { return 3 * T * T + j; };
-    HazardSim sim(3 * T * T + T);
-    HazardSim whole(3 * T * T + T);
+    const int64_t base = 3 * T * T + T;
+    // temporaries per pass: each chain of m products takes m + (m - 1); the
+    // products per pass are 3 T(T-1)(T-2)/6 GEMMs + T(T-1) SYRKs < T^3/2 + T^2
+    const int64_t ntmp = tree3 ? T * T * T + 2 * T * T + 8 : 0;
+    HazardSim sim(base + ntmp);
+    HazardSim whole(base + ntmp);
     int64_t step_cp[3] = {0, 0, 0};
+    int64_t next_tmp = base;
+    // One commutative update chain acc <- acc + sum_q P_q, P_q reading the
+    // tiles ins[q] (Sec. 3: its order is free).  Without SPDINV_DAG_TREE it
+    // is m sequential tasks on acc.  With it (the associative reduction the
+    // paper names for shortening the critical path): m products into fresh
+    // temporaries, a pairwise reduction tree, and one update of acc -- depth
+    // 1 + ceil(log2 m) + 1 instead of m.
+    auto chain = [&](HazardSim& s, int64_t acc, const std::vector<std::vector<int64_t>>& ins) {
+        const size_t m = ins.size();
+        if (!tree || m < 2) {
+            for (const auto& r : ins) {
+                if (r.size() == 1) s.task({acc, r[0]}, {acc}, 1);
+                else s.task({acc, r[0], r[1]}, {acc}, 1);
+            }
+            return;
+        }
+        std::vector<int64_t> tmp(m);
+        for (size_t q = 0; q < m; ++q) {
+            tmp[q] = next_tmp++;
+            if (ins[q].size() == 1) s.task({ins[q][0]}, {tmp[q]}, 1);
+            else s.task({ins[q][0], ins[q][1]}, {tmp[q]}, 1);
+        }
+        while (tmp.size() > 1) {  // each level writes fresh temporaries: no false hazards
+            std::vector<int64_t> up;
+            for (size_t q = 0; q + 1 < tmp.size(); q += 2) {
+                up.push_back(next_tmp++);
+                s.task({tmp[q], tmp[q + 1]}, {up.back()}, 1);
+            }
+            if (tmp.size() % 2) up.push_back(tmp.back());
+            tmp.swap(up);
+        }
+        s.task({acc, tmp[0]}, {acc}, 1);
+    };
 
     for (int pass = 0; pass < 2; ++pass) {
         // pass 0: each step's own DAG (state reset between steps);
         // pass 1: the whole inversion with one continuing state (pipelined).
         HazardSim& s = pass == 0 ? sim : whole;
+        next_tmp = base;  // each pass has its own simulator, so its own temporaries
         // ---- Step 1: tile Cholesky (Algorithm 1, Step 1)
         if (pass == 0) s.reset();
+        tree = tree_all;
         for (int64_t j = 0; j < T; ++j) {
-            for (int64_t k = 0; k < j; ++k) s.task({A(j, j), A(j, k)}, {A(j, j)}, 1);  // SYRK
-            s.task({A(j, j)}, {A(j, j)}, 1);                                            // POTRF
-            for (int64_t i = j + 1; i < T; ++i)
-                for (int64_t k = 0; k < j; ++k) s.task({A(i, j), A(i, k), A(j, k)}, {A(i, j)}, 1);  // GEMM
-            for (int64_t i = j + 1; i < T; ++i) s.task({A(i, j), A(j, j)}, {A(i, j)}, 1);           // TRSM
+            std::vector<std::vector<int64_t>> ins;
+            for (int64_t k = 0; k < j; ++k) ins.push_back({A(j, k)});
+            chain(s, A(j, j), ins);           // SYRK
+            s.task({A(j, j)}, {A(j, j)}, 1);  // POTRF
+            for (int64_t i = j + 1; i < T; ++i) {
+                ins.clear();
+                for (int64_t k = 0; k < j; ++k) ins.push_back({A(i, k), A(j, k)});
+                chain(s, A(i, j), ins);  // GEMM
+            }
+            for (int64_t i = j + 1; i < T; ++i) s.task({A(i, j), A(j, j)}, {A(i, j)}, 1);  // TRSM
         }
         if (pass == 0) step_cp[0] = s.span;
         // ---- Step 2: tile triangular inversion (Algorithm 1, Step 2)
@@ -102,17 +150,19 @@ void dag_critical_path(int t, int flags, int64_t out[4]) {
             for (int64_t i = T - 1; i > j; --i) {
                 const int64_t Xi = rdiag ? D(i) : A(i, i);
                 s.task({Xi, A(i, j)}, {A(i, j)}, 1);  // TRMM: A_ij <- X_ii A_ij
+                std::vector<std::vector<int64_t>> ins;
                 for (int64_t m = 0; m < i - j - 1; ++m) {
                     const int64_t k = uuu ? j + 1 + m : i - 1 - m;  // U or D order
-                    const int64_t Lkj = oop ? B(k, j) : A(k, j);
-                    s.task({A(i, j), A(i, k), Lkj}, {A(i, j)}, 1);  // GEMM
+                    ins.push_back({A(i, k), oop ? B(k, j) : A(k, j)});
                 }
+                chain(s, A(i, j), ins);  // GEMM
                 s.task({A(i, j), Xj}, {A(i, j)}, 1);  // TRMM: A_ij <- -A_ij X_jj
             }
         }
         if (pass == 0) step_cp[1] = s.span;
         // ---- Step 3: product X^T X (Algorithm 1, Step 3)
         if (pass == 0) s.reset();
+        tree = tree3;
         if (oop)
             for (int64_t i = 0; i < T; ++i)
                 for (int64_t j = 0; j <= i; ++j)
@@ -122,15 +172,15 @@ void dag_critical_path(int t, int flags, int64_t out[4]) {
             for (int64_t j = 0; j < i; ++j) s.task({Xii, A(i, j)}, {A(i, j)}, 1);  // TRMM
             if (rdiag) s.task({D(i)}, {A(i, i)}, 1);                                 // LAUUM from D_i
             else s.task({A(i, i)}, {A(i, i)}, 1);                                    // LAUUM in place
-            for (int64_t j = 0; j < i; ++j)
-                for (int64_t k = i + 1; k < T; ++k) {
-                    const int64_t Xki = oop ? C(k, i) : A(k, i), Xkj = oop ? C(k, j) : A(k, j);
-                    s.task({A(i, j), Xki, Xkj}, {A(i, j)}, 1);  // GEMM
-                }
-            for (int64_t k = i + 1; k < T; ++k) {
-                const int64_t Xki = oop ? C(k, i) : A(k, i);
-                s.task({A(i, i), Xki}, {A(i, i)}, 1);  // SYRK
+            std::vector<std::vector<int64_t>> ins;
+            for (int64_t j = 0; j < i; ++j) {
+                ins.clear();
+                for (int64_t k = i + 1; k < T; ++k) ins.push_back({oop ? C(k, i) : A(k, i), oop ? C(k, j) : A(k, j)});
+                chain(s, A(i, j), ins);  // GEMM
             }
+            ins.clear();
+            for (int64_t k = i + 1; k < T; ++k) ins.push_back({oop ? C(k, i) : A(k, i)});
+            chain(s, A(i, i), ins);  // SYRK
         }
         if (pass == 0) step_cp[2] = s.span;
     }

@@ -1,5 +1,6 @@
 """Host planner: the paper's task DAG (Table 1, Sec. 3) and the execution
 plan of the persistent kernel (a topological order of the chain tasks)."""
+import math
 import os
 import re
 
@@ -96,6 +97,41 @@ def _alg1_counts(t):
         c[11] += t - i - 1             # SYRK(i,k)
     return c
 
+
+
+@pytest.mark.parametrize("t", [1, 2, 3, 4, 5, 8, 16, 33, 64])
+def test_tree_reduced_chains(t):
+    """The associative reduction of the commutative update chains (Sec. 3):
+    m products into temporaries, a pairwise sum, one update of the tile.
+    Step 3's chains read tiles that are all final when it starts, so alone it
+    takes ceil(log2(t-1)) + 2 tasks (TRMM or LAUUM, the product level and the
+    tree under the longest chain of t-1 products, the update) instead of t.
+    Steps 1 and 2 receive their inputs one column at a time: a sequential
+    chain ends one task after its last input, a tree ceil(log2 m) + 1 later,
+    so trees there lengthen the path, and no tree variant beats the
+    pipelined renamed chains (5t - 2)."""
+    ren = L.SPDINV_DAG_OUT_OF_PLACE | L.SPDINV_DAG_RENAME_DIAG
+    pip = ren | L.SPDINV_DAG_PIPELINE
+    st, chains = L.spdinv_dag_critical_path(t, pip)
+    assert st == 0 and chains[3] == max(5 * t - 2, 3)
+    _, all_trees = L.spdinv_dag_critical_path(t, pip | L.SPDINV_DAG_TREE)
+    _, s3_trees = L.spdinv_dag_critical_path(t, pip | L.SPDINV_DAG_TREE_STEP3)
+    _, barrier_chains = L.spdinv_dag_critical_path(t, ren)
+    _, barrier_s3 = L.spdinv_dag_critical_path(t, ren | L.SPDINV_DAG_TREE_STEP3)
+    if t <= 2:  # no chain has two products
+        assert all_trees == chains and s3_trees == chains
+        return
+    assert s3_trees[2] == math.ceil(math.log2(t - 1)) + 2
+    assert s3_trees[:2] == chains[:2]
+    assert all_trees[3] > chains[3] and s3_trees[3] >= chains[3]
+    assert all_trees[0] >= chains[0] and all_trees[1] >= chains[1]
+    if t >= 8:
+        assert barrier_s3[3] < barrier_chains[3]
+
+
+def test_tree_flags_bound_t():
+    assert L.spdinv_dag_critical_path(129, L.SPDINV_DAG_TREE)[0] == L.SPDINV_ERR_N
+    assert L.spdinv_dag_critical_path(128, L.SPDINV_DAG_TREE_STEP3)[0] == 0
 
 @pytest.mark.parametrize("t", [1, 2, 3, 7, 20])
 def test_task_counts(t):
