@@ -300,6 +300,8 @@ SPDINV_API spdinv_status spdinv_smirror_lower(int batch, int64_t n, float* dA, i
                                       update (the associative reduction Sec. 3 names for shortening
                                       the critical path; analysis only: the GPU kernel runs chains) */
 #define SPDINV_DAG_TREE_STEP3  32  /* the same for the chains of Step 3 only */
+#define SPDINV_DAG_SHARE_BC    64  /* with SPDINV_DAG_OUT_OF_PLACE: C (the copy of L^{-1}) shares B's storage
+                                      (the copy of L), renaming under a memory budget (Sec. 4) */
 
 /* Critical path, in tasks of unit weight (tile copies weigh 0), of the
  * fine-grained task DAG of Algorithm 1 (Sec. 2) or its variants (Sec. 3)

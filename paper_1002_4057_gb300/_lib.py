@@ -41,6 +41,7 @@ SPDINV_DAG_UUU = 4
 SPDINV_DAG_PIPELINE = 8
 SPDINV_DAG_TREE = 16
 SPDINV_DAG_TREE_STEP3 = 32
+SPDINV_DAG_SHARE_BC = 64
 
 STATUS_NAMES = {0: "SPDINV_OK", -1: "SPDINV_ERR_N", -2: "SPDINV_ERR_LDA", -3: "SPDINV_ERR_NULL",
                 -4: "SPDINV_ERR_CUDA", -5: "SPDINV_ERR_TIMEOUT", -6: "SPDINV_ERR_UNSUPPORTED",

@@ -74,7 +74,12 @@ void dag_critical_path(int t, int flags, int64_t out[4]) {
     // per product of a tree-reduced chain
     auto A = [&](int64_t i, int64_t j) { return i * T + j; };
     auto B = [&](int64_t i, int64_t j) { return T * T + i * T + j; };
-    auto C = [&](int64_t i, int64_t j) { return 2 * T * T + i * T + j; };
+    // SPDINV_DAG_SHARE_BC: C (the copy of L^{-1}) reuses B's storage (the
+    // copy of L), the memory-constrained renaming of Sec. 4: half the extra
+    // memory, at the price of the hazards between Step 2's reads of B and
+    // Step 3's copies into C.
+    const bool share = flags & SPDINV_DAG_SHARE_BC;
+    auto C = [&](int64_t i, int64_t j) { return (share ? T * T : 2 * T * T) + i * T + j; };
     auto D = [&](int64_t j) { return 3 * T * T + j; };
     const int64_t base = 3 * T * T + T;
     // temporaries per pass: each chain of m products takes m + (m - 1); the

@@ -129,6 +129,24 @@ def test_tree_reduced_chains(t):
         assert barrier_s3[3] < barrier_chains[3]
 
 
+
+@pytest.mark.parametrize("t", [1, 2, 3, 4, 8, 16, 33, 64, 128])
+def test_renaming_under_a_memory_budget(t):
+    """C (the copy of L^{-1}) sharing B's storage (the copy of L) halves the
+    renaming's extra memory; each step alone keeps its out-of-place path, but
+    Step 3's copies into C now wait for Step 2's last reads of B, and the
+    pipelined inversion takes 6t - 5 tasks (t >= 3) instead of 5t - 2 --
+    barely under the barriered 6t - 3."""
+    ren = L.SPDINV_DAG_OUT_OF_PLACE | L.SPDINV_DAG_RENAME_DIAG
+    _, full = L.spdinv_dag_critical_path(t, ren | L.SPDINV_DAG_PIPELINE)
+    _, shared = L.spdinv_dag_critical_path(t, ren | L.SPDINV_DAG_PIPELINE | L.SPDINV_DAG_SHARE_BC)
+    _, barrier = L.spdinv_dag_critical_path(t, ren | L.SPDINV_DAG_SHARE_BC)
+    assert shared[:3] == full[:3]
+    if t >= 3:
+        assert shared[3] == 6 * t - 5
+        assert barrier[3] == 6 * t - 3
+    assert full[3] <= shared[3] <= barrier[3]
+
 def test_tree_flags_bound_t():
     assert L.spdinv_dag_critical_path(129, L.SPDINV_DAG_TREE)[0] == L.SPDINV_ERR_N
     assert L.spdinv_dag_critical_path(128, L.SPDINV_DAG_TREE_STEP3)[0] == 0
