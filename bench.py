@@ -215,7 +215,6 @@ def run_mixed_study(args, dev, stream):
     import torch
 
     import spd_inputs as si
-    from oracle import closed_forms as cf
     from paper_1002_4057_gb300 import torch_api as T
 
     n = args.n
@@ -229,7 +228,9 @@ def run_mixed_study(args, dev, stream):
                  1e6: ((0, 2), (1, 4), (2, 2), (3, 2), (4, 2), (2, 3), (2, 4))}
     for cond in [float(c) for c in args.conds.split(",")]:
         A, Q, lam = si.spectral_spd(n, cond, seed=si.SEED_BASE + 2, device=dev)
-        ref = cf.spectral_inverse_columns(Q.cpu().numpy(), lam, cols)
+        # the exact inverse of the generated A, Q diag(1/lam) Q^T, on the sampled columns
+        lt = torch.from_numpy(lam).to(Q.device)
+        ref = (Q @ (Q[cols, :].t() / lt[:, None])).cpu().numpy()
         del Q
         W = torch.empty_like(A)
         info = torch.zeros(1, dtype=torch.int32, device=dev)
