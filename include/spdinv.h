@@ -331,6 +331,22 @@ SPDINV_API spdinv_status spdinv_dag_task_counts(int t, int64_t out[12]);
 SPDINV_API spdinv_status spdinv_plan_tasks(int64_t n, int b, int steps, uint32_t* out, int64_t cap,
                                 int64_t* ntasks, double* crit);
 
+/* Host emulation of the persistent kernel's scheduling protocol (no GPU; no
+ * counterpart in the paper, whose runtime schedules on CPU cores).  `workers`
+ * threads stand in for CTAs: each takes the next ticket of the execution plan
+ * of the full inversion for t x t tiles (the order of spdinv_plan_tasks),
+ * waits for each input tile's readiness flag in the order the kernel reads
+ * them (bounded by wait_limit_s; a wait that runs out stops every worker),
+ * spends a seeded random 0 .. max_delay_us microseconds per chain element,
+ * and publishes its output tile's flag.  drop_task >= 0: the task with that
+ * ticket never publishes (the fault_drop_task hook of spdinv_opts).
+ *   out[0] tasks completed, out[1] tasks in the plan, out[2] protocol errors
+ *   (a flag published twice), out[3] the longest wait in microseconds.
+ * Returns SPDINV_OK when every task completed, SPDINV_ERR_TIMEOUT when a wait
+ * ran out; 1 <= t <= 256, 1 <= workers <= 1024. */
+SPDINV_API spdinv_status spdinv_plan_emulate(int t, int workers, uint64_t seed, int drop_task, double wait_limit_s,
+                                             int max_delay_us, int64_t out[4]);
+
 /* ------------------------------------------------------------------------
  * Library information
  * ------------------------------------------------------------------------ */

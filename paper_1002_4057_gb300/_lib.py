@@ -72,6 +72,7 @@ SIGNATURES = {
                                        P, c_int64, c_int64, P]),
     "spdinv_batched_tiles": (c_int, [c_int, P]),
     "spdinv_batch_shard": (c_int, [c_int, P, c_int, P, P]),
+    "spdinv_plan_emulate": (c_int, [c_int, c_int, ctypes.c_uint64, c_int, c_double, c_int, P]),
     "spdinv_mirror_lower": (c_int, [c_int, c_int64, P, c_int64, c_int64, P]),
     "spdinv_smirror_lower": (c_int, [c_int, c_int64, P, c_int64, c_int64, P]),
     "spdinv_dag_critical_path": (c_int, [c_int, c_int, P]),
@@ -169,6 +170,15 @@ def spdinv_batch_shard(sizes, world):
     st = _call("spdinv_batch_shard", n, ctypes.addressof(hn), int(world), ctypes.addressof(owner),
                ctypes.addressof(load))
     return st, list(owner)[:n], list(load)[:max(int(world), 0)]
+
+
+def spdinv_plan_emulate(t, workers, seed, drop_task=-1, wait_limit_s=5.0, max_delay_us=20):
+    """(status, [completed, tasks, protocol errors, longest wait in us]) of a
+    host emulation of the persistent kernel's scheduling protocol."""
+    out = (ctypes.c_int64 * 4)()
+    st = _call("spdinv_plan_emulate", int(t), int(workers), int(seed), int(drop_task), float(wait_limit_s),
+               int(max_delay_us), ctypes.addressof(out))
+    return st, list(out)
 
 
 def spdinv_mirror_lower(batch, n, dA, lda, stride, stream):
