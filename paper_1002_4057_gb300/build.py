@@ -13,7 +13,8 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "lib")
 LIB = os.path.join(OUT, "libspdinv.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden"]
+FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
+         "-Xcompiler", "-pthread"]
 
 
 def _nvcc():
@@ -56,7 +57,8 @@ def build(force=False, verbose=False):
         for _, err in results:
             print(err)
     tmp = LIB + ".tmp%d" % os.getpid()
-    cmd = [nvcc] + ARCH + ["-shared", "-cudart", "shared", "-o", tmp] + [o for o, _ in results]
+    cmd = [nvcc] + ARCH + ["-shared", "-cudart", "shared", "-Xcompiler", "-pthread", "-o", tmp] + \
+        [o for o, _ in results] + ["-lpthread"]
     subprocess.check_call(cmd)
     os.replace(tmp, LIB)
     return LIB
