@@ -91,10 +91,13 @@ static double wait_timeout_s(const spdinv_opts* o) {
     return 60.0;
 }
 
-// Tile 32 measured faster than 64 at every size (n = 4096, 8192, 16384: 6
-// resident CTAs per SM instead of 3, and fewer wasted flops in the diagonal
-// tiles), so it is the default.
-static int default_tile(int64_t) { return 32; }
+// Tile 32 measured faster than 64 at n = 4096, 8192 and 16384 (6 resident
+// CTAs per SM instead of 3, and fewer wasted flops in the diagonal tiles).
+// Above n = 16384 tile 64 keeps the plan's t at most n / 64: the host builds
+// the plan in O(t^3) (0.35 s at t = 512, 5 s at t = 1024) on the first call
+// with a size, and tile 64 already runs at the FP64 rate there (1084 Gflop/s
+// at n = 32768).
+static int default_tile(int64_t n) { return n <= 16384 ? 32 : 64; }
 
 // Shared body of potrf / trtri / lauum / potri (FP64).
 spdinv_status run_fp64(int64_t n, double* dA, int64_t lda, int steps, const spdinv_opts* o, int* d_info,
