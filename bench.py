@@ -28,6 +28,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "POTRI Gflop/s (n^3/inv) & % tensor peak; mixed vs FP64 speedup at 1e-10 err"
+TRAFFIC_N16384_B32 = 793344264192 + 3259657472  # DRAM bytes read + written, one launch (ncu)
 BF16_NOMINAL_TFLOPS = 2250.0
 FP64_NOMINAL_TFLOPS = 1.25
 
@@ -635,7 +636,12 @@ def main():
     achieved_tf = flops / kern_avg_s / 1e12
     roofline = {
         "bound": "tensor", "achieved": round(achieved_tf, 4), "peak": round(peak_tf, 4), "unit": "TFLOP/s",
-        "frac": round(achieved_tf / peak_tf, 4), "traffic": None,
+        "frac": round(achieved_tf / peak_tf, 4),
+        # dram__bytes_read.sum + dram__bytes_write.sum of one timed launch of this kernel at
+        # n = 16384, tile 32 (an ncu capture of this command with --profile-timed); other
+        # sizes and tiles were not captured at full size
+        "traffic": TRAFFIC_N16384_B32 if (n, b) == (16384, 32) else None,
+        "traffic_unit": "bytes per launch",
         "kernel": "potri_fp64_persistent<%d> (FP64 DMMA m8n8k4)" % b,
         "peak_note": "FP64 peak = bf16_tflops (%s) x nominal FP64/bf16 ratio 1.25/2250; "
                      "DMMA microbenchmark on this GPU: 1.04 TFLOP/s" % src,
