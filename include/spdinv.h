@@ -317,6 +317,15 @@ SPDINV_API spdinv_status spdinv_dag_critical_path(int t, int flags, int64_t out[
  * SYRK(step 3): out[0..11]. */
 SPDINV_API spdinv_status spdinv_dag_task_counts(int t, int64_t out[12]);
 
+/* Check of the planner (host only): builds the plan for t x t tiles and
+ * `steps` (as for spdinv_plan_tasks) twice -- with the bottom levels that
+ * order it computed from running maxima over the task grids (O(t^2), used for
+ * the full inversion and the selected inverse) and by walking every
+ * dependency edge (O(t^3)) -- and compares them.  out[0] = tasks, out[1] =
+ * positions where the two orders differ, out[2] = 1 if the critical path or
+ * the total work differ. */
+SPDINV_API spdinv_status spdinv_plan_check(int t, int steps, int64_t out[3]);
+
 /* The execution plan the persistent kernel runs for an order-n matrix with
  * tile b: the chain tasks (one per output tile and step; each holds its
  * whole commutative update chain, Sec. 3 "loop reversal") in the order CTAs

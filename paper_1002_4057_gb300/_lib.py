@@ -73,6 +73,7 @@ SIGNATURES = {
     "spdinv_batched_tiles": (c_int, [c_int, P]),
     "spdinv_batch_shard": (c_int, [c_int, P, c_int, P, P]),
     "spdinv_plan_emulate": (c_int, [c_int, c_int, ctypes.c_uint64, c_int, c_double, c_int, P]),
+    "spdinv_plan_check": (c_int, [c_int, c_int, P]),
     "spdinv_mirror_lower": (c_int, [c_int, c_int64, P, c_int64, c_int64, P]),
     "spdinv_smirror_lower": (c_int, [c_int, c_int64, P, c_int64, c_int64, P]),
     "spdinv_dag_critical_path": (c_int, [c_int, c_int, P]),
@@ -170,6 +171,14 @@ def spdinv_batch_shard(sizes, world):
     st = _call("spdinv_batch_shard", n, ctypes.addressof(hn), int(world), ctypes.addressof(owner),
                ctypes.addressof(load))
     return st, list(owner)[:n], list(load)[:max(int(world), 0)]
+
+
+def spdinv_plan_check(t, steps):
+    """(status, [tasks, order differences, critical-path/work difference]) of
+    the fast and the exhaustive plan builds."""
+    out = (ctypes.c_int64 * 3)()
+    st = _call("spdinv_plan_check", int(t), int(steps), ctypes.addressof(out))
+    return st, list(out)
 
 
 def spdinv_plan_emulate(t, workers, seed, drop_task=-1, wait_limit_s=5.0, max_delay_us=20):

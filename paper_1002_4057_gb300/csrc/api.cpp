@@ -93,10 +93,9 @@ static double wait_timeout_s(const spdinv_opts* o) {
 
 // Tile 32 measured faster than 64 at n = 4096, 8192 and 16384 (6 resident
 // CTAs per SM instead of 3, and fewer wasted flops in the diagonal tiles).
-// Above n = 16384 tile 64 keeps the plan's t at most n / 64: the host builds
-// the plan in O(t^3) (0.35 s at t = 512, 5 s at t = 1024) on the first call
-// with a size, and tile 64 already runs at the FP64 rate there (1084 Gflop/s
-// at n = 32768).
+// Above n = 16384 the default is the tile measured there: 64 runs at the
+// FP64 rate at n = 32768 (1084 Gflop/s), and it halves t for the first call's
+// plan build (0.15 s at t = 512, 0.64 s at t = 1024).
 static int default_tile(int64_t n) { return n <= 16384 ? 32 : 64; }
 
 // Shared body of potrf / trtri / lauum / potri (FP64).
@@ -209,6 +208,20 @@ spdinv_status spdinv_dag_task_counts(int t, int64_t out[12]) {
     if (t < 1) return SPDINV_ERR_N;
     if (!out) return SPDINV_ERR_NULL;
     dag_task_counts(t, out);
+    return SPDINV_OK;
+}
+
+spdinv_status spdinv_plan_check(int t, int steps, int64_t out[3]) {
+    if (t < 1 || t > 16383) return SPDINV_ERR_N;
+    if (steps < 0 || steps > 4) return SPDINV_ERR_UNSUPPORTED;
+    if (!out) return SPDINV_ERR_NULL;
+    const ExecPlan a = build_exec_plan(t, steps, false), b = build_exec_plan(t, steps, true);
+    int64_t diff = 0;
+    for (size_t m = 0; m < a.order.size() && m < b.order.size(); ++m) diff += a.order[m] != b.order[m];
+    out[0] = (int64_t)a.order.size();
+    out[1] = diff + (int64_t)(a.order.size() > b.order.size() ? a.order.size() - b.order.size()
+                                                               : b.order.size() - a.order.size());
+    out[2] = (a.crit != b.crit || a.work != b.work) ? 1 : 0;
     return SPDINV_OK;
 }
 

@@ -227,7 +227,7 @@ struct TaskIndex {
 
 }  // namespace
 
-ExecPlan build_exec_plan(int t, int steps) {
+ExecPlan build_exec_plan(int t, int steps, bool exhaustive) {
     ExecPlan p;
     p.t = t;
     p.steps = steps;
@@ -309,14 +309,88 @@ ExecPlan build_exec_plan(int t, int steps) {
                 break;
         }
     };
-    // Bottom levels, pushed backwards along the sequential order.
-    std::vector<double> succmax(N, 0.0), bl(N, 0.0);
+    // Bottom levels (cost plus the largest bottom level among the tasks that
+    // read this task's output), in reverse sequential order.
+    std::vector<double> bl(N, 0.0);
     double work = 0.0;
-    for (size_t r = N; r-- > 0;) {
-        const double c = cost(seq[r]);
-        work += c;
-        bl[r] = c + succmax[r];
-        for_preds(seq[r], [&](int32_t p) { succmax[p] = std::max(succmax[p], bl[r]); });
+    const bool fast = !exhaustive && (steps == STEPS_ALL || steps == STEPS_DIAG);
+    if (!fast) {  // push each task's level to its predecessors: O(t^3) edges
+        std::vector<double> succmax(N, 0.0);
+        for (size_t r = N; r-- > 0;) {
+            const double c = cost(seq[r]);
+            work += c;
+            bl[r] = c + succmax[r];
+            for_preds(seq[r], [&](int32_t p) { succmax[p] = std::max(succmax[p], bl[r]); });
+        }
+    } else {
+        // The same levels in O(t^2): the readers of each output form whole
+        // rows, columns or prefixes/suffixes of them in the task grids, so
+        // running maxima replace the edge walk (the max of the same values:
+        // the same doubles, the same order).
+        //   D(j)  <- S1off(., j), S2off(j, .), S2off(., j), S3diag(j), S3off(j, .)
+        //   L(i,j) <- S1diag(i), S1off(i, j'>j), S1off(., i), S2off(i, j), S2off(i'>i, j)
+        //   X(i,j) <- S2off(i, j'<j), S3off(i, j), S3diag(j), S3off(j, .), S3off(j<i'<i, j)
+        const size_t T = (size_t)t;
+        std::vector<double> c1d(T, 0.0), c3d(T, 0.0), g1(T * T, 0.0), g2(T * T, 0.0), g3(T * T, 0.0);
+        for (size_t r = N; r-- > 0;) work += cost(seq[r]);  // summed in the same order as above
+        auto at = [&](int i, int j) { return (size_t)i * T + (size_t)j; };
+        // Step 3 tasks have no readers: level = cost.
+        for (int i = 0; i < t; ++i) {
+            c3d[i] = cost(encode_task(K_S3_DIAG, i, i));
+            if (s3off)
+                for (int j = 0; j < i; ++j) g3[at(i, j)] = cost(encode_task(K_S3_OFF, i, j));
+        }
+        std::vector<double> row3(T, 0.0), colpre3(T * T, 0.0);  // colpre3(i, j) = max g3(i', j), j < i' < i
+        for (int j = 0; j < t; ++j) {
+            for (int k = 0; k < j; ++k) row3[j] = std::max(row3[j], g3[at(j, k)]);
+            double m = 0.0;
+            for (int i = j + 1; i < t; ++i) {
+                colpre3[at(i, j)] = m;
+                m = std::max(m, g3[at(i, j)]);
+            }
+        }
+        // Step 2, reverse sequential order: j ascending, i ascending.
+        std::vector<double> rowpre2(T, 0.0);  // max g2(i, j') over the j' < j done so far
+        for (int j = 0; j < t; ++j)
+            for (int i = j + 1; i < t; ++i) {
+                double m = std::max({rowpre2[i], g3[at(i, j)], c3d[j], row3[j], colpre3[at(i, j)]});
+                g2[at(i, j)] = cost(encode_task(K_S2_OFF, i, j)) + m;
+                rowpre2[i] = std::max(rowpre2[i], g2[at(i, j)]);
+            }
+        std::vector<double> row2(T, 0.0), col2(T, 0.0), colsuf2(T * T, 0.0);  // colsuf2(i, j) = max g2(i', j), i' > i
+        for (int j = 0; j < t; ++j) {
+            for (int k = 0; k < j; ++k) row2[j] = std::max(row2[j], g2[at(j, k)]);
+            double m = 0.0;
+            for (int i = t - 1; i > j; --i) {
+                colsuf2[at(i, j)] = m;
+                m = std::max(m, g2[at(i, j)]);
+            }
+            col2[j] = m;
+        }
+        // Step 1, reverse sequential order: j descending; S1off(i, j) for i
+        // descending, then S1diag(j).
+        std::vector<double> rowsuf1(T, 0.0), col1(T, 0.0);
+        for (int j = t - 1; j >= 0; --j) {
+            for (int i = t - 1; i > j; --i) {
+                double m = std::max({c1d[i], rowsuf1[i], col1[i], g2[at(i, j)], colsuf2[at(i, j)]});
+                g1[at(i, j)] = cost(encode_task(K_S1_OFF, i, j)) + m;
+                rowsuf1[i] = std::max(rowsuf1[i], g1[at(i, j)]);
+                col1[j] = std::max(col1[j], g1[at(i, j)]);
+            }
+            const double m = std::max({col1[j], row2[j], col2[j], c3d[j], row3[j]});
+            c1d[j] = cost(encode_task(K_S1_DIAG, j, j)) + m;
+        }
+        for (size_t r = 0; r < N; ++r) {
+            const uint32_t e = seq[r];
+            const int i = (int)task_i(e), j = (int)task_j(e);
+            switch (task_kind(e)) {
+                case K_S1_DIAG: bl[r] = c1d[j]; break;
+                case K_S1_OFF: bl[r] = g1[at(i, j)]; break;
+                case K_S2_OFF: bl[r] = g2[at(i, j)]; break;
+                case K_S3_DIAG: bl[r] = c3d[i]; break;
+                default: bl[r] = g3[at(i, j)]; break;
+            }
+        }
     }
     std::vector<uint32_t> perm(N);
     std::iota(perm.begin(), perm.end(), 0u);
