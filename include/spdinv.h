@@ -319,8 +319,8 @@ SPDINV_API spdinv_status spdinv_dag_task_counts(int t, int64_t out[12]);
 
 /* Check of the planner (host only): builds the plan for t x t tiles and
  * `steps` (as for spdinv_plan_tasks) twice -- with the bottom levels that
- * order it computed from running maxima over the task grids (O(t^2), used for
- * the full inversion and the selected inverse) and by walking every
+ * order it computed from running maxima over the task grids (O(t^2), the
+ * planner's own path for every `steps`) and by walking every
  * dependency edge (O(t^3)) -- and compares them.  out[0] = tasks, out[1] =
  * positions where the two orders differ, out[2] = 1 if the critical path or
  * the total work differ. */

@@ -95,7 +95,7 @@ static double wait_timeout_s(const spdinv_opts* o) {
 // CTAs per SM instead of 3, and fewer wasted flops in the diagonal tiles).
 // Above n = 16384 the default is the tile measured there: 64 runs at the
 // FP64 rate at n = 32768 (1084 Gflop/s), and it halves t for the first call's
-// plan build (0.15 s at t = 512, 0.64 s at t = 1024).
+// plan build (0.04 s at t = 512, 0.2 s at t = 1024).
 static int default_tile(int64_t n) { return n <= 16384 ? 32 : 64; }
 
 // Shared body of potrf / trtri / lauum / potri (FP64).

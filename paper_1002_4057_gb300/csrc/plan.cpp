@@ -313,8 +313,7 @@ ExecPlan build_exec_plan(int t, int steps, bool exhaustive) {
     // read this task's output), in reverse sequential order.
     std::vector<double> bl(N, 0.0);
     double work = 0.0;
-    const bool fast = !exhaustive && (steps == STEPS_ALL || steps == STEPS_DIAG);
-    if (!fast) {  // push each task's level to its predecessors: O(t^3) edges
+    if (exhaustive) {  // push each task's level to its predecessors: O(t^3) edges
         std::vector<double> succmax(N, 0.0);
         for (size_t r = N; r-- > 0;) {
             const double c = cost(seq[r]);
@@ -330,12 +329,15 @@ ExecPlan build_exec_plan(int t, int steps, bool exhaustive) {
         //   D(j)  <- S1off(., j), S2off(j, .), S2off(., j), S3diag(j), S3off(j, .)
         //   L(i,j) <- S1diag(i), S1off(i, j'>j), S1off(., i), S2off(i, j), S2off(i'>i, j)
         //   X(i,j) <- S2off(i, j'<j), S3off(i, j), S3diag(j), S3off(j, .), S3off(j<i'<i, j)
+        // A step that is not in the plan leaves its grids at zero (its data
+        // is ready at launch); D(j) comes from S2diag(j) in the TRTRI plan.
         const size_t T = (size_t)t;
-        std::vector<double> c1d(T, 0.0), c3d(T, 0.0), g1(T * T, 0.0), g2(T * T, 0.0), g3(T * T, 0.0);
+        std::vector<double> c1d(T, 0.0), c2d(T, 0.0), c3d(T, 0.0), g1(T * T, 0.0), g2(T * T, 0.0),
+            g3(T * T, 0.0);
         for (size_t r = N; r-- > 0;) work += cost(seq[r]);  // summed in the same order as above
         auto at = [&](int i, int j) { return (size_t)i * T + (size_t)j; };
         // Step 3 tasks have no readers: level = cost.
-        for (int i = 0; i < t; ++i) {
+        for (int i = 0; i < t && s3; ++i) {
             c3d[i] = cost(encode_task(K_S3_DIAG, i, i));
             if (s3off)
                 for (int j = 0; j < i; ++j) g3[at(i, j)] = cost(encode_task(K_S3_OFF, i, j));
@@ -351,7 +353,7 @@ ExecPlan build_exec_plan(int t, int steps, bool exhaustive) {
         }
         // Step 2, reverse sequential order: j ascending, i ascending.
         std::vector<double> rowpre2(T, 0.0);  // max g2(i, j') over the j' < j done so far
-        for (int j = 0; j < t; ++j)
+        for (int j = 0; j < t && s2; ++j)
             for (int i = j + 1; i < t; ++i) {
                 double m = std::max({rowpre2[i], g3[at(i, j)], c3d[j], row3[j], colpre3[at(i, j)]});
                 g2[at(i, j)] = cost(encode_task(K_S2_OFF, i, j)) + m;
@@ -366,11 +368,12 @@ ExecPlan build_exec_plan(int t, int steps, bool exhaustive) {
                 m = std::max(m, g2[at(i, j)]);
             }
             col2[j] = m;
+            if (s2diag) c2d[j] = cost(encode_task(K_S2_DIAG, j, j)) + std::max(row2[j], col2[j]);
         }
         // Step 1, reverse sequential order: j descending; S1off(i, j) for i
         // descending, then S1diag(j).
         std::vector<double> rowsuf1(T, 0.0), col1(T, 0.0);
-        for (int j = t - 1; j >= 0; --j) {
+        for (int j = t - 1; j >= 0 && s1; --j) {
             for (int i = t - 1; i > j; --i) {
                 double m = std::max({c1d[i], rowsuf1[i], col1[i], g2[at(i, j)], colsuf2[at(i, j)]});
                 g1[at(i, j)] = cost(encode_task(K_S1_OFF, i, j)) + m;
@@ -386,6 +389,7 @@ ExecPlan build_exec_plan(int t, int steps, bool exhaustive) {
             switch (task_kind(e)) {
                 case K_S1_DIAG: bl[r] = c1d[j]; break;
                 case K_S1_OFF: bl[r] = g1[at(i, j)]; break;
+                case K_S2_DIAG: bl[r] = c2d[j]; break;
                 case K_S2_OFF: bl[r] = g2[at(i, j)]; break;
                 case K_S3_DIAG: bl[r] = c3d[i]; break;
                 default: bl[r] = g3[at(i, j)]; break;

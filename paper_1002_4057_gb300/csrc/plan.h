@@ -39,9 +39,8 @@ struct ExecPlan {
 };
 
 // Builds the chain-task plan for t x t tiles (t <= 16383).  The bottom
-// levels that order it take O(t^2) for STEPS_ALL and STEPS_DIAG; exhaustive
-// (or any other steps value) walks every dependency edge, O(t^3) -- the same
-// result, kept to check the fast path.
+// levels that order it take O(t^2); exhaustive walks every dependency edge,
+// O(t^3) -- the same result, kept to check the fast path.
 ExecPlan build_exec_plan(int t, int steps, bool exhaustive = false);
 
 // Fine-grained DAG of Algorithm 1 / its Sec. 3 variants: critical paths.

@@ -217,12 +217,12 @@ def test_exec_plan_is_topological_and_complete(n, b, steps):
 
 
 
-@pytest.mark.parametrize("steps", [0, 4])
+@pytest.mark.parametrize("steps", [0, 1, 2, 3, 4])
 def test_fast_bottom_levels_match_the_edge_walk(steps):
-    """The plan of the full inversion (0) and of the selected inverse (4) is
-    ordered by bottom levels computed from running maxima over the task
-    grids in O(t^2); walking every dependency edge (O(t^3)) must give the same
-    order, critical path and work."""
+    """Every plan (the full inversion 0, the steps alone 1-3, the selected
+    inverse 4) is ordered by bottom levels computed from running maxima over
+    the task grids in O(t^2); walking every dependency edge (O(t^3)) must give
+    the same order, critical path and work."""
     for t in list(range(1, 41)) + [63, 64, 65, 97, 128]:
         st, (tasks, diff, cw) = L.spdinv_plan_check(t, steps)
         assert st == 0 and tasks > 0
