@@ -67,7 +67,7 @@ typedef enum {
     SPDINV_ERR_NULL = -3,         /* a required pointer is NULL */
     SPDINV_ERR_CUDA = -4,         /* a CUDA runtime call failed (see spdinv_last_cuda_error) */
     SPDINV_ERR_TIMEOUT = -5,      /* device-side: a dependency wait exceeded its limit */
-    SPDINV_ERR_UNSUPPORTED = -6,  /* an option value this build does not implement */
+    SPDINV_ERR_UNSUPPORTED = -6,  /* an option value this library does not implement */
     SPDINV_ERR_WORKSPACE = -7     /* a caller-provided buffer is too small */
 } spdinv_status;
 
@@ -76,7 +76,7 @@ typedef enum {
     SPDINV_PREC_FP64 = 0,         /* every operation in native FP64 (DMMA tensor cores) */
     SPDINV_PREC_MIXED_FP32 = 1,   /* bulk updates FP32; diagonal POTRF/TRTRI and the residual FP64 */
     SPDINV_PREC_MIXED_BF16X3 = 2  /* reserved: bulk updates as three BF16 products (returns
-                                     SPDINV_ERR_UNSUPPORTED in this build) */
+                                     SPDINV_ERR_UNSUPPORTED in this version) */
 } spdinv_precision;
 
 /* Options for spdinv_potri_ex.  Zero-initialise and set what you need. */

@@ -22,7 +22,7 @@ def declared_symbols():
     return sorted(set(re.findall(r"SPDINV_API\s+[\w\s\*]+?\b(spdinv_\w+)\s*\(", text)))
 
 
-def test_header_declares_the_north_star_entry_points():
+def test_header_declares_the_three_steps_and_the_pipelined_whole():
     names = declared_symbols()
     for n in ("spdinv_potrf", "spdinv_trtri", "spdinv_lauum", "spdinv_potri", "spdinv_potri_batched"):
         assert n in names
