@@ -81,7 +81,8 @@ typedef enum {
 
 /* Options for spdinv_potri_ex.  Zero-initialise and set what you need. */
 typedef struct {
-    int tile;            /* tile order b; 0 = automatic (64 for FP64) */
+    int tile;            /* tile order b, 32 or 64; 0 = automatic (FP64: 32 up to n = 16384,
+                            64 above; mixed precision: 64) */
     int ctas_per_sm;     /* resident CTAs per SM of the persistent kernel; 0 = automatic */
     int precision;       /* spdinv_precision */
     int refine_steps;    /* mixed precision only: residual corrections X <- X + X(I - A X); 0 = none */
@@ -177,7 +178,8 @@ SPDINV_API spdinv_status spdinv_potri_diag(int64_t n, const double* dA, int64_t 
  * (error about 1e-16 |A||X|, like the native residual;
  * SPDINV_RESIDUAL_EMULATED_MMA_SYNC the same on the
  * warp-level MMA); SPDINV_RESIDUAL_FP64 uses native FP64 MMA.
- * Uses the library workspace (may allocate on first use). */
+ * Uses the library workspace (may allocate on first use).  An unknown
+ * `residual` returns SPDINV_ERR_UNSUPPORTED. */
 SPDINV_API spdinv_status spdinv_inverse_residual(int64_t n, const double* dA, int64_t lda, const double* dX,
                                                  double* dR, int residual, cudaStream_t stream);
 
@@ -244,7 +246,8 @@ SPDINV_API spdinv_status spdinv_spotri_batched(int batch, const int* h_n, float*
  * order n, from the saved inverse X (full symmetric, column-major, ldx) and
  * the incoming gradient G (full, ldg).  Writes the full symmetric grad_A
  * (ldgrad).  Matrix k starts at element offset k*stride_* of each pointer.
- * X, G and grad_A must not overlap. */
+ * X, G and grad_A must not overlap.  0 <= batch <= 65535 (else SPDINV_ERR_N);
+ * the library workspace holds 2 batch n^2 elements (Y = X G and sym(G)). */
 SPDINV_API spdinv_status spdinv_potri_backward(int batch, int64_t n, const double* dX, int64_t ldx, int64_t stride_x,
                                     const double* dG, int64_t ldg, int64_t stride_g,
                                     double* dGrad, int64_t ldgrad, int64_t stride_grad,
@@ -280,7 +283,8 @@ SPDINV_API spdinv_status spdinv_batched_tiles(int fp32, int tiles[8]);
 /* Copies the lower triangle of `batch` column-major n x n matrices onto their
  * strictly upper triangle (A_ij = A_ji, i < j); matrix k starts at element
  * k*stride.  Used to form the full symmetric A^{-1} (no counterpart in the
- * paper, whose result is the lower triangle). */
+ * paper, whose result is the lower triangle).  0 <= batch <= 65535 (else
+ * SPDINV_ERR_N). */
 SPDINV_API spdinv_status spdinv_mirror_lower(int batch, int64_t n, double* dA, int64_t lda, int64_t stride,
                                              cudaStream_t stream);
 SPDINV_API spdinv_status spdinv_smirror_lower(int batch, int64_t n, float* dA, int64_t lda, int64_t stride,

@@ -386,6 +386,9 @@ spdinv_status run_mixed(int64_t n, double* dA, int64_t lda, const spdinv_opts* o
     const int order = o->refine_order == 0 ? 2 : o->refine_order;
     if (order < 2 || order > 8) return SPDINV_ERR_UNSUPPORTED;
     if (order > 2 && o->residual != SPDINV_RESIDUAL_EMULATED) return SPDINV_ERR_UNSUPPORTED;
+    if (o->residual != SPDINV_RESIDUAL_EMULATED && o->residual != SPDINV_RESIDUAL_EMULATED_MMA_SYNC &&
+        o->residual != SPDINV_RESIDUAL_FP64)
+        return SPDINV_ERR_UNSUPPORTED;
     const int64_t t64 = (n + b - 1) / b;
     if (t64 > 16383) return SPDINV_ERR_N;
     if (n == 0) {
@@ -409,7 +412,6 @@ spdinv_status run_mixed(int64_t n, double* dA, int64_t lda, const spdinv_opts* o
     const size_t nn = align((size_t)n * n * sizeof(double));
     const int steps = o->refine_steps;
     const bool emulated = o->residual == SPDINV_RESIDUAL_EMULATED || o->residual == SPDINV_RESIDUAL_EMULATED_MMA_SYNC;
-    if (!emulated && o->residual != SPDINV_RESIDUAL_FP64) return SPDINV_ERR_UNSUPPORTED;
     // 7 slices of 8 bits cover the 53-bit significands.  Products of slice
     // levels s + t <= 6 (28 pairs) leave an error small enough for every step
     // but the last, whose residual error stays in the result: it keeps the

@@ -1,5 +1,6 @@
 """The C-ABI library loads, exports every symbol include/spdinv.h declares,
 and rejects bad arguments synchronously (no GPU needed)."""
+import ctypes
 import os
 import re
 
@@ -72,3 +73,114 @@ def test_planner_queries_need_no_gpu(lib):
     st, cp = L.spdinv_dag_critical_path(4, 0)
     assert st == 0 and cp[:3] == [10, 9, 10]
     assert L.spdinv_dag_critical_path(0, 0)[0] == L.SPDINV_ERR_N
+
+
+def _ints(*v):
+    a = (ctypes.c_int * max(len(v), 1))(*v)
+    return a, ctypes.addressof(a)
+
+
+FAKE = 4096  # a non-NULL pointer that no argument check may dereference
+
+
+def test_potri_ex_option_errors(lib):
+    """Every option is checked before any device work."""
+    mixed = L.SPDINV_PREC_MIXED_FP32
+    bad = [
+        L.spdinv_opts(48, 0, mixed, 1, 0.0, -1, 0, 0),   # tile
+        L.spdinv_opts(64, 0, mixed, 17, 0.0, -1, 0, 0),  # correction steps
+        L.spdinv_opts(64, 0, mixed, -1, 0.0, -1, 0, 0),
+        L.spdinv_opts(64, 0, mixed, 1, 0.0, -1, 5, 0),   # residual path
+        L.spdinv_opts(64, 0, mixed, 1, 0.0, -1, -1, 0),
+        L.spdinv_opts(64, 0, 2, 1, 0.0, -1, 0, 0),       # reserved precision
+        L.spdinv_opts(64, 0, 7, 1, 0.0, -1, 0, 0),
+    ]
+    for o in bad:
+        assert L.spdinv_potri_ex(100, FAKE, 100, o, None, None) == L.SPDINV_ERR_UNSUPPORTED
+    o = L.spdinv_opts(64, 0, mixed, 1, 0.0, -1, 0, 0)
+    assert L.spdinv_potri_ex(100, FAKE, 99, o, None, None) == L.SPDINV_ERR_LDA
+    assert L.spdinv_potri_ex(100, None, 100, o, None, None) == L.SPDINV_ERR_NULL
+    assert L.spdinv_potri_ex(-1, FAKE, 100, o, None, None) == L.SPDINV_ERR_N
+    assert L.spdinv_potri_ex(0, None, 1, o, None, None) == L.SPDINV_OK
+
+
+def test_tile_grid_limit(lib):
+    """The plan encodes tile indices in 14 bits: t = ceil(n / b) <= 16383."""
+    o = L.spdinv_opts(32, 0, 0, 0, 0.0, -1, 0, 0)
+    n = 16384 * 32
+    assert L.spdinv_potri_ex(n, FAKE, n, o, None, None) == L.SPDINV_ERR_N
+    assert L.spdinv_potrf(2 * n, FAKE, 2 * n, None, None) == L.SPDINV_ERR_N  # default tile 64
+
+
+def test_potri_diag_and_noalloc_errors(lib):
+    assert L.spdinv_potri_diag(10, FAKE, 10, None, None, None) == L.SPDINV_ERR_NULL
+    assert L.spdinv_potri_diag(10, FAKE, 9, FAKE, None, None) == L.SPDINV_ERR_LDA
+    assert L.spdinv_potri_diag(-1, FAKE, 9, FAKE, None, None) == L.SPDINV_ERR_N
+    assert L.spdinv_potri_diag(0, None, 1, None, None, None) == L.SPDINV_OK
+    assert L.spdinv_potri_noalloc(1025, FAKE, 1025, None, None) == L.SPDINV_ERR_N
+    assert L.spdinv_potri_noalloc(-1, FAKE, 1, None, None) == L.SPDINV_ERR_N
+    assert L.spdinv_potri_noalloc(10, FAKE, 9, None, None) == L.SPDINV_ERR_LDA
+    assert L.spdinv_potri_noalloc(10, None, 10, None, None) == L.SPDINV_ERR_NULL
+    assert L.spdinv_potri_noalloc(0, None, 1, None, None) == L.SPDINV_OK
+
+
+def test_inverse_residual_errors(lib):
+    f = L.spdinv_inverse_residual
+    assert f(-1, FAKE, 1, FAKE, FAKE, 0, None) == L.SPDINV_ERR_N
+    assert f(8, FAKE, 7, FAKE, FAKE, 0, None) == L.SPDINV_ERR_LDA
+    for args in ((None, FAKE, FAKE), (FAKE, None, FAKE), (FAKE, FAKE, None)):
+        assert f(8, args[0], 8, args[1], args[2], 0, None) == L.SPDINV_ERR_NULL
+    assert f(8, FAKE, 8, FAKE, FAKE, 3, None) == L.SPDINV_ERR_UNSUPPORTED
+    assert f(0, None, 1, None, None, 0, None) == L.SPDINV_OK
+
+
+@pytest.mark.parametrize("fn", ["spdinv_potri_batched", "spdinv_spotri_batched"])
+def test_batched_errors(lib, fn):
+    f = getattr(L, fn)
+    n, pn = _ints(16, 32, 5)
+    ld, pld = _ints(16, 32, 5)
+    assert f(-1, pn, FAKE, pld, None, None) == L.SPDINV_ERR_N
+    assert f(0, None, None, None, None, None) == L.SPDINV_OK
+    assert f(3, None, FAKE, pld, None, None) == L.SPDINV_ERR_NULL
+    assert f(3, pn, None, pld, None, None) == L.SPDINV_ERR_NULL
+    assert f(3, pn, FAKE, None, None, None) == L.SPDINV_ERR_NULL
+    big, pbig = _ints(16, 4097, 5)
+    assert f(3, pbig, FAKE, pbig, None, None) == L.SPDINV_ERR_N
+    neg, pneg = _ints(16, -1, 5)
+    assert f(3, pneg, FAKE, pld, None, None) == L.SPDINV_ERR_N
+    short, pshort = _ints(16, 31, 5)
+    assert f(3, pn, FAKE, pshort, None, None) == L.SPDINV_ERR_LDA
+
+
+@pytest.mark.parametrize("fn", ["spdinv_potri_backward", "spdinv_spotri_backward"])
+def test_backward_errors(lib, fn):
+    f = getattr(L, fn)
+    n = 8
+
+    def call(batch, n, X=FAKE, G=FAKE, R=FAKE, ldx=8, ldg=8, ldr=8):
+        return f(batch, n, X, ldx, n * ldx, G, ldg, n * ldg, R, ldr, n * ldr, None)
+    assert call(-1, n) == L.SPDINV_ERR_N
+    assert call(1, -1) == L.SPDINV_ERR_N
+    for k in ("ldx", "ldg", "ldr"):
+        assert call(1, n, **{k: n - 1}) == L.SPDINV_ERR_LDA
+    for k in ("X", "G", "R"):
+        assert call(1, n, **{k: None}) == L.SPDINV_ERR_NULL
+    assert call(65536, n) == L.SPDINV_ERR_N
+    assert call(0, n, X=None, G=None, R=None) == L.SPDINV_OK
+    assert call(3, 0, X=None, G=None, R=None) == L.SPDINV_OK
+
+
+@pytest.mark.parametrize("fn", ["spdinv_mirror_lower", "spdinv_smirror_lower"])
+def test_mirror_errors(lib, fn):
+    f = getattr(L, fn)
+    assert f(-1, 8, FAKE, 8, 64, None) == L.SPDINV_ERR_N
+    assert f(1, -8, FAKE, 8, 64, None) == L.SPDINV_ERR_N
+    assert f(65536, 8, FAKE, 8, 64, None) == L.SPDINV_ERR_N
+    assert f(1, 8, FAKE, 7, 64, None) == L.SPDINV_ERR_LDA
+    assert f(1, 8, None, 8, 64, None) == L.SPDINV_ERR_NULL
+    assert f(0, 8, None, 8, 64, None) == L.SPDINV_OK
+    assert f(2, 0, None, 1, 0, None) == L.SPDINV_OK
+
+
+def test_batched_tiles_needs_an_output(lib):
+    assert L._call("spdinv_batched_tiles", 0, None) == L.SPDINV_ERR_NULL
