@@ -347,18 +347,27 @@ SPDINV_API spdinv_status spdinv_plan_tasks(int64_t n, int b, int steps, uint32_t
 /* Host emulation of the persistent kernel's scheduling protocol (no GPU; no
  * counterpart in the paper, whose runtime schedules on CPU cores).  `workers`
  * threads stand in for CTAs: each takes the next ticket of the execution plan
- * of the full inversion for t x t tiles (the order of spdinv_plan_tasks),
- * waits for each input tile's readiness flag in the order the kernel reads
- * them (bounded by wait_limit_s; a wait that runs out stops every worker),
- * spends a seeded random 0 .. max_delay_us microseconds per chain element,
- * and publishes its output tile's flag.  drop_task >= 0: the task with that
- * ticket never publishes (the fault_drop_task hook of spdinv_opts).
+ * for t x t tiles and `steps` (as for spdinv_plan_tasks), waits for each input
+ * tile's readiness flag in the order the kernel reads them (bounded by
+ * wait_limit_s; a wait that runs out stops every worker), spends a seeded
+ * random 0 .. max_delay_us microseconds per chain element and per tile
+ * kernel, stores its output tiles and publishes their flags.  Every tile
+ * location carries the task that last stored it, and every read checks it
+ * against what Algorithm 1 needs there (the input for A's tiles, the
+ * producing task for the renamed stores): a read before the producer stored,
+ * or after Step 3 overwrote a tile of A, is a hazard.
+ *   drop_task >= 0: the task with that ticket never publishes (the
+ *     fault_drop_task hook of spdinv_opts);
+ *   skip_wait_task >= 0: the task with that ticket reads without waiting (a
+ *     protocol with a wait missing, to show that the hazard check sees it).
  *   out[0] tasks completed, out[1] tasks in the plan, out[2] protocol errors
- *   (a flag published twice), out[3] the longest wait in microseconds.
+ *   (a flag published twice), out[3] hazards, out[4] the longest wait in
+ *   microseconds.
  * Returns SPDINV_OK when every task completed, SPDINV_ERR_TIMEOUT when a wait
- * ran out; 1 <= t <= 256, 1 <= workers <= 1024. */
-SPDINV_API spdinv_status spdinv_plan_emulate(int t, int workers, uint64_t seed, int drop_task, double wait_limit_s,
-                                             int max_delay_us, int64_t out[4]);
+ * ran out; 1 <= t <= 256, 0 <= steps <= 4, 1 <= workers <= 1024. */
+SPDINV_API spdinv_status spdinv_plan_emulate(int t, int steps, int workers, uint64_t seed, int drop_task,
+                                             int skip_wait_task, double wait_limit_s, int max_delay_us,
+                                             int64_t out[5]);
 
 /* ------------------------------------------------------------------------
  * Library information

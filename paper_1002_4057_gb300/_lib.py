@@ -72,7 +72,7 @@ SIGNATURES = {
                                        P, c_int64, c_int64, P]),
     "spdinv_batched_tiles": (c_int, [c_int, P]),
     "spdinv_batch_shard": (c_int, [c_int, P, c_int, P, P]),
-    "spdinv_plan_emulate": (c_int, [c_int, c_int, ctypes.c_uint64, c_int, c_double, c_int, P]),
+    "spdinv_plan_emulate": (c_int, [c_int, c_int, c_int, ctypes.c_uint64, c_int, c_int, c_double, c_int, P]),
     "spdinv_plan_check": (c_int, [c_int, c_int, P]),
     "spdinv_mirror_lower": (c_int, [c_int, c_int64, P, c_int64, c_int64, P]),
     "spdinv_smirror_lower": (c_int, [c_int, c_int64, P, c_int64, c_int64, P]),
@@ -181,12 +181,13 @@ def spdinv_plan_check(t, steps):
     return st, list(out)
 
 
-def spdinv_plan_emulate(t, workers, seed, drop_task=-1, wait_limit_s=5.0, max_delay_us=20):
-    """(status, [completed, tasks, protocol errors, longest wait in us]) of a
-    host emulation of the persistent kernel's scheduling protocol."""
-    out = (ctypes.c_int64 * 4)()
-    st = _call("spdinv_plan_emulate", int(t), int(workers), int(seed), int(drop_task), float(wait_limit_s),
-               int(max_delay_us), ctypes.addressof(out))
+def spdinv_plan_emulate(t, workers, seed, drop_task=-1, wait_limit_s=5.0, max_delay_us=20, steps=0,
+                        skip_wait_task=-1):
+    """(status, [completed, tasks, protocol errors, hazards, longest wait in
+    us]) of a host emulation of the persistent kernel's scheduling protocol."""
+    out = (ctypes.c_int64 * 5)()
+    st = _call("spdinv_plan_emulate", int(t), int(steps), int(workers), int(seed), int(drop_task),
+               int(skip_wait_task), float(wait_limit_s), int(max_delay_us), ctypes.addressof(out))
     return st, list(out)
 
 

@@ -3,19 +3,31 @@
 // execution plan (build_exec_plan, the order the kernel's CTAs take tasks),
 // waits -- bounded, as the kernel does -- for the readiness flag of every
 // input tile of its task in the order the kernel reads them, spends a
-// seeded random time on each chain element, and publishes its output flag.
-// Run with many worker counts and seeds, it covers the protocol's races and
-// deadlock freedom on the CPU; a dropped completion (the kernel's
-// fault_drop_task hook) must end every worker with a timeout, not a hang.
+// seeded random time on each chain element and on its own tile kernel, stores
+// its outputs and publishes its output flag.  Run with many worker counts and
+// seeds, it covers the protocol's races and deadlock freedom on the CPU; a
+// dropped completion (the kernel's fault_drop_task hook) must end every worker
+// with a timeout, not a hang.
 //
-// Inputs and outputs per task kind, as the kernel waits for and publishes
-// them (Algorithm 1 with the renamed stores B = L, C = X, D = X_jj):
-//   Step 1, diagonal j      waits L(j,k), k < j;                publishes D(j)
-//   Step 1, off-diagonal    waits (L(i,k), L(j,k)), k < j; D(j); publishes L(i,j)
-//   Step 2, off-diagonal    waits (D(i), L(i,j)); (X(i,k), L(k,j)), k = i-1 .. j+1;
-//                           D(j);                                publishes X(i,j)
-//   Step 3, off-diagonal    waits (D(i), X(i,j)); (X(k,i), X(k,j)), k > i
-//   Step 3, diagonal        waits D(i); X(k,i), k > i
+// Besides the flags, every tile location the kernel touches carries a writer
+// word: the task that last stored it (0 = the caller's input, or a copy of it
+// staged before the launch).  Every read checks that it sees the value
+// Algorithm 1 needs there -- the input for A's tiles, the producing task for
+// the renamed stores B = L, C = X, D = X_jj -- so a read before its producer
+// stored (a missing wait) or after Step 3 overwrote A (a write-after-read
+// hazard that renaming must remove) counts as a hazard.
+//
+// Inputs and outputs per task kind, as the kernel waits for, reads and
+// writes them (the standalone steps wait only for what their own launch
+// produces; their other inputs are staged):
+//   Step 1, diagonal j      A(j,j); L(j,k), k < j;                  -> D(j) [A(j,j) in potrf]
+//   Step 1, off-diagonal    A(i,j); (L(i,k), L(j,k)), k < j; D(j)   -> L(i,j) [A(i,j) in potrf]
+//   Step 2, diagonal j      A(j,j) (trtri only)                     -> D(j), A(j,j)
+//   Step 2, off-diagonal    (D(i), L(i,j)); (X(i,k), L(k,j)), k = i-1 .. j+1; D(j)
+//                                                                   -> X(i,j) [A(i,j) in trtri]
+//   Step 3, off-diagonal    (D(i), X(i,j)); (X(k,i), X(k,j)), k > i -> A(i,j)
+//   Step 3, diagonal        D(i); X(k,i), k > i                     -> A(i,i) (diag(A^{-1}) alone
+//                                                                      in the selected inverse)
 #include <atomic>
 #include <chrono>
 #include <cstdint>
@@ -30,13 +42,18 @@
 namespace spdinv {
 namespace {
 
+using Flags = std::unique_ptr<std::atomic<int>[]>;
+using Words = std::unique_ptr<std::atomic<uint32_t>[]>;
+
 struct Emu {
-    int t = 0;
+    int t = 0, steps = STEPS_ALL;
+    bool s1 = true, s2 = true, from_A = true, wait_d = true, wait_x = true;
     const std::vector<uint32_t>* tasks = nullptr;
-    std::unique_ptr<std::atomic<int>[]> fL, fX, fD;  // readiness flags of B, C, D
-    std::atomic<int> ticket{0}, abort{0}, completed{0}, order_errors{0};
+    Flags fL, fX, fD;      // readiness flags of B, C, D
+    Words wA, wB, wC, wD;  // writer words: encoded task + 1, or 0 for input / staged data
+    std::atomic<int> ticket{0}, abort{0}, completed{0}, protocol_errors{0}, hazards{0};
     std::atomic<int64_t> max_wait_us{0};
-    int drop = -1;
+    int drop = -1, skip = -1;
     double limit_s = 1.0;
     int max_delay_us = 20;
     uint64_t seed = 0;
@@ -71,8 +88,28 @@ struct Emu {
 
     void publish(std::atomic<int>& f, int tk) {
         if (tk == drop) return;  // fault injection: the consumers never see this tile
-        if (f.exchange(1, std::memory_order_release)) order_errors.fetch_add(1);  // published twice
+        if (f.exchange(1, std::memory_order_release)) protocol_errors.fetch_add(1);  // published twice
     }
+
+    static uint32_t code(uint32_t kind, int i, int j) { return encode_task(kind, (uint32_t)i, (uint32_t)j) + 1u; }
+
+    // What a read must find in each location.
+    uint32_t expect_B(int i, int j) const { return s1 ? code(K_S1_OFF, i, j) : 0u; }
+    uint32_t expect_C(int i, int j) const { return s2 ? code(K_S2_OFF, i, j) : 0u; }
+    uint32_t expect_D(int j) const {
+        if (s1) return code(K_S1_DIAG, j, j);
+        if (steps == STEPS_TRTRI) return code(K_S2_DIAG, j, j);
+        return 0u;  // lauum: staged
+    }
+
+    void check(const std::atomic<uint32_t>& w, uint32_t want) {
+        if (w.load(std::memory_order_acquire) != want) hazards.fetch_add(1);
+    }
+    void read_A(int i, int j) { check(wA[(size_t)i * t + j], 0u); }
+    void read_B(int i, int j) { check(wB[(size_t)i * t + j], expect_B(i, j)); }
+    void read_C(int i, int j) { check(wC[(size_t)i * t + j], expect_C(i, j)); }
+    void read_D(int j) { check(wD[j], expect_D(j)); }
+    static void store(std::atomic<uint32_t>& w, uint32_t c) { w.store(c, std::memory_order_release); }
 
     std::atomic<int>* L(int i, int j) { return &fL[(size_t)i * t + j]; }
     std::atomic<int>* X(int i, int j) { return &fX[(size_t)i * t + j]; }
@@ -87,66 +124,123 @@ struct Emu {
             if (tk >= n) return;
             const uint32_t e = (*tasks)[tk];
             const int kind = (int)task_kind(e), i = (int)task_i(e), j = (int)task_j(e);
+            const uint32_t me = e + 1u;
+            const bool waits = tk != skip;  // test hook: this task reads at once, without waiting
             bool ok = true;
+            // Waits for up to two flags (either may be absent), then runs one
+            // chain element.
             auto need = [&](std::atomic<int>* a, std::atomic<int>* b) {
+                if (!waits) return;
                 ok = ok && wait(a) && wait(b);
                 if (ok) work(rng);
             };
             if (kind == K_S1_DIAG) {
-                for (int k = 0; k < j && ok; ++k) need(L(j, k), nullptr);
+                read_A(j, j);
+                for (int k = 0; k < j && ok; ++k) {
+                    need(L(j, k), nullptr);
+                    if (ok) read_B(j, k);
+                }
                 if (!ok) return;
+                work(rng);  // POTRF and TRTRI of the tile
+                if (steps == STEPS_POTRF) store(wA[(size_t)j * t + j], me);
+                store(wD[j], me);
                 publish(*D(j), tk);
             } else if (kind == K_S1_OFF) {
-                for (int k = 0; k < j && ok; ++k) need(L(i, k), L(j, k));
+                read_A(i, j);
+                for (int k = 0; k < j && ok; ++k) {
+                    need(L(i, k), L(j, k));
+                    if (ok) { read_B(i, k); read_B(j, k); }
+                }
                 need(D(j), nullptr);
                 if (!ok) return;
+                read_D(j);
+                store(wB[(size_t)i * t + j], me);
+                if (steps == STEPS_POTRF) store(wA[(size_t)i * t + j], me);
                 publish(*L(i, j), tk);
+            } else if (kind == K_S2_DIAG) {
+                read_A(j, j);
+                work(rng);
+                store(wD[j], me);
+                store(wA[(size_t)j * t + j], me);
+                publish(*D(j), tk);
             } else if (kind == K_S2_OFF) {
-                need(D(i), L(i, j));
-                for (int k = i - 1; k > j && ok; --k) need(X(i, k), L(k, j));
+                need(D(i), from_A ? L(i, j) : nullptr);
+                if (ok) { read_D(i); read_B(i, j); }
+                for (int k = i - 1; k > j && ok; --k) {
+                    need(X(i, k), from_A ? L(k, j) : nullptr);
+                    if (ok) { read_C(i, k); read_B(k, j); }
+                }
                 need(D(j), nullptr);
                 if (!ok) return;
+                read_D(j);
+                store(wC[(size_t)i * t + j], me);
+                if (steps == STEPS_TRTRI) store(wA[(size_t)i * t + j], me);
                 publish(*X(i, j), tk);
             } else if (kind == K_S3_OFF) {
-                need(D(i), X(i, j));
-                for (int k = i + 1; k < t && ok; ++k) need(X(k, i), X(k, j));
+                need(wait_d ? D(i) : nullptr, wait_x ? X(i, j) : nullptr);
+                if (ok) { read_D(i); read_C(i, j); }
+                for (int k = i + 1; k < t && ok; ++k) {
+                    need(wait_x ? X(k, i) : nullptr, wait_x ? X(k, j) : nullptr);
+                    if (ok) { read_C(k, i); read_C(k, j); }
+                }
                 if (!ok) return;
+                store(wA[(size_t)i * t + j], me);
             } else if (kind == K_S3_DIAG) {
-                need(D(i), nullptr);
-                for (int k = i + 1; k < t && ok; ++k) need(X(k, i), nullptr);
+                need(wait_d ? D(i) : nullptr, nullptr);
+                if (ok) read_D(i);
+                for (int k = i + 1; k < t && ok; ++k) {
+                    need(wait_x ? X(k, i) : nullptr, nullptr);
+                    if (ok) read_C(k, i);
+                }
                 if (!ok) return;
+                if (steps != STEPS_DIAG) store(wA[(size_t)i * t + i], me);
             } else {
-                order_errors.fetch_add(1);  // no other kind in the full inversion's plan
+                protocol_errors.fetch_add(1);  // no other kind exists
             }
             completed.fetch_add(1);
         }
     }
 };
 
+template <typename W>
+W zeroed(size_t count) {
+    W a(new typename W::element_type[count]);
+    for (size_t q = 0; q < count; ++q) a[q].store(0);
+    return a;
+}
+
 }  // namespace
 }  // namespace spdinv
 
 using namespace spdinv;
 
-extern "C" SPDINV_API spdinv_status spdinv_plan_emulate(int t, int workers, uint64_t seed, int drop_task,
-                                                        double wait_limit_s, int max_delay_us, int64_t out[4]) {
+extern "C" SPDINV_API spdinv_status spdinv_plan_emulate(int t, int steps, int workers, uint64_t seed, int drop_task,
+                                                        int skip_wait_task, double wait_limit_s, int max_delay_us,
+                                                        int64_t out[5]) {
     if (t < 1 || t > 256) return SPDINV_ERR_N;
+    if (steps < STEPS_ALL || steps > STEPS_DIAG) return SPDINV_ERR_UNSUPPORTED;
     if (workers < 1 || workers > 1024 || wait_limit_s <= 0.0 || max_delay_us < 0) return SPDINV_ERR_UNSUPPORTED;
     if (!out) return SPDINV_ERR_NULL;
-    const ExecPlan plan = build_exec_plan(t, STEPS_ALL);
+    const ExecPlan plan = build_exec_plan(t, steps);
     Emu emu;
     emu.t = t;
+    emu.steps = steps;
+    emu.s1 = steps == STEPS_ALL || steps == STEPS_POTRF || steps == STEPS_DIAG;
+    emu.s2 = steps == STEPS_ALL || steps == STEPS_TRTRI || steps == STEPS_DIAG;
+    emu.from_A = emu.s1;                   // else L is staged before the launch
+    emu.wait_d = steps != STEPS_LAUUM;     // lauum stages D and C
+    emu.wait_x = steps != STEPS_LAUUM;
     emu.tasks = &plan.order;
     const size_t tt = (size_t)t * t;
-    emu.fL.reset(new std::atomic<int>[tt]);
-    emu.fX.reset(new std::atomic<int>[tt]);
-    emu.fD.reset(new std::atomic<int>[t]);
-    for (size_t q = 0; q < tt; ++q) {
-        emu.fL[q].store(0);
-        emu.fX[q].store(0);
-    }
-    for (int q = 0; q < t; ++q) emu.fD[q].store(0);
+    emu.fL = zeroed<Flags>(tt);
+    emu.fX = zeroed<Flags>(tt);
+    emu.fD = zeroed<Flags>((size_t)t);
+    emu.wA = zeroed<Words>(tt);
+    emu.wB = zeroed<Words>(tt);
+    emu.wC = zeroed<Words>(tt);
+    emu.wD = zeroed<Words>((size_t)t);
     emu.drop = drop_task;
+    emu.skip = skip_wait_task;
     emu.limit_s = wait_limit_s;
     emu.max_delay_us = max_delay_us;
     emu.seed = seed;
@@ -156,8 +250,8 @@ extern "C" SPDINV_API spdinv_status spdinv_plan_emulate(int t, int workers, uint
     for (auto& x : th) x.join();
     out[0] = emu.completed.load();
     out[1] = (int64_t)plan.order.size();
-    out[2] = emu.order_errors.load();
-    out[3] = emu.max_wait_us.load();
-    if (emu.order_errors.load()) return SPDINV_ERR_UNSUPPORTED;
+    out[2] = emu.protocol_errors.load();
+    out[3] = emu.hazards.load();
+    out[4] = emu.max_wait_us.load();
     return emu.abort.load() ? SPDINV_ERR_TIMEOUT : SPDINV_OK;
 }
