@@ -1,7 +1,8 @@
 """Pins the pins: plants one plausible mistake at a time in a temporary copy
 of the oracle (dropped term, off-by-one bound, transposed operand, wrong
-sign) and checks that the closed-form and LAPACK checks reject every mutant.
-CPU only; the committed oracle is never modified."""
+sign) and checks that the closed-form and LAPACK checks reject every mutant;
+the same for copies of its Python error measures and backward against their
+hand-derived values.  CPU only; the committed oracle is never modified."""
 import ctypes
 import os
 import subprocess
@@ -67,3 +68,49 @@ def test_mutant_is_caught(name, tmp_path):
     text = open(SRC).read()
     assert text.count(old) == 1, name
     assert not _pins_pass(_compile(text.replace(old, new), tmp_path, name))
+
+
+# Planted mistakes in the oracle's Python measures; each must fail its pin.
+PY_MUTANTS = {
+    "ratio_eps": ("lapack_ratio", "* EPS))", "* 2.0 * EPS))"),
+    "ratio_order": ("lapack_ratio", "A @ X", "X @ A"),
+    "ratio_norm": ("lapack_ratio", "np.linalg.norm(R, 1)", "np.linalg.norm(R, np.inf)"),
+    "ratio_no_n": ("lapack_ratio", "(n * np.linalg", "(np.linalg"),
+    "relF_denominator": ("rel_frobenius", "np.linalg.norm(Y))", "np.linalg.norm(X))"),
+    "backward_no_sym": ("backward", "-(M + M.T) / 2.0", "-M"),
+    "backward_sign": ("backward", "-(M + M.T) / 2.0", "(M + M.T) / 2.0"),
+    "backward_order": ("backward", "X @ G @ X", "G @ X @ X"),
+}
+
+
+def _mutated(fn_name, old=None, new=None):
+    """A fresh copy of an oracle function, with `old` replaced by `new`."""
+    import inspect
+    import textwrap
+
+    import oracle
+    src = textwrap.dedent(inspect.getsource(getattr(oracle, fn_name)))
+    if old is not None:
+        assert src.count(old) == 1, (fn_name, old)
+        src = src.replace(old, new)
+    ns = {"np": np, "EPS": oracle.EPS}
+    exec(src, ns)
+    return ns[fn_name]
+
+
+def _pin_for(fn_name):
+    import test_oracle_pins as P
+    return {"lapack_ratio": P.pin_lapack_ratio, "rel_frobenius": P.pin_rel_frobenius,
+            "backward": P.pin_backward}[fn_name]
+
+
+@pytest.mark.parametrize("fn_name", ["lapack_ratio", "rel_frobenius", "backward"])
+def test_unmutated_measure_passes(fn_name):
+    _pin_for(fn_name)(_mutated(fn_name))
+
+
+@pytest.mark.parametrize("name", sorted(PY_MUTANTS))
+def test_measure_mutant_is_caught(name):
+    fn_name, old, new = PY_MUTANTS[name]
+    with pytest.raises(AssertionError):
+        _pin_for(fn_name)(_mutated(fn_name, old, new))

@@ -276,3 +276,66 @@ def test_backward_finite_differences(n):
     X = oracle.symmetrize_lower(oracle.potri(A)[0])
     an = float(np.sum(oracle.backward(X, G) * E))
     assert abs(fd - an) <= 1e-6 * max(1.0, abs(an))
+
+
+# ------------------------------------------------------------ error measures
+# Each pin_* check takes the function under test, so that the mutant tests can
+# run the same check against planted mistakes.
+def pin_lapack_ratio(ratio):
+    """A = diag(1, 2, 4), X = A^{-1} plus a in each entry of column 0
+    (a = 2^-30, all exact): I - A X = -A E has column 0 = -(a, 2a, 4a), so
+    ||I - A X||_1 = 7a; ||A||_1 = 4; ||X||_1 = 1 + 3a.  The ratio is
+    7a / (3 * 4 * (1 + 3a) * 2^-53).  (X A instead of A X gives 3a, the
+    infinity norm 4a, eps = 2^-52 half the value.)"""
+    a = 2.0 ** -30
+    A = np.diag([1.0, 2.0, 4.0])
+    X = np.diag([1.0, 0.5, 0.25])
+    X[:, 0] += a
+    want = 7 * a / (3 * 4 * (1 + 3 * a) * 2.0 ** -53)
+    assert ratio(A, X) == pytest.approx(want, rel=1e-12)
+
+
+def pin_rel_frobenius(rel):
+    """Y = 2 I_4 (||Y||_F = 4) and X = Y plus 1 in entry (0, 1): the error
+    is 1/4; measured against X instead it would be 1/sqrt(17)."""
+    Y = 2.0 * np.eye(4)
+    X = Y.copy()
+    X[0, 1] = 1.0
+    assert rel(X, Y) == 0.25
+    assert rel(Y, X) == pytest.approx(17 ** -0.5, rel=1e-15)
+
+
+def pin_backward(backward):
+    """Diagonal X = diag(1/a) and a non-symmetric G: (X G X)_ij = G_ij /
+    (a_i a_j), so -sym(X G X)_ij = -(G_ij + G_ji) / (2 a_i a_j); the result
+    is exactly symmetric.  Then finite differences of f(A) = <G, A^{-1}>
+    along symmetric directions, which fix every symmetric gradient."""
+    a = np.array([1.0, 2.0, 4.0, 0.5])
+    G = si.rng(si.SEED_BASE + 40).standard_normal((4, 4))
+    grad = backward(np.diag(1.0 / a), G)
+    assert np.allclose(grad, -(G + G.T) / (2.0 * np.outer(a, a)), rtol=1e-15, atol=0)
+    assert np.array_equal(grad, grad.T)
+    n = 12
+    A = si.wishart_spd(n, 1.0, seed=si.SEED_BASE + 41)
+    G = si.rng(si.SEED_BASE + 42).standard_normal((n, n))
+    X = oracle.symmetrize_lower(oracle.potri(A)[0])
+    grad = backward(X, G)
+    h = 1e-5 * np.linalg.norm(A, 2)
+    for q in range(3):
+        E = si.symmetric_gaussian(n, seed=si.SEED_BASE + 43 + q)
+        fp = float(np.sum(G * oracle.symmetrize_lower(oracle.potri(A + h * E)[0])))
+        fm = float(np.sum(G * oracle.symmetrize_lower(oracle.potri(A - h * E)[0])))
+        an = float(np.sum(grad * E))
+        assert abs((fp - fm) / (2 * h) - an) <= 1e-6 * max(1.0, abs(an))
+
+
+def test_lapack_ratio_hand_value():
+    pin_lapack_ratio(oracle.lapack_ratio)
+
+
+def test_rel_frobenius_hand_value():
+    pin_rel_frobenius(oracle.rel_frobenius)
+
+
+def test_backward_nonsymmetric_gradient():
+    pin_backward(oracle.backward)
