@@ -98,12 +98,6 @@ def inverse_diag(A, info=None, stream=None):
     return d
 
 
-def mirror_lower(A):
-    """Full symmetric matrix from the lower triangle (a new tensor)."""
-    Lo = torch.tril(A)
-    return Lo + torch.tril(Lo, -1).t()
-
-
 # ---------------------------------------------------------------- batched
 class PreparedBatch:
     """The host size arrays and the device pointer array of a batch of
