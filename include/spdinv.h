@@ -40,7 +40,9 @@
  *    the dependency counters, about n*n + n*b elements) and a plan cache;
  *    both grow on demand with cudaMalloc.  A call made for the first time
  *    with a given size may therefore allocate and must come before any CUDA
- *    graph capture that later replays the same size.
+ *    graph capture that later replays the same size.  The single-matrix
+ *    calls can use a caller's buffer instead (spdinv_workspace_size,
+ *    spdinv_set_workspace).
  *  - Calls on different streams of the same device share that workspace and
  *    must not overlap in time; calls on one stream are ordered by the stream.
  */
@@ -68,7 +70,8 @@ typedef enum {
     SPDINV_ERR_CUDA = -4,         /* a CUDA runtime call failed (see spdinv_last_cuda_error) */
     SPDINV_ERR_TIMEOUT = -5,      /* device-side: a dependency wait exceeded its limit */
     SPDINV_ERR_UNSUPPORTED = -6,  /* an option value this library does not implement */
-    SPDINV_ERR_WORKSPACE = -7     /* a caller-provided buffer is too small */
+    SPDINV_ERR_WORKSPACE = -7     /* a caller-provided buffer is too small, misaligned or not
+                                     device memory of the current device */
 } spdinv_status;
 
 /* Precision of the bulk tile updates (GEMM/SYRK/TRMM). */
@@ -210,6 +213,48 @@ SPDINV_API spdinv_status spdinv_inverse_residual(int64_t n, const double* dA, in
  *    race on the array and give wrong results; order them on one stream. */
 SPDINV_API spdinv_status spdinv_potri_noalloc(int64_t n, double* dA, int64_t lda, int* d_info,
                                               cudaStream_t stream);
+
+/* ------------------------------------------------------------------------
+ * Caller-owned workspace (capture-safe use; the paper has no counterpart)
+ * ------------------------------------------------------------------------ */
+
+/* Routines for spdinv_workspace_size. */
+#define SPDINV_ROUTINE_POTRI 0            /* spdinv_potri, spdinv_potri_ex (FP64 or mixed, per opts) */
+#define SPDINV_ROUTINE_POTRF 1            /* spdinv_potrf */
+#define SPDINV_ROUTINE_TRTRI 2            /* spdinv_trtri */
+#define SPDINV_ROUTINE_LAUUM 3            /* spdinv_lauum */
+#define SPDINV_ROUTINE_POTRI_DIAG 4       /* spdinv_potri_diag */
+#define SPDINV_ROUTINE_INVERSE_RESIDUAL 5 /* spdinv_inverse_residual (opts->residual: its path) */
+
+/* Bytes of device workspace one call of `routine` on an order-n matrix uses
+ * (host only, no GPU needed).  opts (nullable) are those the call would get:
+ * spdinv_potri_ex's options for SPDINV_ROUTINE_POTRI (tile, precision,
+ * correction steps and path), and only `residual` for
+ * SPDINV_ROUTINE_INVERSE_RESIDUAL; the other routines take none.  The same
+ * argument checks as the call: an option the call would reject returns the
+ * call's status.  n == 0 needs 0 bytes.  Layout, in order, each part on a
+ * 256-byte boundary: FP64 -- status words and readiness flags
+ * (4 + 2t^2 + t ints, t = ceil(n/b)), B and C (t(t-1)/2 b x b FP64 tiles each,
+ * B absent for lauum and C for potrf), D (t tiles); mixed -- status words
+ * and flags, B, C and D as FP32 b x (b+1) tiles, the FP64 n x n matrix X
+ * (three of them with correction steps) and the BF16 slice planes. */
+SPDINV_API spdinv_status spdinv_workspace_size(int64_t n, int routine, const spdinv_opts* opts, size_t* bytes);
+
+/* Makes the single-matrix calls of the current device (potrf, trtri, lauum,
+ * potri, potri_ex, potri_diag, inverse_residual) use the caller's device
+ * buffer [d_ws, d_ws + bytes) as their workspace instead of the library's
+ * own: they then allocate no workspace, and a call that needs more than
+ * `bytes` (spdinv_workspace_size) returns SPDINV_ERR_WORKSPACE and launches
+ * nothing.  d_ws must be 256-byte aligned device (or managed) memory of the
+ * current device, else SPDINV_ERR_WORKSPACE.  d_ws == NULL returns to the
+ * library's workspace.  The caller keeps ownership: the buffer must stay
+ * valid until the work queued with it has finished, and calls whose work
+ * overlaps in time must not share it.  The plan of each (size, tile,
+ * routine) is still built, and uploaded with one allocation, by the first
+ * call with it; later calls with a caller buffer allocate nothing and can be
+ * captured in a CUDA graph.  The batched, backward and no-allocation calls
+ * keep their own buffers. */
+SPDINV_API spdinv_status spdinv_set_workspace(void* d_ws, size_t bytes);
 
 /* ------------------------------------------------------------------------
  * Many independent matrices of uneven sizes in one persistent launch

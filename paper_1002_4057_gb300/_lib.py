@@ -31,6 +31,13 @@ SPDINV_PREC_MIXED_BF16X3 = 2
 
 SPDINV_NOALLOC_MAX_N = 1024
 
+SPDINV_ROUTINE_POTRI = 0
+SPDINV_ROUTINE_POTRF = 1
+SPDINV_ROUTINE_TRTRI = 2
+SPDINV_ROUTINE_LAUUM = 3
+SPDINV_ROUTINE_POTRI_DIAG = 4
+SPDINV_ROUTINE_INVERSE_RESIDUAL = 5
+
 SPDINV_RESIDUAL_EMULATED = 0
 SPDINV_RESIDUAL_FP64 = 1
 SPDINV_RESIDUAL_EMULATED_MMA_SYNC = 2
@@ -74,6 +81,8 @@ SIGNATURES = {
     "spdinv_batch_shard": (c_int, [c_int, P, c_int, P, P]),
     "spdinv_plan_emulate": (c_int, [c_int, c_int, c_int, ctypes.c_uint64, c_int, c_int, c_double, c_int, P]),
     "spdinv_plan_check": (c_int, [c_int, c_int, P]),
+    "spdinv_workspace_size": (c_int, [c_int64, c_int, ctypes.POINTER(spdinv_opts), P]),
+    "spdinv_set_workspace": (c_int, [P, ctypes.c_size_t]),
     "spdinv_mirror_lower": (c_int, [c_int, c_int64, P, c_int64, c_int64, P]),
     "spdinv_smirror_lower": (c_int, [c_int, c_int64, P, c_int64, c_int64, P]),
     "spdinv_dag_critical_path": (c_int, [c_int, c_int, P]),
@@ -179,6 +188,18 @@ def spdinv_plan_check(t, steps):
     out = (ctypes.c_int64 * 3)()
     st = _call("spdinv_plan_check", int(t), int(steps), ctypes.addressof(out))
     return st, list(out)
+
+
+def spdinv_workspace_size(n, routine, opts=None):
+    """(status, bytes of device workspace) of one call of `routine`."""
+    out = ctypes.c_size_t(0)
+    st = _call("spdinv_workspace_size", int(n), int(routine), ctypes.byref(opts) if opts is not None else None,
+               ctypes.addressof(out))
+    return st, out.value
+
+
+def spdinv_set_workspace(d_ws, nbytes):
+    return _call("spdinv_set_workspace", d_ws, int(nbytes))
 
 
 def spdinv_plan_emulate(t, workers, seed, drop_task=-1, wait_limit_s=5.0, max_delay_us=20, steps=0,

@@ -5,6 +5,7 @@
 
 #include <atomic>
 #include <climits>
+#include <cstdint>
 #include <cstdlib>
 #include <cstring>
 #include <map>
@@ -59,6 +60,18 @@ cudaError_t DeviceState::ensure_workspace(size_t bytes) {
     return e;
 }
 
+spdinv_status DeviceState::acquire(size_t bytes, void** out) {
+    if (user_ws) {
+        if (bytes > user_bytes) return SPDINV_ERR_WORKSPACE;
+        *out = user_ws;
+        return SPDINV_OK;
+    }
+    cudaError_t e = ensure_workspace(bytes);
+    if (e != cudaSuccess) return cuda_fail(e);
+    *out = ws;
+    return SPDINV_OK;
+}
+
 cudaError_t DeviceState::exec_plan(int t, int steps, const uint32_t** d_tasks, int* ntasks) {
     const auto key = std::make_pair(t, steps);
     auto it = plans.find(key);
@@ -98,6 +111,31 @@ static double wait_timeout_s(const spdinv_opts* o) {
 // plan build (0.04 s at t = 512, 0.2 s at t = 1024).
 static int default_tile(int64_t n) { return n <= 16384 ? 32 : 64; }
 
+spdinv_status fp64_layout(int64_t n, int steps, const spdinv_opts* o, Fp64Layout* out) {
+    if (n < 0) return SPDINV_ERR_N;
+    const int b = (o && o->tile > 0) ? o->tile : default_tile(n);
+    if (b != 32 && b != 64) return SPDINV_ERR_UNSUPPORTED;
+    if (o && o->precision != SPDINV_PREC_FP64) return SPDINV_ERR_UNSUPPORTED;
+    const int64_t t64 = (n + b - 1) / b;
+    if (t64 > 16383) return SPDINV_ERR_N;
+    Fp64Layout L;
+    L.b = b;
+    L.t = (int)t64;
+    L.needB = steps != STEPS_LAUUM;
+    L.needC = steps != STEPS_POTRF;
+    if (n > 0) {
+        const size_t tile_bytes = (size_t)b * b * sizeof(double);  // a multiple of 256
+        const size_t ntri = (size_t)L.t * (L.t - 1) / 2;
+        L.ctrl = align_up(sizeof(int) * (4 + 2 * (size_t)L.t * L.t + L.t), 256);  // status words, flags
+        L.B = L.needB ? ntri * tile_bytes : 0;
+        L.C = L.needC ? ntri * tile_bytes : 0;
+        L.D = (size_t)L.t * tile_bytes;
+        L.total = L.ctrl + L.B + L.C + L.D;
+    }
+    *out = L;
+    return SPDINV_OK;
+}
+
 // Shared body of potrf / trtri / lauum / potri (FP64).
 spdinv_status run_fp64(int64_t n, double* dA, int64_t lda, int steps, const spdinv_opts* o, int* d_info,
                        cudaStream_t stream, double* d_diag) {
@@ -105,11 +143,9 @@ spdinv_status run_fp64(int64_t n, double* dA, int64_t lda, int steps, const spdi
     if (lda < (n > 1 ? n : 1)) return SPDINV_ERR_LDA;
     if (n > 0 && dA == nullptr) return SPDINV_ERR_NULL;
     if (steps == STEPS_DIAG && n > 0 && d_diag == nullptr) return SPDINV_ERR_NULL;
-    int b = (o && o->tile > 0) ? o->tile : default_tile(n);
-    if (b != 32 && b != 64) return SPDINV_ERR_UNSUPPORTED;
-    if (o && o->precision != SPDINV_PREC_FP64) return SPDINV_ERR_UNSUPPORTED;
-    const int64_t t64 = (n + b - 1) / b;
-    if (t64 > 16383) return SPDINV_ERR_N;
+    Fp64Layout W;
+    const spdinv_status ls = fp64_layout(n, steps, o, &W);
+    if (ls != SPDINV_OK) return ls;
     if (n == 0) {
         if (d_info) {
             cudaError_t e = cudaMemsetAsync(d_info, 0, sizeof(int), stream);
@@ -123,15 +159,10 @@ spdinv_status run_fp64(int64_t n, double* dA, int64_t lda, int steps, const spdi
     DeviceState& ds = device_state(dev);
     std::lock_guard<std::mutex> lk(ds.mu);
 
-    const int t = (int)t64;
-    const size_t tile_bytes = (size_t)b * b * sizeof(double);
-    const size_t ntri = (size_t)t * (t - 1) / 2;
-    const size_t ctrl_bytes = align_up(sizeof(int) * (4 + 2 * (size_t)t * t + t), 256);
-    const bool needB = steps != STEPS_LAUUM, needC = steps != STEPS_POTRF;
-    const size_t bytesB = needB ? ntri * tile_bytes : 0, bytesC = needC ? ntri * tile_bytes : 0;
-    const size_t total = ctrl_bytes + bytesB + bytesC + (size_t)t * tile_bytes;
-    e = ds.ensure_workspace(total);
-    if (e != cudaSuccess) return cuda_fail(e);
+    const int t = W.t, b = W.b;
+    void* wsp = nullptr;
+    const spdinv_status ws = ds.acquire(W.total, &wsp);
+    if (ws != SPDINV_OK) return ws;
 
     KParamsF64 p{};
     p.n = n;
@@ -140,19 +171,19 @@ spdinv_status run_fp64(int64_t n, double* dA, int64_t lda, int steps, const spdi
     p.b = b;
     p.steps = steps;
     p.A = dA;
-    char* base = static_cast<char*>(ds.ws);
+    char* base = static_cast<char*>(wsp);
     p.ctrl = reinterpret_cast<int*>(base);
     p.flags = p.ctrl + 4;
-    p.Bw = needB ? reinterpret_cast<double*>(base + ctrl_bytes) : nullptr;
-    p.Cw = needC ? reinterpret_cast<double*>(base + ctrl_bytes + bytesB) : nullptr;
-    p.Dw = reinterpret_cast<double*>(base + ctrl_bytes + bytesB + bytesC);
+    p.Bw = W.needB ? reinterpret_cast<double*>(base + W.ctrl) : nullptr;
+    p.Cw = W.needC ? reinterpret_cast<double*>(base + W.ctrl + W.B) : nullptr;
+    p.Dw = reinterpret_cast<double*>(base + W.ctrl + W.B + W.C);
     p.timeout_ns = (long long)(wait_timeout_s(o) * 1e9);
     p.drop_task = (o && o->wait_timeout_s > 0 && o->fault_drop_task >= 0) ? o->fault_drop_task : -1;
     p.diag = d_diag;
     e = ds.exec_plan(t, steps, &p.tasks, &p.ntasks);
     if (e != cudaSuccess) return cuda_fail(e);
 
-    e = cudaMemsetAsync(p.ctrl, 0, ctrl_bytes, stream);
+    e = cudaMemsetAsync(p.ctrl, 0, W.ctrl, stream);
     if (e != cudaSuccess) return cuda_fail(e);
     int grid = 0;
     const int per = (o && o->ctas_per_sm > 0) ? o->ctas_per_sm : 0;
@@ -195,6 +226,48 @@ spdinv_status spdinv_potri_diag(int64_t n, const double* dA, int64_t lda, double
                                 cudaStream_t stream) {
     // A is only read: Step 3 keeps just the diagonal of each diagonal tile.
     return run_fp64(n, const_cast<double*>(dA), lda, STEPS_DIAG, nullptr, d_info, stream, d_diag);
+}
+
+spdinv_status spdinv_workspace_size(int64_t n, int routine, const spdinv_opts* opts, size_t* bytes) {
+    if (!bytes) return SPDINV_ERR_NULL;
+    spdinv_status st = SPDINV_OK;
+    if (routine == SPDINV_ROUTINE_INVERSE_RESIDUAL) {
+        size_t need = 0;
+        st = residual_workspace(n, opts ? opts->residual : SPDINV_RESIDUAL_EMULATED, &need);
+        if (st == SPDINV_OK) *bytes = need;
+        return st;
+    }
+    if (routine < SPDINV_ROUTINE_POTRI || routine > SPDINV_ROUTINE_POTRI_DIAG) return SPDINV_ERR_UNSUPPORTED;
+    if (routine == SPDINV_ROUTINE_POTRI && opts && opts->precision != SPDINV_PREC_FP64) {
+        MixedLayout L;
+        st = mixed_layout(n, opts, &L);
+        if (st == SPDINV_OK) *bytes = L.total;
+        return st;
+    }
+    // The routine numbers are the plan's step sets; only spdinv_potri_ex takes options.
+    Fp64Layout L;
+    st = fp64_layout(n, routine, routine == SPDINV_ROUTINE_POTRI ? opts : nullptr, &L);
+    if (st == SPDINV_OK) *bytes = L.total;
+    return st;
+}
+
+spdinv_status spdinv_set_workspace(void* d_ws, size_t bytes) {
+    if (d_ws && (reinterpret_cast<uintptr_t>(d_ws) & 255u)) return SPDINV_ERR_WORKSPACE;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e);
+    if (d_ws) {
+        cudaPointerAttributes at{};
+        e = cudaPointerGetAttributes(&at, d_ws);
+        if (e != cudaSuccess) return cuda_fail(e);
+        if ((at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged) || at.device != dev)
+            return SPDINV_ERR_WORKSPACE;
+    }
+    DeviceState& ds = device_state(dev);
+    std::lock_guard<std::mutex> lk(ds.mu);
+    ds.user_ws = d_ws;
+    ds.user_bytes = d_ws ? bytes : 0;
+    return SPDINV_OK;
 }
 
 spdinv_status spdinv_dag_critical_path(int t, int flags, int64_t out[4]) {

@@ -20,13 +20,37 @@ struct DevicePlan {
 struct DeviceState {
     std::mutex mu;
     int num_sms = 0;
-    void* ws = nullptr;
+    void* ws = nullptr;       // the library's own workspace, grown on demand
     size_t ws_bytes = 0;
+    void* user_ws = nullptr;  // a caller's buffer (spdinv_set_workspace), used instead when set
+    size_t user_bytes = 0;
     int last_grid = 0;
     std::map<std::pair<int, int>, DevicePlan> plans;  // (t, steps) -> plan
     cudaError_t ensure_workspace(size_t bytes);
+    // The workspace of one call: the caller's buffer when one is set
+    // (SPDINV_ERR_WORKSPACE when it is too small; nothing is allocated), else
+    // the library's own.  Call with mu held.
+    spdinv_status acquire(size_t bytes, void** out);
     cudaError_t exec_plan(int t, int steps, const uint32_t** d_tasks, int* ntasks);
 };
+
+// Workspace layouts of the single-matrix calls (byte offsets from the
+// workspace base; every part starts on a 256-byte boundary).  The same
+// functions size the calls and answer spdinv_workspace_size.
+struct Fp64Layout {
+    int b = 0, t = 0;
+    bool needB = false, needC = false;                // the call uses the store B (L) / C (X)
+    size_t ctrl = 0, B = 0, C = 0, D = 0, total = 0;  // sizes of the parts, in this order
+};
+struct MixedLayout {
+    int b = 0, t = 0, order = 2;  // tile, tiles per side, correction order
+    size_t ctrl = 0, BC = 0, D = 0, nn = 0, oz = 0, total = 0;  // ctrl, B, C, D, X0 [, R, X1, slices]
+};
+// Argument checks that need no device (the status of the call, or
+// SPDINV_OK) and the layout of a call with those arguments.
+spdinv_status fp64_layout(int64_t n, int steps, const spdinv_opts* o, Fp64Layout* out);
+spdinv_status mixed_layout(int64_t n, const spdinv_opts* o, MixedLayout* out);
+spdinv_status residual_workspace(int64_t n, int residual, size_t* bytes);
 
 DeviceState& device_state(int dev);
 void count_launches(int k);

@@ -374,12 +374,15 @@ cudaError_t launch_mixed_dag(const KParamsMixed& p, int ctas_per_sm, int num_sms
 
 }  // namespace
 
-spdinv_status run_mixed(int64_t n, double* dA, int64_t lda, const spdinv_opts* o, int* d_info,
-                        cudaStream_t stream) {
+// 7 slices of 8 bits cover the 53-bit significands.  Products of slice
+// levels s + t <= 6 (28 pairs) leave an error small enough for every step
+// but the last, whose residual error stays in the result: it keeps the
+// levels up to 7 (34 pairs), which matches the native FP64 residual.
+constexpr int kSlices = 7, kLevels = 6, kLevelsLast = 7;
+
+spdinv_status mixed_layout(int64_t n, const spdinv_opts* o, MixedLayout* out) {
     if (n < 0) return SPDINV_ERR_N;
-    if (lda < (n > 1 ? n : 1)) return SPDINV_ERR_LDA;
-    if (n > 0 && dA == nullptr) return SPDINV_ERR_NULL;
-    if (o->precision != SPDINV_PREC_MIXED_FP32) return SPDINV_ERR_UNSUPPORTED;
+    if (!o || o->precision != SPDINV_PREC_MIXED_FP32) return SPDINV_ERR_UNSUPPORTED;
     const int b = o->tile > 0 ? o->tile : 64;
     if (b != 32 && b != 64) return SPDINV_ERR_UNSUPPORTED;
     if (o->refine_steps < 0 || o->refine_steps > 16) return SPDINV_ERR_UNSUPPORTED;
@@ -391,6 +394,48 @@ spdinv_status run_mixed(int64_t n, double* dA, int64_t lda, const spdinv_opts* o
         return SPDINV_ERR_UNSUPPORTED;
     const int64_t t64 = (n + b - 1) / b;
     if (t64 > 16383) return SPDINV_ERR_N;
+    MixedLayout L;
+    L.b = b;
+    L.t = (int)t64;
+    L.order = order;
+    if (n > 0) {
+        auto align = [](size_t v) { return (v + 255) / 256 * 256; };
+        const size_t tileb = (size_t)b * (b + 1) * sizeof(float);
+        const size_t ntri = (size_t)L.t * (L.t - 1) / 2;
+        L.ctrl = align(sizeof(int) * (4 + 2 * (size_t)L.t * L.t + L.t));
+        L.BC = align(ntri * tileb);
+        L.D = align((size_t)L.t * tileb);
+        L.nn = align((size_t)n * n * sizeof(double));
+        const int steps = o->refine_steps;
+        const bool emulated =
+            o->residual == SPDINV_RESIDUAL_EMULATED || o->residual == SPDINV_RESIDUAL_EMULATED_MMA_SYNC;
+        const bool chain = o->residual == SPDINV_RESIDUAL_EMULATED;
+        L.oz = (steps > 0 && emulated)
+                   ? align(chain ? ozaki_refine_workspace_bytes(n) : ozaki_workspace_bytes(n, kSlices))
+                   : 0;
+        L.total = L.ctrl + 2 * L.BC + L.D + L.nn * (steps > 0 ? 3 : 1) + L.oz;
+    }
+    *out = L;
+    return SPDINV_OK;
+}
+
+spdinv_status residual_workspace(int64_t n, int residual, size_t* bytes) {
+    if (n < 0) return SPDINV_ERR_N;
+    const bool emulated = residual == SPDINV_RESIDUAL_EMULATED || residual == SPDINV_RESIDUAL_EMULATED_MMA_SYNC;
+    if (!emulated && residual != SPDINV_RESIDUAL_FP64) return SPDINV_ERR_UNSUPPORTED;
+    // status words (zero: no abort) + the slices
+    *bytes = n == 0 ? 0 : 256 + (emulated ? ozaki_workspace_bytes(n, kSlices) : 0);
+    return SPDINV_OK;
+}
+
+spdinv_status run_mixed(int64_t n, double* dA, int64_t lda, const spdinv_opts* o, int* d_info,
+                        cudaStream_t stream) {
+    if (n < 0) return SPDINV_ERR_N;
+    if (lda < (n > 1 ? n : 1)) return SPDINV_ERR_LDA;
+    if (n > 0 && dA == nullptr) return SPDINV_ERR_NULL;
+    MixedLayout W;
+    const spdinv_status ls = mixed_layout(n, o, &W);
+    if (ls != SPDINV_OK) return ls;
     if (n == 0) {
         if (d_info) {
             cudaError_t e = cudaMemsetAsync(d_info, 0, sizeof(int), stream);
@@ -403,28 +448,15 @@ spdinv_status run_mixed(int64_t n, double* dA, int64_t lda, const spdinv_opts* o
     if (e != cudaSuccess) return cuda_fail(e);
     DeviceState& ds = device_state(dev);
     std::lock_guard<std::mutex> lk(ds.mu);
-    const int t = (int)t64;
-    auto align = [](size_t v) { return (v + 255) / 256 * 256; };
-    const size_t tileb = (size_t)b * (b + 1) * sizeof(float);
-    const size_t ntri = (size_t)t * (t - 1) / 2;
-    const size_t ctrl_bytes = align(sizeof(int) * (4 + 2 * (size_t)t * t + t));
-    const size_t bytesBC = align(ntri * tileb), bytesD = align((size_t)t * tileb);
-    const size_t nn = align((size_t)n * n * sizeof(double));
+    const int t = W.t, b = W.b, order = W.order;
+    const size_t ctrl_bytes = W.ctrl, bytesBC = W.BC, bytesD = W.D, nn = W.nn, oz = W.oz;
     const int steps = o->refine_steps;
     const bool emulated = o->residual == SPDINV_RESIDUAL_EMULATED || o->residual == SPDINV_RESIDUAL_EMULATED_MMA_SYNC;
-    // 7 slices of 8 bits cover the 53-bit significands.  Products of slice
-    // levels s + t <= 6 (28 pairs) leave an error small enough for every step
-    // but the last, whose residual error stays in the result: it keeps the
-    // levels up to 7 (34 pairs), which matches the native FP64 residual.
-    constexpr int kSlices = 7, kLevels = 6, kLevelsLast = 7;
     const bool chain = o->residual == SPDINV_RESIDUAL_EMULATED;  // order-p step on tcgen05
-    const size_t oz = (steps > 0 && emulated)
-                          ? align(chain ? ozaki_refine_workspace_bytes(n) : ozaki_workspace_bytes(n, kSlices))
-                          : 0;
-    const size_t total = ctrl_bytes + 2 * bytesBC + bytesD + nn * (steps > 0 ? 3 : 1) + oz;
-    e = ds.ensure_workspace(total);
-    if (e != cudaSuccess) return cuda_fail(e);
-    char* base = static_cast<char*>(ds.ws);
+    void* wsp = nullptr;
+    const spdinv_status ws = ds.acquire(W.total, &wsp);
+    if (ws != SPDINV_OK) return ws;
+    char* base = static_cast<char*>(wsp);
     KParamsMixed p{};
     p.n = n;
     p.lda = lda;
@@ -500,23 +532,24 @@ extern "C" SPDINV_API spdinv_status spdinv_inverse_residual(int64_t n, const dou
     if (lda < (n > 1 ? n : 1)) return SPDINV_ERR_LDA;
     if (n == 0) return SPDINV_OK;
     if (!dA || !dX || !dR) return SPDINV_ERR_NULL;
+    size_t need = 0;
+    const spdinv_status ls = residual_workspace(n, residual, &need);
+    if (ls != SPDINV_OK) return ls;
     const bool emulated = residual == SPDINV_RESIDUAL_EMULATED || residual == SPDINV_RESIDUAL_EMULATED_MMA_SYNC;
-    if (!emulated && residual != SPDINV_RESIDUAL_FP64) return SPDINV_ERR_UNSUPPORTED;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_fail(e);
     DeviceState& ds = device_state(dev);
     std::lock_guard<std::mutex> lk(ds.mu);
-    // status words (zero: no abort) + the slices
-    const size_t need = 256 + (emulated ? ozaki_workspace_bytes(n, 7) : 0);
-    e = ds.ensure_workspace(need);
-    if (e != cudaSuccess) return cuda_fail(e);
-    int* ctrl = static_cast<int*>(ds.ws);
+    void* wsp = nullptr;
+    const spdinv_status ws = ds.acquire(need, &wsp);
+    if (ws != SPDINV_OK) return ws;
+    int* ctrl = static_cast<int*>(wsp);
     e = cudaMemsetAsync(ctrl, 0, 256, stream);
     if (e != cudaSuccess) return cuda_fail(e);
     int launches = 0;
     if (emulated) {
-        e = ozaki_residual(n, dA, lda, dX, dR, static_cast<char*>(ds.ws) + 256, 7, 7,
+        e = ozaki_residual(n, dA, lda, dX, dR, static_cast<char*>(wsp) + 256, 7, 7,
                            residual == SPDINV_RESIDUAL_EMULATED, ctrl + 2, stream, &launches);
     } else {
         const int rt = (int)((n + RB - 1) / RB);

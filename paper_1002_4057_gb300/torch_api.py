@@ -98,6 +98,39 @@ def inverse_diag(A, info=None, stream=None):
     return d
 
 
+# ------------------------------------------------------- caller workspace
+_workspaces = {}  # device index -> the caller's buffer, kept alive while set
+
+
+def workspace_size(n, routine=L.SPDINV_ROUTINE_POTRI, tile=0, precision=0, refine_steps=0, residual=0,
+                   refine_order=0):
+    """Bytes of device workspace one call of `routine` on an order-n matrix
+    uses (the options as for potri_)."""
+    o = L.spdinv_opts(tile, 0, precision, refine_steps, 0.0, -1, residual, refine_order)
+    st, nbytes = L.spdinv_workspace_size(n, routine, o)
+    _check(st, "spdinv_workspace_size")
+    return nbytes
+
+
+def set_workspace(buf, device=None):
+    """Make the single-matrix calls on buf's device use `buf` (a contiguous
+    CUDA tensor; its bytes, from a 256-byte aligned start) as their
+    workspace, so that they allocate nothing; None returns `device`'s
+    (default: the current device's) calls to the library's own workspace.
+    The tensor is kept alive here until it is replaced."""
+    if buf is None:
+        dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+        with torch.cuda.device(dev):
+            _check(L.spdinv_set_workspace(None, 0), "spdinv_set_workspace")
+        _workspaces.pop(dev.index, None)
+        return
+    if not buf.is_cuda or not buf.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    with torch.cuda.device(buf.device):
+        _check(L.spdinv_set_workspace(buf.data_ptr(), buf.numel() * buf.element_size()), "spdinv_set_workspace")
+    _workspaces[buf.device.index] = buf
+
+
 # ---------------------------------------------------------------- batched
 class PreparedBatch:
     """The host size arrays and the device pointer array of a batch of

@@ -184,3 +184,64 @@ def test_mirror_errors(lib, fn):
 
 def test_batched_tiles_needs_an_output(lib):
     assert L._call("spdinv_batched_tiles", 0, None) == L.SPDINV_ERR_NULL
+
+
+# ------------------------------------------------------- caller workspace
+def _ws(n, routine, opts=None):
+    st, nbytes = L.spdinv_workspace_size(n, routine, opts)
+    assert st == L.SPDINV_OK, st
+    return nbytes
+
+
+def test_workspace_size_fp64_layout(lib):
+    """n = 100, tile 32: t = 4; status words and flags 4 * (4 + 2*16 + 4)
+    bytes rounded up to 256; B and C hold t(t-1)/2 = 6 tiles of 32*32*8 =
+    8192 bytes; D holds 4 tiles."""
+    tiles6, tiles4 = 6 * 8192, 4 * 8192
+    assert _ws(100, L.SPDINV_ROUTINE_POTRI) == 256 + 2 * tiles6 + tiles4
+    assert _ws(100, L.SPDINV_ROUTINE_POTRI_DIAG) == 256 + 2 * tiles6 + tiles4
+    assert _ws(100, L.SPDINV_ROUTINE_TRTRI) == 256 + 2 * tiles6 + tiles4
+    assert _ws(100, L.SPDINV_ROUTINE_POTRF) == 256 + tiles6 + tiles4  # no C
+    assert _ws(100, L.SPDINV_ROUTINE_LAUUM) == 256 + tiles6 + tiles4  # no B
+    o = L.spdinv_opts(64, 0, 0, 0, 0.0, -1, 0, 0)  # tile 64: t = 2, one 32 KB tile in B and C
+    assert _ws(100, L.SPDINV_ROUTINE_POTRI, o) == 256 + 2 * 32768 + 2 * 32768
+    # the benchmark's size: t = 512, flags 4 * 524804 bytes -> 2099456; 130816 tiles in B and C
+    assert _ws(16384, L.SPDINV_ROUTINE_POTRI) == 2099456 + 2 * 130816 * 8192 + 512 * 8192
+    assert _ws(0, L.SPDINV_ROUTINE_POTRI) == 0
+
+
+def test_workspace_size_mixed_and_residual_layout(lib):
+    """Mixed, n = 100, tile 64: t = 2; FP32 tiles of 64 x 65 floats = 16640
+    bytes (one in B, one in C, two in D); X is 100*100*8 = 80000 bytes,
+    rounded to 80128; with correction steps three such matrices and 23 BF16
+    planes of 256 x 256 (7 + 7 slices for R, 5 of R, 4 of the terms) plus
+    256 * (8 + 16) bytes of scales and 1024 bytes of pad."""
+    mixed = L.SPDINV_PREC_MIXED_FP32
+    base = 256 + 2 * 16640 + 33280
+    o = L.spdinv_opts(0, 0, mixed, 0, 0.0, -1, 0, 0)
+    assert _ws(100, L.SPDINV_ROUTINE_POTRI, o) == base + 80128
+    o = L.spdinv_opts(0, 0, mixed, 1, 0.0, -1, 0, 3)
+    planes = 23 * 65536 * 2 + 256 * 24 + 1024
+    assert _ws(100, L.SPDINV_ROUTINE_POTRI, o) == base + 3 * 80128 + planes
+    # the residual alone: 256 bytes of status words, plus 2 x 7 slice planes,
+    # 256 ints and 256 64-bit maxima per side and 1024 bytes of pad when emulated
+    r = L.SPDINV_ROUTINE_INVERSE_RESIDUAL
+    assert _ws(100, r, L.spdinv_opts(0, 0, 0, 0, 0.0, -1, L.SPDINV_RESIDUAL_FP64, 0)) == 256
+    assert _ws(100, r) == 256 + 14 * 65536 * 2 + 2 * 256 * 4 + 2 * 256 * 8 + 1024
+
+
+def test_workspace_size_errors(lib):
+    f = L.spdinv_workspace_size
+    assert f(-1, 0)[0] == L.SPDINV_ERR_N
+    assert f(10, 6)[0] == L.SPDINV_ERR_UNSUPPORTED
+    assert f(10, -1)[0] == L.SPDINV_ERR_UNSUPPORTED
+    assert f(10, 0, L.spdinv_opts(48, 0, 0, 0, 0.0, -1, 0, 0))[0] == L.SPDINV_ERR_UNSUPPORTED
+    assert f(10, 0, L.spdinv_opts(0, 0, 2, 0, 0.0, -1, 0, 0))[0] == L.SPDINV_ERR_UNSUPPORTED  # reserved BF16x3
+    assert f(10, 0, L.spdinv_opts(0, 0, 1, 1, 0.0, -1, 0, 9))[0] == L.SPDINV_ERR_UNSUPPORTED  # order 9
+    assert f(10, 5, L.spdinv_opts(0, 0, 0, 0, 0.0, -1, 7, 0))[0] == L.SPDINV_ERR_UNSUPPORTED  # residual path
+    assert f(32 * 16384, 0, L.spdinv_opts(32, 0, 0, 0, 0.0, -1, 0, 0))[0] == L.SPDINV_ERR_N
+    assert L._call("spdinv_workspace_size", 10, 0, None, None) == L.SPDINV_ERR_NULL
+
+
+def test_set_workspace_rejects_a_misaligned_buffer(lib):
+    assert L.spdinv_set_workspace(4096 + 16, 1 << 20) == L.SPDINV_ERR_WORKSPACE

@@ -253,3 +253,55 @@ def test_full_size_n16384_sampled(T, gpu):
         err = np.linalg.norm(Xc - ref) / np.linalg.norm(ref)
         assert err <= 1e-10, (b, err)
         del A, Lo
+
+
+def test_caller_workspace_and_graph_capture(T, gpu):
+    """spdinv_set_workspace: the FP64 and the mixed inversion run in a
+    caller's buffer of spdinv_workspace_size bytes and match the oracle; a
+    buffer 256 bytes too small is refused before any work; with the plan
+    built by a first call, a call in the caller's buffer is captured in a
+    CUDA graph and replayed."""
+    import torch
+    n = 300
+    A, _, _ = si.spectral_spd(n, 1e2, seed=si.SEED_BASE + 50)
+    M, oinfo = oracle.potri(A)
+    assert oinfo == 0
+    ref = oracle.symmetrize_lower(M)
+    need = T.workspace_size(n)
+    need_mixed = T.workspace_size(n, precision=1, refine_steps=1, refine_order=3)
+    buf = torch.empty(max(need, need_mixed), dtype=torch.uint8, device=gpu)
+    T.set_workspace(buf)
+    try:
+        dA = to_dev(A, gpu)
+        assert int(T.potri_(dA).item()) == 0
+        assert oracle.rel_frobenius(full_from_lower(lower_np(dA)), ref) <= 1e-10
+        dA = to_dev(A, gpu)
+        assert int(T.potri_(dA, precision=1, refine_steps=1, refine_order=3).item()) == 0
+        assert oracle.rel_frobenius(full_from_lower(lower_np(dA)), ref) <= 1e-10
+
+        T.set_workspace(buf[:need - 256])
+        with pytest.raises(T.SpdinvError, match="SPDINV_ERR_WORKSPACE"):
+            T.potri_(to_dev(A, gpu))
+
+        T.set_workspace(buf[:need])
+        dA = to_dev(A, gpu)
+        orig = dA.clone()
+        info = torch.zeros(1, dtype=torch.int32, device=gpu)
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            T.potri_(dA, info=info, stream=s)
+        torch.cuda.current_stream().wait_stream(s)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            T.potri_(dA, info=info)
+        for _ in range(2):
+            dA.copy_(orig)
+            info.fill_(-1)
+            g.replay()
+            torch.cuda.synchronize()
+            assert int(info.item()) == 0
+            assert oracle.rel_frobenius(full_from_lower(lower_np(dA)), ref) <= 1e-10
+    finally:
+        T.set_workspace(None)
