@@ -45,6 +45,14 @@
  *    spdinv_set_workspace).
  *  - Calls on different streams of the same device share that workspace and
  *    must not overlap in time; calls on one stream are ordered by the stream.
+ *  - Environment (read once per process):
+ *      SPDINV_LOG=1       each call that returns an error status prints one
+ *                         line to stderr (name, size, status, CUDA error
+ *                         text); =2 every call.  Device-side results
+ *                         (d_info) are not known at return and not logged.
+ *      SPDINV_TILE=32|64  the default tile of the FP64 single-matrix calls.
+ *      SPDINV_WAIT_TIMEOUT_S  the default limit of one dependency wait (60 s).
+ *      SPDINV_BATCHED_TILE=16|32|64  one tile for every batched size class.
  */
 #ifndef SPDINV_H
 #define SPDINV_H

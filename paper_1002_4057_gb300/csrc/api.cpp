@@ -6,6 +6,7 @@
 #include <atomic>
 #include <climits>
 #include <cstdint>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <map>
@@ -32,6 +33,45 @@ void count_launches(int k) { g_launches.fetch_add((uint64_t)k, std::memory_order
 spdinv_status cuda_fail(cudaError_t e) {
     g_last_cuda_error = cudaGetErrorString(e);
     return SPDINV_ERR_CUDA;
+}
+
+namespace {
+const char* status_name(spdinv_status st) {
+    switch (st) {
+        case SPDINV_OK: return "SPDINV_OK";
+        case SPDINV_ERR_N: return "SPDINV_ERR_N";
+        case SPDINV_ERR_LDA: return "SPDINV_ERR_LDA";
+        case SPDINV_ERR_NULL: return "SPDINV_ERR_NULL";
+        case SPDINV_ERR_CUDA: return "SPDINV_ERR_CUDA";
+        case SPDINV_ERR_TIMEOUT: return "SPDINV_ERR_TIMEOUT";
+        case SPDINV_ERR_UNSUPPORTED: return "SPDINV_ERR_UNSUPPORTED";
+        case SPDINV_ERR_WORKSPACE: return "SPDINV_ERR_WORKSPACE";
+    }
+    return "unknown status";
+}
+
+int log_level() {
+    static const int level = [] {
+        const char* env = std::getenv("SPDINV_LOG");
+        return env ? std::atoi(env) : 0;
+    }();
+    return level;
+}
+
+std::mutex g_log_mu;
+}  // namespace
+
+spdinv_status log_status(const char* fn, const char* size_name, int64_t size, spdinv_status st) {
+    const int level = log_level();
+    if (level >= 2 || (level >= 1 && st != SPDINV_OK)) {
+        std::lock_guard<std::mutex> lk(g_log_mu);
+        if (st == SPDINV_ERR_CUDA)
+            std::fprintf(stderr, "[spdinv] %s %s=%lld: %s (%s)\n", fn, size_name, (long long)size, status_name(st),
+                         g_last_cuda_error.c_str());
+        else
+            std::fprintf(stderr, "[spdinv] %s %s=%lld: %s\n", fn, size_name, (long long)size, status_name(st));
+    }
+    return st;
 }
 
 DeviceState& device_state(int dev) {
@@ -109,7 +149,16 @@ static double wait_timeout_s(const spdinv_opts* o) {
 // Above n = 16384 the default is the tile measured there: 64 runs at the
 // FP64 rate at n = 32768 (1084 Gflop/s), and it halves t for the first call's
 // plan build (0.04 s at t = 512, 0.2 s at t = 1024).
-static int default_tile(int64_t n) { return n <= 16384 ? 32 : 64; }
+// SPDINV_TILE=32|64 in the environment overrides it.
+static int default_tile(int64_t n) {
+    static const int forced = [] {
+        const char* env = std::getenv("SPDINV_TILE");
+        const int v = env ? std::atoi(env) : 0;
+        return (v == 32 || v == 64) ? v : 0;
+    }();
+    if (forced) return forced;
+    return n <= 16384 ? 32 : 64;
+}
 
 spdinv_status fp64_layout(int64_t n, int steps, const spdinv_opts* o, Fp64Layout* out) {
     if (n < 0) return SPDINV_ERR_N;
@@ -201,31 +250,33 @@ using namespace spdinv;
 extern "C" {
 
 spdinv_status spdinv_potrf(int64_t n, double* dA, int64_t lda, int* d_info, cudaStream_t stream) {
-    return run_fp64(n, dA, lda, STEPS_POTRF, nullptr, d_info, stream);
+    return log_status("spdinv_potrf", "n", n, run_fp64(n, dA, lda, STEPS_POTRF, nullptr, d_info, stream));
 }
 
 spdinv_status spdinv_trtri(int64_t n, double* dA, int64_t lda, int* d_info, cudaStream_t stream) {
-    return run_fp64(n, dA, lda, STEPS_TRTRI, nullptr, d_info, stream);
+    return log_status("spdinv_trtri", "n", n, run_fp64(n, dA, lda, STEPS_TRTRI, nullptr, d_info, stream));
 }
 
 spdinv_status spdinv_lauum(int64_t n, double* dA, int64_t lda, cudaStream_t stream) {
-    return run_fp64(n, dA, lda, STEPS_LAUUM, nullptr, nullptr, stream);
+    return log_status("spdinv_lauum", "n", n, run_fp64(n, dA, lda, STEPS_LAUUM, nullptr, nullptr, stream));
 }
 
 spdinv_status spdinv_potri(int64_t n, double* dA, int64_t lda, int* d_info, cudaStream_t stream) {
-    return run_fp64(n, dA, lda, STEPS_ALL, nullptr, d_info, stream);
+    return log_status("spdinv_potri", "n", n, run_fp64(n, dA, lda, STEPS_ALL, nullptr, d_info, stream));
 }
 
 spdinv_status spdinv_potri_ex(int64_t n, double* dA, int64_t lda, const spdinv_opts* opts, int* d_info,
                               cudaStream_t stream) {
-    if (opts && opts->precision != SPDINV_PREC_FP64) return run_mixed(n, dA, lda, opts, d_info, stream);
-    return run_fp64(n, dA, lda, STEPS_ALL, opts, d_info, stream);
+    if (opts && opts->precision != SPDINV_PREC_FP64)
+        return log_status("spdinv_potri_ex", "n", n, run_mixed(n, dA, lda, opts, d_info, stream));
+    return log_status("spdinv_potri_ex", "n", n, run_fp64(n, dA, lda, STEPS_ALL, opts, d_info, stream));
 }
 
 spdinv_status spdinv_potri_diag(int64_t n, const double* dA, int64_t lda, double* d_diag, int* d_info,
                                 cudaStream_t stream) {
     // A is only read: Step 3 keeps just the diagonal of each diagonal tile.
-    return run_fp64(n, const_cast<double*>(dA), lda, STEPS_DIAG, nullptr, d_info, stream, d_diag);
+    return log_status("spdinv_potri_diag", "n", n,
+                      run_fp64(n, const_cast<double*>(dA), lda, STEPS_DIAG, nullptr, d_info, stream, d_diag));
 }
 
 spdinv_status spdinv_workspace_size(int64_t n, int routine, const spdinv_opts* opts, size_t* bytes) {
@@ -251,7 +302,7 @@ spdinv_status spdinv_workspace_size(int64_t n, int routine, const spdinv_opts* o
     return st;
 }
 
-spdinv_status spdinv_set_workspace(void* d_ws, size_t bytes) {
+static spdinv_status set_workspace(void* d_ws, size_t bytes) {
     if (d_ws && (reinterpret_cast<uintptr_t>(d_ws) & 255u)) return SPDINV_ERR_WORKSPACE;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -268,6 +319,10 @@ spdinv_status spdinv_set_workspace(void* d_ws, size_t bytes) {
     ds.user_ws = d_ws;
     ds.user_bytes = d_ws ? bytes : 0;
     return SPDINV_OK;
+}
+
+spdinv_status spdinv_set_workspace(void* d_ws, size_t bytes) {
+    return log_status("spdinv_set_workspace", "bytes", (int64_t)bytes, set_workspace(d_ws, bytes));
 }
 
 spdinv_status spdinv_dag_critical_path(int t, int flags, int64_t out[4]) {

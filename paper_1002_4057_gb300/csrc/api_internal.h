@@ -55,6 +55,9 @@ spdinv_status residual_workspace(int64_t n, int residual, size_t* bytes);
 DeviceState& device_state(int dev);
 void count_launches(int k);
 spdinv_status cuda_fail(cudaError_t e);
+// With SPDINV_LOG=1 in the environment, a call that returns an error status
+// prints one line to stderr (SPDINV_LOG=2: every call); returns st.
+spdinv_status log_status(const char* fn, const char* size_name, int64_t size, spdinv_status st);
 // d_diag: STEPS_DIAG only, receives diag(A^{-1}).
 spdinv_status run_fp64(int64_t n, double* dA, int64_t lda, int steps, const spdinv_opts* o, int* d_info,
                        cudaStream_t stream, double* d_diag = nullptr);

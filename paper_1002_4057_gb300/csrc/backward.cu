@@ -231,13 +231,13 @@ extern "C" {
 SPDINV_API spdinv_status spdinv_potri_backward(int batch, int64_t n, const double* dX, int64_t ldx, int64_t sx,
                                                const double* dG, int64_t ldg, int64_t sg, double* dGrad,
                                                int64_t ldr, int64_t sr, cudaStream_t stream) {
-    return run_backward<double>(batch, n, dX, ldx, sx, dG, ldg, sg, dGrad, ldr, sr, stream);
+    return log_status("spdinv_potri_backward", "n", n, run_backward<double>(batch, n, dX, ldx, sx, dG, ldg, sg, dGrad, ldr, sr, stream));
 }
 
 SPDINV_API spdinv_status spdinv_spotri_backward(int batch, int64_t n, const float* dX, int64_t ldx, int64_t sx,
                                                 const float* dG, int64_t ldg, int64_t sg, float* dGrad,
                                                 int64_t ldr, int64_t sr, cudaStream_t stream) {
-    return run_backward<float>(batch, n, dX, ldx, sx, dG, ldg, sg, dGrad, ldr, sr, stream);
+    return log_status("spdinv_spotri_backward", "n", n, run_backward<float>(batch, n, dX, ldx, sx, dG, ldg, sg, dGrad, ldr, sr, stream));
 }
 
 }  // extern "C"

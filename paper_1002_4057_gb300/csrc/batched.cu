@@ -665,12 +665,12 @@ extern "C" {
 
 SPDINV_API spdinv_status spdinv_potri_batched(int batch, const int* h_n, double* const* d_Aptrs, const int* h_lda,
                                               int* d_info, cudaStream_t stream) {
-    return run_batched<double>(batch, h_n, d_Aptrs, h_lda, d_info, stream);
+    return log_status("spdinv_potri_batched", "batch", batch, run_batched<double>(batch, h_n, d_Aptrs, h_lda, d_info, stream));
 }
 
 SPDINV_API spdinv_status spdinv_spotri_batched(int batch, const int* h_n, float* const* d_Aptrs, const int* h_lda,
                                                int* d_info, cudaStream_t stream) {
-    return run_batched<float>(batch, h_n, d_Aptrs, h_lda, d_info, stream);
+    return log_status("spdinv_spotri_batched", "batch", batch, run_batched<float>(batch, h_n, d_Aptrs, h_lda, d_info, stream));
 }
 
 SPDINV_API spdinv_status spdinv_batch_shard(int batch, const int* h_n, int world, int* owner, double* load) {

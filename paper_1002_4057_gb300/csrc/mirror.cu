@@ -53,10 +53,10 @@ using namespace spdinv;
 extern "C" {
 SPDINV_API spdinv_status spdinv_mirror_lower(int batch, int64_t n, double* dA, int64_t lda, int64_t stride,
                                              cudaStream_t stream) {
-    return run_mirror<double>(batch, n, dA, lda, stride, stream);
+    return log_status("spdinv_mirror_lower", "n", n, run_mirror<double>(batch, n, dA, lda, stride, stream));
 }
 SPDINV_API spdinv_status spdinv_smirror_lower(int batch, int64_t n, float* dA, int64_t lda, int64_t stride,
                                               cudaStream_t stream) {
-    return run_mirror<float>(batch, n, dA, lda, stride, stream);
+    return log_status("spdinv_smirror_lower", "n", n, run_mirror<float>(batch, n, dA, lda, stride, stream));
 }
 }

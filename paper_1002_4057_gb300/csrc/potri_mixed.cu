@@ -526,7 +526,7 @@ spdinv_status run_mixed(int64_t n, double* dA, int64_t lda, const spdinv_opts* o
 
 using namespace spdinv;
 
-extern "C" SPDINV_API spdinv_status spdinv_inverse_residual(int64_t n, const double* dA, int64_t lda, const double* dX,
+static spdinv_status inverse_residual_impl(int64_t n, const double* dA, int64_t lda, const double* dX,
                                                             double* dR, int residual, cudaStream_t stream) {
     if (n < 0) return SPDINV_ERR_N;
     if (lda < (n > 1 ? n : 1)) return SPDINV_ERR_LDA;
@@ -564,4 +564,9 @@ extern "C" SPDINV_API spdinv_status spdinv_inverse_residual(int64_t n, const dou
     if (e != cudaSuccess) return cuda_fail(e);
     count_launches(launches);
     return SPDINV_OK;
+}
+
+extern "C" SPDINV_API spdinv_status spdinv_inverse_residual(int64_t n, const double* dA, int64_t lda, const double* dX,
+                                                            double* dR, int residual, cudaStream_t stream) {
+    return log_status("spdinv_inverse_residual", "n", n, inverse_residual_impl(n, dA, lda, dX, dR, residual, stream));
 }

@@ -84,7 +84,7 @@ cudaError_t scratch_for(int dev, void** addr, int* num_sms) {
 
 using namespace spdinv;
 
-extern "C" SPDINV_API spdinv_status spdinv_potri_noalloc(int64_t n, double* dA, int64_t lda, int* d_info,
+static spdinv_status potri_noalloc_impl(int64_t n, double* dA, int64_t lda, int* d_info,
                                                          cudaStream_t stream) {
     if (n < 0 || n > SPDINV_NOALLOC_MAX_N) return SPDINV_ERR_N;
     if (lda < (n > 1 ? n : 1)) return SPDINV_ERR_LDA;
@@ -139,4 +139,9 @@ extern "C" SPDINV_API spdinv_status spdinv_potri_noalloc(int64_t n, double* dA, 
     if (e != cudaSuccess) return cuda_fail(e);
     count_launches(2 + (d_info ? 1 : 0));
     return SPDINV_OK;
+}
+
+extern "C" SPDINV_API spdinv_status spdinv_potri_noalloc(int64_t n, double* dA, int64_t lda, int* d_info,
+                                                         cudaStream_t stream) {
+    return log_status("spdinv_potri_noalloc", "n", n, potri_noalloc_impl(n, dA, lda, d_info, stream));
 }

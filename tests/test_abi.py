@@ -245,3 +245,39 @@ def test_workspace_size_errors(lib):
 
 def test_set_workspace_rejects_a_misaligned_buffer(lib):
     assert L.spdinv_set_workspace(4096 + 16, 1 << 20) == L.SPDINV_ERR_WORKSPACE
+
+
+def _run_py(code, **env):
+    import subprocess
+    import sys
+    e = dict(os.environ)
+    e.update(env)
+    return subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=e, capture_output=True, text=True,
+                          timeout=120, check=True)
+
+
+_CALLS = ("from paper_1002_4057_gb300 import _lib as L\n"
+          "L.spdinv_potri(-1, None, 1, None, None)\n"
+          "L.spdinv_potri(0, None, 1, None, None)\n"
+          "L.spdinv_potri_batched(-2, None, None, None, None, None)\n")
+
+
+def test_log_flag(lib):
+    """SPDINV_LOG=1: one stderr line per call that returns an error status;
+    SPDINV_LOG=2: every call; unset: nothing."""
+    quiet = _run_py(_CALLS)
+    assert "[spdinv]" not in quiet.stderr
+    errs = [l for l in _run_py(_CALLS, SPDINV_LOG="1").stderr.splitlines() if l.startswith("[spdinv]")]
+    assert errs == ["[spdinv] spdinv_potri n=-1: SPDINV_ERR_N",
+                    "[spdinv] spdinv_potri_batched batch=-2: SPDINV_ERR_N"]
+    every = [l for l in _run_py(_CALLS, SPDINV_LOG="2").stderr.splitlines() if l.startswith("[spdinv]")]
+    assert every[1] == "[spdinv] spdinv_potri n=0: SPDINV_OK" and len(every) == 3
+
+
+def test_tile_override(lib):
+    """SPDINV_TILE=64 replaces the default tile 32 at n = 16384 (t = 256:
+    flags 4 * 131332 bytes -> 525568; 32640 tiles of 32 KB in B and C)."""
+    code = ("from paper_1002_4057_gb300 import _lib as L\n"
+            "print(L.spdinv_workspace_size(16384, 0)[1])\n")
+    assert int(_run_py(code, SPDINV_TILE="64").stdout) == 525568 + 2 * 32640 * 32768 + 256 * 32768
+    assert int(_run_py(code, SPDINV_TILE="48").stdout) == _ws(16384, L.SPDINV_ROUTINE_POTRI)  # ignored
