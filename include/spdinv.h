@@ -423,6 +423,20 @@ SPDINV_API spdinv_status spdinv_plan_emulate(int t, int steps, int workers, uint
                                              int64_t out[5]);
 
 /* ------------------------------------------------------------------------
+ * Debugging
+ * ------------------------------------------------------------------------ */
+
+/* Fill the renamed stores B, C and D of every FP64 single-matrix call with
+ * NaN (all bits set) before its kernel runs, so that a tile read before it
+ * was written turns the result into NaN instead of passing unseen. */
+#define SPDINV_DEBUG_POISON 1u
+
+/* Sets the debug flags of the process (SPDINV_DEBUG_* ORed; the initial value
+ * is SPDINV_DEBUG from the environment, else 0) and returns the previous
+ * ones.  Host only; takes effect for calls made after it returns. */
+SPDINV_API unsigned spdinv_set_debug_flags(unsigned flags);
+
+/* ------------------------------------------------------------------------
  * Library information
  * ------------------------------------------------------------------------ */
 

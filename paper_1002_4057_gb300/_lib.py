@@ -31,6 +31,8 @@ SPDINV_PREC_MIXED_BF16X3 = 2
 
 SPDINV_NOALLOC_MAX_N = 1024
 
+SPDINV_DEBUG_POISON = 1
+
 SPDINV_ROUTINE_POTRI = 0
 SPDINV_ROUTINE_POTRF = 1
 SPDINV_ROUTINE_TRTRI = 2
@@ -88,6 +90,7 @@ SIGNATURES = {
     "spdinv_dag_critical_path": (c_int, [c_int, c_int, P]),
     "spdinv_dag_task_counts": (c_int, [c_int, P]),
     "spdinv_plan_tasks": (c_int, [c_int64, c_int, c_int, P, c_int64, P, P]),
+    "spdinv_set_debug_flags": (ctypes.c_uint, [ctypes.c_uint]),
     "spdinv_last_cuda_error": (ctypes.c_char_p, []),
     "spdinv_kernel_launches": (ctypes.c_uint64, []),
     "spdinv_version": (c_int, []),
@@ -242,6 +245,11 @@ def spdinv_plan_tasks(n, b, steps):
     st = _call("spdinv_plan_tasks", n, b, steps, ctypes.addressof(buf), cnt.value, ctypes.addressof(cnt),
                ctypes.addressof(crit))
     return st, list(buf)[:cnt.value], crit.value
+
+
+def spdinv_set_debug_flags(flags):
+    """Sets the process's debug flags; returns the previous ones."""
+    return _call("spdinv_set_debug_flags", int(flags))
 
 
 def spdinv_last_cuda_error():

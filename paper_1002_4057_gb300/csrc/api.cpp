@@ -59,6 +59,14 @@ int log_level() {
 }
 
 std::mutex g_log_mu;
+
+std::atomic<unsigned>& debug_flags() {
+    static std::atomic<unsigned> flags{[] {
+        const char* env = std::getenv("SPDINV_DEBUG");
+        return env ? (unsigned)std::strtoul(env, nullptr, 0) : 0u;
+    }()};
+    return flags;
+}
 }  // namespace
 
 spdinv_status log_status(const char* fn, const char* size_name, int64_t size, spdinv_status st) {
@@ -212,6 +220,10 @@ spdinv_status run_fp64(int64_t n, double* dA, int64_t lda, int steps, const spdi
     void* wsp = nullptr;
     const spdinv_status ws = ds.acquire(W.total, &wsp);
     if (ws != SPDINV_OK) return ws;
+    if (debug_flags().load(std::memory_order_relaxed) & SPDINV_DEBUG_POISON) {
+        e = cudaMemsetAsync(static_cast<char*>(wsp) + W.ctrl, 0xFF, W.total - W.ctrl, stream);  // B, C, D
+        if (e != cudaSuccess) return cuda_fail(e);
+    }
 
     KParamsF64 p{};
     p.n = n;
@@ -367,6 +379,8 @@ spdinv_status spdinv_plan_tasks(int64_t n, int b, int steps, uint32_t* out, int6
     if (m > 0) std::memcpy(out, p.order.data(), sizeof(uint32_t) * (size_t)m);
     return SPDINV_OK;
 }
+
+unsigned spdinv_set_debug_flags(unsigned flags) { return debug_flags().exchange(flags); }
 
 const char* spdinv_last_cuda_error(void) { return g_last_cuda_error.c_str(); }
 

@@ -281,3 +281,12 @@ def test_tile_override(lib):
             "print(L.spdinv_workspace_size(16384, 0)[1])\n")
     assert int(_run_py(code, SPDINV_TILE="64").stdout) == 525568 + 2 * 32640 * 32768 + 256 * 32768
     assert int(_run_py(code, SPDINV_TILE="48").stdout) == _ws(16384, L.SPDINV_ROUTINE_POTRI)  # ignored
+
+
+def test_debug_flags_round_trip(lib):
+    old = L.spdinv_set_debug_flags(L.SPDINV_DEBUG_POISON)
+    try:
+        assert L.spdinv_set_debug_flags(0) == L.SPDINV_DEBUG_POISON
+        assert L.spdinv_set_debug_flags(0) == 0
+    finally:
+        L.spdinv_set_debug_flags(old)

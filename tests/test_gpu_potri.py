@@ -305,3 +305,31 @@ def test_caller_workspace_and_graph_capture(T, gpu):
             assert oracle.rel_frobenius(full_from_lower(lower_np(dA)), ref) <= 1e-10
     finally:
         T.set_workspace(None)
+
+
+@pytest.mark.parametrize("n", [1, 33, 100, 257])
+def test_poisoned_stores_are_never_read_unwritten(T, gpu, n):
+    """SPDINV_DEBUG_POISON: B, C and D start as NaN in every call, so a tile
+    read before its producer wrote it would make the result NaN.  The
+    pipelined inversion (tiles 32 and 64), the three steps one after the
+    other and the selected inverse still match the oracle."""
+    from paper_1002_4057_gb300 import _lib as L
+    A, _, _ = si.spectral_spd(n, 1e3, seed=si.SEED_BASE + 60 + n)
+    M, oinfo = oracle.potri(A)
+    assert oinfo == 0
+    ref = oracle.symmetrize_lower(M)
+    old = L.spdinv_set_debug_flags(L.SPDINV_DEBUG_POISON)
+    try:
+        for b in (32, 64):
+            dA = to_dev(A, gpu)
+            assert int(T.potri_(dA, tile=b).item()) == 0
+            assert oracle.rel_frobenius(full_from_lower(lower_np(dA)), ref) <= 1e-10
+        dA = to_dev(A, gpu)
+        assert int(T.potrf_(dA).item()) == 0
+        assert int(T.trtri_(dA).item()) == 0
+        T.lauum_(dA)
+        assert oracle.rel_frobenius(full_from_lower(lower_np(dA)), ref) <= 1e-10
+        d = T.inverse_diag(to_dev(A, gpu)).cpu().numpy()
+        assert np.max(np.abs(d - np.diag(ref)) / np.abs(np.diag(ref))) <= 1e-10
+    finally:
+        L.spdinv_set_debug_flags(old)
