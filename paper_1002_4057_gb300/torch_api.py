@@ -98,6 +98,30 @@ def inverse_diag(A, info=None, stream=None):
     return d
 
 
+def potri_noalloc_(A, info=None, stream=None):
+    """potri_ (FP64, tile 32) without any device allocation by the library,
+    for n <= SPDINV_NOALLOC_MAX_N; calls must not overlap on the GPU."""
+    n, lda = _lda(A, torch.float64)
+    info = _info_buf(A.device) if info is None else info
+    _check(L.spdinv_potri_noalloc(n, A.data_ptr(), lda, info.data_ptr(), _stream(stream)), "spdinv_potri_noalloc")
+    return info
+
+
+def inverse_residual(A, X, residual=L.SPDINV_RESIDUAL_EMULATED, stream=None):
+    """R = I - A X as a new column-major n x n float64 tensor, for a
+    symmetric A given by its lower triangle (column-major) and a full X
+    (column-major, leading dimension n).  residual selects how the product
+    is formed (SPDINV_RESIDUAL_*)."""
+    n, lda = _lda(A, torch.float64)
+    nx, ldx = _lda(X, torch.float64)
+    if nx != n or ldx != max(n, 1) or X.device != A.device:
+        raise ValueError("X must be n x n on A's device, column-major with leading dimension n")
+    R = torch.empty((n, n), dtype=torch.float64, device=A.device).t()
+    _check(L.spdinv_inverse_residual(n, A.data_ptr(), lda, X.data_ptr(), R.data_ptr(), int(residual),
+                                     _stream(stream)), "spdinv_inverse_residual")
+    return R
+
+
 # ------------------------------------------------------- caller workspace
 _workspaces = {}  # device index -> the caller's buffer, kept alive while set
 

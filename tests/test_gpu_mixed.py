@@ -194,3 +194,22 @@ def test_mixed_emulated_matches_native_residual(gpu, n):
     print("n=%d errors emulated(tcgen05) %.2e native %.2e emulated(mma.sync) %.2e" % (n, errs[0], errs[1], errs[2]))
     assert errs[0] <= 1e-10 and errs[1] <= 1e-10 and errs[2] <= 1e-10
 
+
+
+def test_torch_wrappers_of_residual_and_noalloc(gpu):
+    """torch_api.inverse_residual and potri_noalloc_: the integer case's
+    residual is exactly zero, and the no-allocation inversion equals the
+    oracle within the FP64 tolerance."""
+    import torch
+    from paper_1002_4057_gb300 import torch_api as T
+    n = 300
+    A, s = si.bidiag_integer_spd(n, seed=6)
+    X = cf.bidiag_inverse(s)
+    R = T.inverse_residual(to_dev(A, gpu), torch.from_numpy(np.asfortranarray(X)).to(gpu))
+    assert R.stride() == (1, n)
+    assert np.array_equal(R.cpu().numpy(), np.zeros((n, n)))
+    A, _, _ = si.spectral_spd(n, 1e3, seed=si.SEED_BASE + 70)
+    dA = to_dev(A, gpu)
+    assert int(T.potri_noalloc_(dA).item()) == 0
+    M, _ = oracle.potri(A)
+    assert oracle.rel_frobenius(full_from_lower(lower_np(dA)), oracle.symmetrize_lower(M)) <= 1e-10
