@@ -440,6 +440,10 @@ SPDINV_API unsigned spdinv_set_debug_flags(unsigned flags);
  * Library information
  * ------------------------------------------------------------------------ */
 
+/* Name of a status code ("SPDINV_ERR_N", ...; "unknown status" otherwise),
+ * a static string. */
+SPDINV_API const char* spdinv_status_name(int status);
+
 /* Text of the last CUDA runtime error seen by this thread's calls (or ""). */
 SPDINV_API const char* spdinv_last_cuda_error(void);
 

@@ -91,6 +91,7 @@ SIGNATURES = {
     "spdinv_dag_task_counts": (c_int, [c_int, P]),
     "spdinv_plan_tasks": (c_int, [c_int64, c_int, c_int, P, c_int64, P, P]),
     "spdinv_set_debug_flags": (ctypes.c_uint, [ctypes.c_uint]),
+    "spdinv_status_name": (ctypes.c_char_p, [c_int]),
     "spdinv_last_cuda_error": (ctypes.c_char_p, []),
     "spdinv_kernel_launches": (ctypes.c_uint64, []),
     "spdinv_version": (c_int, []),
@@ -250,6 +251,10 @@ def spdinv_plan_tasks(n, b, steps):
 def spdinv_set_debug_flags(flags):
     """Sets the process's debug flags; returns the previous ones."""
     return _call("spdinv_set_debug_flags", int(flags))
+
+
+def spdinv_status_name(status):
+    return _call("spdinv_status_name", int(status)).decode()
 
 
 def spdinv_last_cuda_error():

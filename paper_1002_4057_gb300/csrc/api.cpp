@@ -36,7 +36,7 @@ spdinv_status cuda_fail(cudaError_t e) {
 }
 
 namespace {
-const char* status_name(spdinv_status st) {
+const char* status_name(int st) {
     switch (st) {
         case SPDINV_OK: return "SPDINV_OK";
         case SPDINV_ERR_N: return "SPDINV_ERR_N";
@@ -379,6 +379,8 @@ spdinv_status spdinv_plan_tasks(int64_t n, int b, int steps, uint32_t* out, int6
     if (m > 0) std::memcpy(out, p.order.data(), sizeof(uint32_t) * (size_t)m);
     return SPDINV_OK;
 }
+
+const char* spdinv_status_name(int status) { return status_name(status); }
 
 unsigned spdinv_set_debug_flags(unsigned flags) { return debug_flags().exchange(flags); }
 

@@ -290,3 +290,9 @@ def test_debug_flags_round_trip(lib):
         assert L.spdinv_set_debug_flags(0) == 0
     finally:
         L.spdinv_set_debug_flags(old)
+
+
+def test_status_names_match_the_binding(lib):
+    for code, name in L.STATUS_NAMES.items():
+        assert L.spdinv_status_name(code) == name
+    assert L.spdinv_status_name(-99) == "unknown status"
