@@ -1,6 +1,8 @@
 // Device-side machinery shared by the persistent tile-DAG kernels: error and
 // info words, bounded waits on readiness flags, bulk (TMA) tile fetches into
-// shared memory and publication of finished tiles.
+// shared memory and publication of finished tiles.  It takes the place of the
+// paper's dynamic scheduler (Sec. 3): a task starts as soon as the tiles it
+// reads are final, across the boundaries of the three steps.
 //
 // Protocol.  A producer CTA writes a tile with ordinary stores; every thread
 // then fences its stores for the async proxy and the GPU scope, the CTA

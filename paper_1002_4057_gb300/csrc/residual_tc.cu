@@ -1,4 +1,5 @@
-// The slice products of the emulated FP64 residual (residual_ozaki.cu) on the
+// The slice products of the emulated FP64 residual (residual_ozaki.cu; the
+// error-free splitting of Ozaki, Ogita, Oishi and Rump 2012) on the
 // fifth-generation tensor cores: tcgen05.mma (BF16 in, FP32 accumulator in
 // tensor memory), operands staged by TMA with 128-byte swizzle.
 //
