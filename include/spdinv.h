@@ -422,6 +422,20 @@ SPDINV_API spdinv_status spdinv_plan_emulate(int t, int steps, int workers, uint
                                              int skip_wait_task, double wait_limit_s, int max_delay_us,
                                              int64_t out[5]);
 
+/* Deterministic schedule of the execution plan for t x t tiles and `steps`
+ * on `workers` CTAs (host only; a list-scheduling model of the persistent
+ * kernel, no counterpart in the paper, whose Sec. 3 analyses critical paths
+ * only).  The next ticket goes to the CTA that becomes free first; the CTA
+ * runs the task's chain elements in the kernel's order, each one starting
+ * when the previous one is done and its input tiles are final.  Costs are in
+ * units of one b x b x b tile product: 1 per chain element and per TRMM,
+ * 0.7 for a diagonal POTRF + TRTRI, 0.4 for a TRTRI alone.
+ *   out[0] makespan, out[1] total work (the sum of the costs), out[2] the
+ *   plan's weighted critical path (task granularity, as spdinv_plan_tasks).
+ * work / (workers * makespan) is the fraction of CTA time the schedule keeps
+ * busy.  1 <= t <= 4096, 0 <= steps <= 4, workers >= 1. */
+SPDINV_API spdinv_status spdinv_plan_simulate(int t, int steps, int workers, double out[3]);
+
 /* ------------------------------------------------------------------------
  * Debugging
  * ------------------------------------------------------------------------ */

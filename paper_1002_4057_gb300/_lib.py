@@ -90,6 +90,7 @@ SIGNATURES = {
     "spdinv_dag_critical_path": (c_int, [c_int, c_int, P]),
     "spdinv_dag_task_counts": (c_int, [c_int, P]),
     "spdinv_plan_tasks": (c_int, [c_int64, c_int, c_int, P, c_int64, P, P]),
+    "spdinv_plan_simulate": (c_int, [c_int, c_int, c_int, P]),
     "spdinv_set_debug_flags": (ctypes.c_uint, [ctypes.c_uint]),
     "spdinv_status_name": (ctypes.c_char_p, [c_int]),
     "spdinv_last_cuda_error": (ctypes.c_char_p, []),
@@ -191,6 +192,14 @@ def spdinv_plan_check(t, steps):
     the fast and the exhaustive plan builds."""
     out = (ctypes.c_int64 * 3)()
     st = _call("spdinv_plan_check", int(t), int(steps), ctypes.addressof(out))
+    return st, list(out)
+
+
+def spdinv_plan_simulate(t, steps, workers):
+    """(status, [makespan, work, critical path]) of the plan scheduled on
+    `workers` CTAs, in units of one tile product."""
+    out = (ctypes.c_double * 3)()
+    st = _call("spdinv_plan_simulate", int(t), int(steps), int(workers), ctypes.addressof(out))
     return st, list(out)
 
 

@@ -31,7 +31,10 @@
 #include <atomic>
 #include <chrono>
 #include <cstdint>
+#include <algorithm>
+#include <functional>
 #include <memory>
+#include <queue>
 #include <random>
 #include <thread>
 #include <vector>
@@ -254,4 +257,74 @@ extern "C" SPDINV_API spdinv_status spdinv_plan_emulate(int t, int steps, int wo
     out[3] = emu.hazards.load();
     out[4] = emu.max_wait_us.load();
     return emu.abort.load() ? SPDINV_ERR_TIMEOUT : SPDINV_OK;
+}
+
+// Deterministic schedule of the same plan on `workers` CTAs (a list-scheduling
+// model of the persistent kernel): the next ticket goes to the CTA that
+// becomes free first, which then runs the task's chain elements in the
+// kernel's order, each starting when the CTA is done with the previous one
+// and the element's input tiles are final.  Costs in units of one b x b x b
+// tile product, as in the plan: 1 per chain element and per TRMM, 0.7 for a
+// diagonal POTRF + TRTRI, 0.4 for a TRTRI alone.
+extern "C" SPDINV_API spdinv_status spdinv_plan_simulate(int t, int steps, int workers, double out[3]) {
+    if (t < 1 || t > 4096) return SPDINV_ERR_N;
+    if (steps < STEPS_ALL || steps > STEPS_DIAG || workers < 1) return SPDINV_ERR_UNSUPPORTED;
+    if (!out) return SPDINV_ERR_NULL;
+    const ExecPlan plan = build_exec_plan(t, steps);
+    const bool s1 = steps == STEPS_ALL || steps == STEPS_POTRF || steps == STEPS_DIAG;
+    const bool from_A = s1, wait_d = steps != STEPS_LAUUM, wait_x = steps != STEPS_LAUUM;
+    const size_t tt = (size_t)t * t;
+    // Time at which each renamed tile is final (0: input or staged before the launch).
+    std::vector<double> rL(tt, 0.0), rX(tt, 0.0), rD((size_t)t, 0.0);
+    auto L = [&](int i, int j) -> double& { return rL[(size_t)i * t + j]; };
+    auto X = [&](int i, int j) -> double& { return rX[(size_t)i * t + j]; };
+    std::priority_queue<double, std::vector<double>, std::greater<double>> free_at;
+    for (int w = 0; w < workers && w < (int)plan.order.size(); ++w) free_at.push(0.0);
+    double makespan = 0.0, work = 0.0;
+    for (const uint32_t e : plan.order) {
+        const int kind = (int)task_kind(e), i = (int)task_i(e), j = (int)task_j(e);
+        double now = free_at.top(), busy = 0.0;
+        free_at.pop();
+        auto elem = [&](double r0, double r1, double c) {
+            now = std::max(now, std::max(r0, r1)) + c;
+            busy += c;
+        };
+        switch (kind) {
+            case K_S1_DIAG:
+                for (int k = 0; k < j; ++k) elem(L(j, k), 0.0, 1.0);
+                elem(0.0, 0.0, 0.7);
+                rD[j] = now;
+                break;
+            case K_S1_OFF:
+                for (int k = 0; k < j; ++k) elem(L(i, k), L(j, k), 1.0);
+                elem(rD[j], 0.0, 1.0);
+                L(i, j) = now;
+                break;
+            case K_S2_DIAG:
+                elem(0.0, 0.0, 0.4);
+                rD[j] = now;
+                break;
+            case K_S2_OFF:
+                elem(rD[i], from_A ? L(i, j) : 0.0, 1.0);
+                for (int k = i - 1; k > j; --k) elem(X(i, k), from_A ? L(k, j) : 0.0, 1.0);
+                elem(rD[j], 0.0, 1.0);
+                X(i, j) = now;
+                break;
+            case K_S3_OFF:
+                elem(wait_d ? rD[i] : 0.0, wait_x ? X(i, j) : 0.0, 1.0);
+                for (int k = i + 1; k < t; ++k) elem(wait_x ? X(k, i) : 0.0, wait_x ? X(k, j) : 0.0, 1.0);
+                break;
+            default:  // K_S3_DIAG
+                elem(wait_d ? rD[i] : 0.0, 0.0, 1.0);
+                for (int k = i + 1; k < t; ++k) elem(wait_x ? X(k, i) : 0.0, 0.0, 1.0);
+                break;
+        }
+        work += busy;
+        free_at.push(now);
+        makespan = std::max(makespan, now);
+    }
+    out[0] = makespan;
+    out[1] = work;
+    out[2] = plan.crit;
+    return SPDINV_OK;
 }

@@ -231,3 +231,36 @@ def test_fast_bottom_levels_match_the_edge_walk(steps):
 def test_exec_plan_puts_the_critical_path_first():
     _, tasks, _ = L.spdinv_plan_tasks(64 * 16, 64, 0)
     assert tasks[0] >> 28 == 0 and (tasks[0] & 0x3FFF) == 0  # Step-1 diagonal tile 0
+
+
+@pytest.mark.parametrize("steps", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("t", [1, 2, 7, 40])
+def test_schedule_model_bounds(steps, t):
+    """spdinv_plan_simulate: one CTA runs the tickets back to back, so the
+    makespan is the total work; any number of CTAs needs at least work / P
+    and at most the task-level critical path once every task has a CTA."""
+    st, (m1, w1, crit) = L.spdinv_plan_simulate(t, steps, 1)
+    assert st == 0 and m1 == pytest.approx(w1, rel=1e-12)  # the same sum, in another order
+    for P in (2, 5, 64):
+        st, (m, w, _) = L.spdinv_plan_simulate(t, steps, P)
+        assert st == 0 and w == w1 and w / P <= m * (1 + 1e-12) and m <= w * (1 + 1e-12)
+    st, (minf, _, _) = L.spdinv_plan_simulate(t, steps, 10 ** 7)
+    assert minf <= crit * (1 + 1e-12)
+
+
+@pytest.mark.parametrize("t", [16, 64, 256])
+def test_element_pipelined_critical_path_is_below_5t(t):
+    """With a CTA for every task and each chain element waiting only for its
+    own inputs, the full inversion's makespan stays under 5t tile products:
+    the chain tasks keep the pipelined fine-grained DAG's critical path
+    (5t - 2 unit tasks, Sec. 3), far below the task-level path (order t^2)."""
+    st, (m, _, crit) = L.spdinv_plan_simulate(t, 0, 10 ** 7)
+    assert st == 0
+    assert 4 * t < m < 5 * t
+    assert crit > t * t
+
+
+def test_schedule_model_argument_errors():
+    assert L.spdinv_plan_simulate(0, 0, 4)[0] == L.SPDINV_ERR_N
+    assert L.spdinv_plan_simulate(4, 5, 4)[0] == L.SPDINV_ERR_UNSUPPORTED
+    assert L.spdinv_plan_simulate(4, 0, 0)[0] == L.SPDINV_ERR_UNSUPPORTED
