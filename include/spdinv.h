@@ -436,6 +436,27 @@ SPDINV_API spdinv_status spdinv_plan_emulate(int t, int steps, int workers, uint
  * busy.  1 <= t <= 4096, 0 <= steps <= 4, workers >= 1. */
 SPDINV_API spdinv_status spdinv_plan_simulate(int t, int steps, int workers, double out[3]);
 
+/* Ticket order of the persistent kernel's plans (the result does not depend
+ * on it: every output tile keeps its own accumulation order, and both orders
+ * are topological, so no grid can deadlock).
+ *   SPDINV_PLAN_BOTTOM_LEVEL  decreasing task-level bottom level (default);
+ *   SPDINV_PLAN_ALAP          increasing latest finish time of each task when
+ *                             every chain element starts as soon as its own
+ *                             inputs are final (unlimited CTAs), raised to the
+ *                             largest key among the task's producers.  Takes
+ *                             O(t^3) host time on the first call per size.
+ *                             The schedule model (spdinv_plan_simulate)
+ *                             predicts 7 % more throughput at n = 4096, tile
+ *                             32, and 12 % at tile 64; not yet measured.
+ * Sets the order for plans built after the call (plans are cached per order)
+ * and for the host queries; returns the previous order, or
+ * SPDINV_ERR_UNSUPPORTED for an unknown one (nothing changes).  The initial
+ * order is SPDINV_PLAN_ORDER=alap (or 1) from the environment, else the
+ * default. */
+#define SPDINV_PLAN_BOTTOM_LEVEL 0
+#define SPDINV_PLAN_ALAP 1
+SPDINV_API int spdinv_set_plan_order(int order);
+
 /* ------------------------------------------------------------------------
  * Debugging
  * ------------------------------------------------------------------------ */

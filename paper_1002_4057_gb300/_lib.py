@@ -33,6 +33,9 @@ SPDINV_NOALLOC_MAX_N = 1024
 
 SPDINV_DEBUG_POISON = 1
 
+SPDINV_PLAN_BOTTOM_LEVEL = 0
+SPDINV_PLAN_ALAP = 1
+
 SPDINV_ROUTINE_POTRI = 0
 SPDINV_ROUTINE_POTRF = 1
 SPDINV_ROUTINE_TRTRI = 2
@@ -91,6 +94,7 @@ SIGNATURES = {
     "spdinv_dag_task_counts": (c_int, [c_int, P]),
     "spdinv_plan_tasks": (c_int, [c_int64, c_int, c_int, P, c_int64, P, P]),
     "spdinv_plan_simulate": (c_int, [c_int, c_int, c_int, P]),
+    "spdinv_set_plan_order": (c_int, [c_int]),
     "spdinv_set_debug_flags": (ctypes.c_uint, [ctypes.c_uint]),
     "spdinv_status_name": (ctypes.c_char_p, [c_int]),
     "spdinv_last_cuda_error": (ctypes.c_char_p, []),
@@ -255,6 +259,11 @@ def spdinv_plan_tasks(n, b, steps):
     st = _call("spdinv_plan_tasks", n, b, steps, ctypes.addressof(buf), cnt.value, ctypes.addressof(cnt),
                ctypes.addressof(crit))
     return st, list(buf)[:cnt.value], crit.value
+
+
+def spdinv_set_plan_order(order):
+    """Sets the ticket order of plans built from now on; returns the previous one."""
+    return _call("spdinv_set_plan_order", int(order))
 
 
 def spdinv_set_debug_flags(flags):

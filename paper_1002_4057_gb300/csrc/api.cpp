@@ -121,10 +121,11 @@ spdinv_status DeviceState::acquire(size_t bytes, void** out) {
 }
 
 cudaError_t DeviceState::exec_plan(int t, int steps, const uint32_t** d_tasks, int* ntasks) {
-    const auto key = std::make_pair(t, steps);
+    const int order = current_plan_order();
+    const auto key = std::make_tuple(t, steps, order);
     auto it = plans.find(key);
     if (it == plans.end()) {
-        ExecPlan p = build_exec_plan(t, steps);
+        ExecPlan p = build_exec_plan(t, steps, false, order);
         DevicePlan dp;
         dp.ntasks = (int)p.order.size();
         cudaError_t e = cudaMalloc(&dp.d_tasks, sizeof(uint32_t) * (p.order.size() + 1));
@@ -372,7 +373,7 @@ spdinv_status spdinv_plan_tasks(int64_t n, int b, int steps, uint32_t* out, int6
     if (!ntasks || (cap > 0 && !out)) return SPDINV_ERR_NULL;
     const int64_t t = (n + b - 1) / b;
     if (t > 16383) return SPDINV_ERR_N;
-    ExecPlan p = build_exec_plan((int)t, steps);
+    ExecPlan p = build_exec_plan((int)t, steps, false, current_plan_order());
     *ntasks = (int64_t)p.order.size();
     if (crit) *crit = p.crit;
     const int64_t m = cap < *ntasks ? cap : *ntasks;
@@ -381,6 +382,11 @@ spdinv_status spdinv_plan_tasks(int64_t n, int b, int steps, uint32_t* out, int6
 }
 
 const char* spdinv_status_name(int status) { return status_name(status); }
+
+int spdinv_set_plan_order(int order) {
+    if (order != SPDINV_PLAN_BOTTOM_LEVEL && order != SPDINV_PLAN_ALAP) return SPDINV_ERR_UNSUPPORTED;
+    return set_plan_order(order);
+}
 
 unsigned spdinv_set_debug_flags(unsigned flags) { return debug_flags().exchange(flags); }
 

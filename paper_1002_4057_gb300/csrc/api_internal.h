@@ -5,6 +5,7 @@
 #include <cstdint>
 #include <map>
 #include <mutex>
+#include <tuple>
 #include <utility>
 
 #include "../../include/spdinv.h"
@@ -25,7 +26,7 @@ struct DeviceState {
     void* user_ws = nullptr;  // a caller's buffer (spdinv_set_workspace), used instead when set
     size_t user_bytes = 0;
     int last_grid = 0;
-    std::map<std::pair<int, int>, DevicePlan> plans;  // (t, steps) -> plan
+    std::map<std::tuple<int, int, int>, DevicePlan> plans;  // (t, steps, ticket order) -> plan
     cudaError_t ensure_workspace(size_t bytes);
     // The workspace of one call: the caller's buffer when one is set
     // (SPDINV_ERR_WORKSPACE when it is too small; nothing is allocated), else

@@ -224,7 +224,7 @@ extern "C" SPDINV_API spdinv_status spdinv_plan_emulate(int t, int steps, int wo
     if (steps < STEPS_ALL || steps > STEPS_DIAG) return SPDINV_ERR_UNSUPPORTED;
     if (workers < 1 || workers > 1024 || wait_limit_s <= 0.0 || max_delay_us < 0) return SPDINV_ERR_UNSUPPORTED;
     if (!out) return SPDINV_ERR_NULL;
-    const ExecPlan plan = build_exec_plan(t, steps);
+    const ExecPlan plan = build_exec_plan(t, steps, false, current_plan_order());
     Emu emu;
     emu.t = t;
     emu.steps = steps;
@@ -270,7 +270,7 @@ extern "C" SPDINV_API spdinv_status spdinv_plan_simulate(int t, int steps, int w
     if (t < 1 || t > 4096) return SPDINV_ERR_N;
     if (steps < STEPS_ALL || steps > STEPS_DIAG || workers < 1) return SPDINV_ERR_UNSUPPORTED;
     if (!out) return SPDINV_ERR_NULL;
-    const ExecPlan plan = build_exec_plan(t, steps);
+    const ExecPlan plan = build_exec_plan(t, steps, false, current_plan_order());
     const bool s1 = steps == STEPS_ALL || steps == STEPS_POTRF || steps == STEPS_DIAG;
     const bool from_A = s1, wait_d = steps != STEPS_LAUUM, wait_x = steps != STEPS_LAUUM;
     const size_t tt = (size_t)t * t;

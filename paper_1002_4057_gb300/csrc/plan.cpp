@@ -21,6 +21,8 @@
 #include "plan.h"
 
 #include <algorithm>
+#include <atomic>
+#include <cstdlib>
 #include <cstring>
 #include <numeric>
 #include <vector>
@@ -227,7 +229,7 @@ struct TaskIndex {
 
 }  // namespace
 
-ExecPlan build_exec_plan(int t, int steps, bool exhaustive) {
+ExecPlan build_exec_plan(int t, int steps, bool exhaustive, int order) {
     ExecPlan p;
     p.t = t;
     p.steps = steps;
@@ -399,11 +401,106 @@ ExecPlan build_exec_plan(int t, int steps, bool exhaustive) {
     std::vector<uint32_t> perm(N);
     std::iota(perm.begin(), perm.end(), 0u);
     std::stable_sort(perm.begin(), perm.end(), [&](uint32_t a, uint32_t b) { return bl[a] > bl[b]; });
-    p.order.resize(N);
-    for (size_t m = 0; m < N; ++m) p.order[m] = seq[perm[m]];
     p.crit = N ? bl[perm[0]] : 0.0;
     p.work = work;
+
+    if (order == ORDER_ALAP && N) {
+        // Each task's chain elements in the kernel's order: up to two producer
+        // tasks (-1: ready at launch) and a cost; the costs add up to cost().
+        struct Elem {
+            int32_t p0, p1;
+            double c;
+        };
+        std::vector<Elem> el;
+        auto elements = [&](uint32_t e) {
+            const int i = task_i(e), j = task_j(e);
+            el.clear();
+            switch (task_kind(e)) {
+                case K_S1_DIAG:
+                    for (int k = 0; k < j; ++k) el.push_back({lprod(j, k), -1, 1.0});
+                    el.push_back({-1, -1, 0.7});
+                    break;
+                case K_S1_OFF:
+                    for (int k = 0; k < j; ++k) el.push_back({lprod(i, k), lprod(j, k), 1.0});
+                    el.push_back({dprod(j), -1, 1.0});
+                    break;
+                case K_S2_DIAG:
+                    el.push_back({-1, -1, 0.4});
+                    break;
+                case K_S2_OFF:
+                    el.push_back({dprod(i), lprod(i, j), 1.0});
+                    for (int k = i - 1; k > j; --k) el.push_back({xprod(i, k), lprod(k, j), 1.0});
+                    el.push_back({dprod(j), -1, 1.0});
+                    break;
+                case K_S3_DIAG:
+                    el.push_back({dprod(i), -1, 1.0});
+                    for (int k = i + 1; k < t; ++k) el.push_back({xprod(k, i), -1, 1.0});
+                    break;
+                default:  // K_S3_OFF
+                    el.push_back({dprod(i), xprod(i, j), 1.0});
+                    for (int k = i + 1; k < t; ++k) el.push_back({xprod(k, i), xprod(k, j), 1.0});
+                    break;
+            }
+        };
+        // Earliest finish with unlimited CTAs (seq is topological).
+        std::vector<double> fin(N, 0.0);
+        double span = 0.0;
+        for (size_t r = 0; r < N; ++r) {
+            elements(seq[r]);
+            double now = 0.0;
+            for (const Elem& x : el) {
+                if (x.p0 >= 0) now = std::max(now, fin[x.p0]);
+                if (x.p1 >= 0) now = std::max(now, fin[x.p1]);
+                now += x.c;
+            }
+            fin[r] = now;
+            span = std::max(span, now);
+        }
+        // Latest finish that keeps the span: each element's latest start
+        // bounds the finish of the tasks it reads.
+        std::vector<double> late(N, span);
+        for (size_t r = N; r-- > 0;) {
+            elements(seq[r]);
+            double tail = late[r];
+            for (size_t q = el.size(); q-- > 0;) {
+                tail -= el[q].c;
+                if (el[q].p0 >= 0) late[el[q].p0] = std::min(late[el[q].p0], tail);
+                if (el[q].p1 >= 0) late[el[q].p1] = std::min(late[el[q].p1], tail);
+            }
+        }
+        // Keys raised to the producers' keys keep the sorted order topological
+        // (ties go to the earlier task of Algorithm 1's order).
+        std::vector<double> key(N, 0.0);
+        for (size_t r = 0; r < N; ++r) {
+            elements(seq[r]);
+            double k = late[r];
+            for (const Elem& x : el) {
+                if (x.p0 >= 0) k = std::max(k, key[x.p0]);
+                if (x.p1 >= 0) k = std::max(k, key[x.p1]);
+            }
+            key[r] = k;
+        }
+        std::iota(perm.begin(), perm.end(), 0u);
+        std::stable_sort(perm.begin(), perm.end(), [&](uint32_t a, uint32_t b) { return key[a] < key[b]; });
+    }
+    p.order.resize(N);
+    for (size_t m = 0; m < N; ++m) p.order[m] = seq[perm[m]];
     return p;
 }
+
+namespace {
+std::atomic<int>& plan_order_setting() {
+    static std::atomic<int> order{[] {
+        const char* env = std::getenv("SPDINV_PLAN_ORDER");
+        if (env && (std::strcmp(env, "alap") == 0 || std::strcmp(env, "1") == 0)) return (int)ORDER_ALAP;
+        return (int)ORDER_BOTTOM_LEVEL;
+    }()};
+    return order;
+}
+}  // namespace
+
+int current_plan_order() { return plan_order_setting().load(std::memory_order_relaxed); }
+
+int set_plan_order(int order) { return plan_order_setting().exchange(order); }
 
 }  // namespace spdinv

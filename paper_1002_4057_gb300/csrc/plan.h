@@ -38,10 +38,26 @@ struct ExecPlan {
     double work = 0.0;            // total weight
 };
 
+// Ticket order of a plan (both are topological, so any grid is free of
+// deadlock, and the result does not depend on the order: every output tile
+// keeps its own accumulation order).
+//   ORDER_BOTTOM_LEVEL  decreasing task-level bottom level (the default);
+//   ORDER_ALAP          increasing latest finish time of each task in the
+//                       element-pipelined schedule on unlimited CTAs (each
+//                       chain element starts when its own inputs are final),
+//                       raised to the largest key among the task's producers
+//                       so that the order stays topological.  O(t^3).
+enum PlanOrder { ORDER_BOTTOM_LEVEL = 0, ORDER_ALAP = 1 };
+
+// The order the library plans with: ORDER_BOTTOM_LEVEL unless
+// SPDINV_PLAN_ORDER=alap (or 1) in the environment or spdinv_set_plan_order.
+int current_plan_order();
+int set_plan_order(int order);  // returns the previous one
+
 // Builds the chain-task plan for t x t tiles (t <= 16383).  The bottom
 // levels that order it take O(t^2); exhaustive walks every dependency edge,
 // O(t^3) -- the same result, kept to check the fast path.
-ExecPlan build_exec_plan(int t, int steps, bool exhaustive = false);
+ExecPlan build_exec_plan(int t, int steps, bool exhaustive = false, int order = ORDER_BOTTOM_LEVEL);
 
 // Fine-grained DAG of Algorithm 1 / its Sec. 3 variants: critical paths.
 void dag_critical_path(int t, int flags, int64_t out[4]);

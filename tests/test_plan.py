@@ -163,8 +163,8 @@ def test_task_counts(t):
 def _deps(kind, i, j, t, steps):
     """Tasks whose output (kind, i, j) reads, written out from the chain
     definitions of the three steps (independent of the C++ planner)."""
-    s1 = steps in (0, 1)
-    s2 = steps in (0, 2)
+    s1 = steps in (0, 1, 4)
+    s2 = steps in (0, 2, 4)
     d = []
     D = (lambda q: [(0, q, q)]) if s1 else ((lambda q: [(2, q, q)]) if steps == 2 else (lambda q: []))
     Lt = (lambda a, b: [(1, a, b)]) if s1 else (lambda a, b: [])
@@ -191,9 +191,16 @@ def _deps(kind, i, j, t, steps):
     return d
 
 
+@pytest.fixture(params=[L.SPDINV_PLAN_BOTTOM_LEVEL, L.SPDINV_PLAN_ALAP], ids=["bottom_level", "alap"])
+def plan_order(request):
+    old = L.spdinv_set_plan_order(request.param)
+    yield request.param
+    L.spdinv_set_plan_order(old)
+
+
 @pytest.mark.parametrize("n,b,steps", [(512, 64, 0), (1000, 32, 0), (700, 64, 1), (700, 64, 2),
-                                       (700, 64, 3), (33, 32, 0), (1, 32, 0)])
-def test_exec_plan_is_topological_and_complete(n, b, steps):
+                                       (700, 64, 3), (700, 64, 4), (33, 32, 0), (1, 32, 0)])
+def test_exec_plan_is_topological_and_complete(n, b, steps, plan_order):
     st, tasks, crit = L.spdinv_plan_tasks(n, b, steps)
     assert st == 0
     t = (n + b - 1) // b
@@ -201,14 +208,16 @@ def test_exec_plan_is_topological_and_complete(n, b, steps):
     pos = {d: m for m, d in enumerate(dec)}
     assert len(pos) == len(dec)  # no duplicates
     expect = set()
-    if steps in (0, 1):
+    if steps in (0, 1, 4):
         expect |= {(0, j, j) for j in range(t)} | {(1, i, j) for i in range(t) for j in range(i)}
     if steps == 2:
         expect |= {(2, j, j) for j in range(t)}
-    if steps in (0, 2):
+    if steps in (0, 2, 4):
         expect |= {(3, i, j) for i in range(t) for j in range(i)}
+    if steps in (0, 3, 4):
+        expect |= {(4, i, i) for i in range(t)}
     if steps in (0, 3):
-        expect |= {(4, i, i) for i in range(t)} | {(5, i, j) for i in range(t) for j in range(i)}
+        expect |= {(5, i, j) for i in range(t) for j in range(i)}
     assert set(dec) == expect
     for m, (k, i, j) in enumerate(dec):
         for dep in _deps(k, i, j, t, steps):
@@ -264,3 +273,42 @@ def test_schedule_model_argument_errors():
     assert L.spdinv_plan_simulate(0, 0, 4)[0] == L.SPDINV_ERR_N
     assert L.spdinv_plan_simulate(4, 5, 4)[0] == L.SPDINV_ERR_UNSUPPORTED
     assert L.spdinv_plan_simulate(4, 0, 0)[0] == L.SPDINV_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("t,P,gain", [(64, 456, 0.08), (128, 912, 0.05), (128, 456, 0.02)])
+def test_alap_order_keeps_more_ctas_busy(t, P, gain):
+    """The ALAP ticket order (latest finish first, kept topological) against
+    the bottom-level order in the schedule model: never worse, and clearly
+    better where dependency waits cost most (n = 4096 at tiles 64 and 32)."""
+    eff = {}
+    for order in (L.SPDINV_PLAN_BOTTOM_LEVEL, L.SPDINV_PLAN_ALAP):
+        old = L.spdinv_set_plan_order(order)
+        try:
+            st, (m, w, _) = L.spdinv_plan_simulate(t, 0, P)
+        finally:
+            L.spdinv_set_plan_order(old)
+        assert st == 0
+        eff[order] = w / (P * m)
+    assert eff[L.SPDINV_PLAN_ALAP] >= eff[L.SPDINV_PLAN_BOTTOM_LEVEL] + gain, eff
+
+
+@pytest.mark.parametrize("steps", [0, 1, 2, 3, 4])
+def test_alap_order_runs_the_protocol_without_hazards(steps):
+    old = L.spdinv_set_plan_order(L.SPDINV_PLAN_ALAP)
+    try:
+        for workers in (1, 7, 64):
+            st, (done, total, errors, hazards, _) = L.spdinv_plan_emulate(17, workers, 3, max_delay_us=10,
+                                                                          steps=steps)
+            assert st == L.SPDINV_OK and done == total and errors == 0 and hazards == 0
+    finally:
+        L.spdinv_set_plan_order(old)
+
+
+def test_plan_order_setter():
+    old = L.spdinv_set_plan_order(L.SPDINV_PLAN_ALAP)
+    try:
+        assert L.spdinv_set_plan_order(7) == L.SPDINV_ERR_UNSUPPORTED
+        assert L.spdinv_set_plan_order(L.SPDINV_PLAN_BOTTOM_LEVEL) == L.SPDINV_PLAN_ALAP
+    finally:
+        L.spdinv_set_plan_order(old)
+
