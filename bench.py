@@ -42,6 +42,8 @@ def parse():
     ap.add_argument("--n", type=int, default=16384)
     ap.add_argument("--tile", type=int, default=32)
     ap.add_argument("--ctas-per-sm", type=int, default=0)
+    ap.add_argument("--plan-order", default="bottom_level", choices=["bottom_level", "alap"],
+                    help="ticket order of the persistent kernel's plans (spdinv_set_plan_order)")
     ap.add_argument("--cond", type=float, default=1e4)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-e2e", action="store_true")
@@ -301,10 +303,13 @@ def run_variants(args, dev, stream):
     steps run one after another (spdinv_potrf, spdinv_trtri, spdinv_lauum:
     every step waits for the previous one to finish), for tiles 32 and 64 at
     n = 4096, 8192 and 16384; and the selected inverse diag(A^{-1})
-    (spdinv_potri_diag: Step 3 on the diagonal tiles only)."""
+    (spdinv_potri_diag: Step 3 on the diagonal tiles only).  The pipelined
+    runs also take the ALAP ticket order (key suffix _alap) and, at tile 32
+    and n <= 8192, 2, 3 and 4 resident CTAs per SM (suffix _ctasK).
     import torch
 
     import spd_inputs as si
+    from paper_1002_4057_gb300 import _lib as L
     from paper_1002_4057_gb300 import torch_api as T
 
     sizes = (4096, 8192, 16384) if args.n == 16384 else (args.n,)
@@ -315,11 +320,16 @@ def run_variants(args, dev, stream):
         flops = float(n) ** 3
         rec = {"workload": "variants", "n": n}
         for b in (32, 64):
-            def piped():
-                W.copy_(A)
-                T.potri_(W, info=info, tile=b)
-            ms = timed_steps(piped, args.steps, args.warmup, stream)
-            rec["pipelined_b%d" % b] = {"ms": round(ms, 2), "gflops": round(flops / (ms * 1e-3) / 1e9, 1)}
+            for order, suffix in ((L.SPDINV_PLAN_BOTTOM_LEVEL, ""), (L.SPDINV_PLAN_ALAP, "_alap")):
+                old = L.spdinv_set_plan_order(order)
+                for per in ((0, 2, 3, 4) if (b == 32 and n <= 8192 and not suffix) else (0,)):
+                    def piped():
+                        W.copy_(A)
+                        T.potri_(W, info=info, tile=b, ctas_per_sm=per)
+                    ms = timed_steps(piped, args.steps, args.warmup, stream)
+                    key = "pipelined_b%d%s%s" % (b, suffix, "_ctas%d" % per if per else "")
+                    rec[key] = {"ms": round(ms, 2), "gflops": round(flops / (ms * 1e-3) / 1e9, 1)}
+                L.spdinv_set_plan_order(old)
         ms_copy = timed_steps(lambda: W.copy_(A), args.steps, args.warmup, stream)
 
         def stepwise():
@@ -484,6 +494,9 @@ def main():
     args = parse()
     PROFILE_TIMED = args.profile_timed
     rank, world, local = dist_env()
+    if args.plan_order != "bottom_level" and args.impl != "reference":
+        from paper_1002_4057_gb300 import _lib as L
+        L.spdinv_set_plan_order(L.SPDINV_PLAN_ALAP)
     if args.impl == "reference":
         run_reference(args, rank, world)
         return
@@ -655,6 +668,7 @@ def main():
                        "generator": "A = Q diag(lam) Q^T, Q from QR of seeded N(0,1), lam log-uniform [1, cond]",
                        "l2": "inputs larger than L2 (A is %.1f GiB)" % (n * n * 8 / 2 ** 30),
                        "step": "restore A from a device copy + spdinv_potri_ex",
+                       "plan_order": args.plan_order,
                        "parallelism": "replicas" if world > 1 else "single"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": int(launches),
             "kernel_ms": [round(x, 3) for x in kern_ms],
