@@ -305,7 +305,7 @@ def run_variants(args, dev, stream):
     n = 4096, 8192 and 16384; and the selected inverse diag(A^{-1})
     (spdinv_potri_diag: Step 3 on the diagonal tiles only).  The pipelined
     runs also take the ALAP ticket order (key suffix _alap) and, at tile 32
-    and n <= 8192, 2, 3 and 4 resident CTAs per SM (suffix _ctasK).
+    and n <= 8192, 2, 3 and 4 resident CTAs per SM (suffix _ctasK)."""
     import torch
 
     import spd_inputs as si
