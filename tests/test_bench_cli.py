@@ -29,3 +29,12 @@ def test_reference_arm_line():
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
     assert line["value"] > 0
+
+
+def test_graft_entry_exposes_build_and_smoke():
+    sys.path.insert(0, ROOT)
+    try:
+        import __graft_entry__ as g
+    finally:
+        sys.path.remove(ROOT)
+    assert callable(g.build) and callable(g.smoke)
