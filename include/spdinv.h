@@ -283,7 +283,10 @@ SPDINV_API spdinv_status spdinv_set_workspace(void* d_ws, size_t bytes);
  * each capped table on a synthetic batch of the same sizes (skipped above
  * 2 GiB), keeps the fastest and uploads it; this call allocates and
  * synchronises.  A later call with the same list queues only the kernel
- * launch and can be captured in a CUDA graph. */
+ * launch and can be captured in a CUDA graph.  Plans stay cached for the
+ * life of the process (16 bytes of device memory and 8 bytes of host memory
+ * per matrix), since a captured graph may still use them: a caller with
+ * ever-changing size lists should pad them to a few fixed lists. */
 SPDINV_API spdinv_status spdinv_potri_batched(int batch, const int* h_n, double* const* d_Aptrs,
                                    const int* h_lda, int* d_info, cudaStream_t stream);
 
