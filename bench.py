@@ -55,12 +55,15 @@ def parse():
                          "ncu --profile-from-start off (warm-up, tuning and set-up launches are then not captured)")
     ap.add_argument("--workload", default="fp64",
                     choices=["fp64", "batched64", "batched32", "backward64", "backward32", "mixed", "residual",
-                             "variants"],
+                             "variants", "peaks"],
                     help="fp64 (default, the headline line): one n x n FP64 inversion per step; "
                          "batched*: 4096 matrices per GPU, n ~ U{16..256}, one graph-captured launch per step "
                          "(with N GPUs the 4096 N matrices are split by spdinv_batch_shard); "
                          "backward*: forward + backward of 256 matrices n = 512; "
-                         "variants: pipelined vs step-by-step (barriered) execution and the tile size")
+                         "variants: pipelined vs step-by-step (barriered) execution and the tile size; "
+                         "peaks: the FP64 MMA / FMA and FP32 FMA microbenchmarks")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="default line without its mixed-precision, batched and backward sub-records")
     return ap.parse_args()
 
 
@@ -126,30 +129,60 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline(n_full, cond, budget_s=15.0):
-    """The FP64 oracle (unblocked potf2/trti2/lauu2, OpenMP) on one matrix of
-    the same generator, with n chosen so that the run takes about budget_s."""
+def cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu model")):
+                return line.split(":", 1)[1].strip()
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+def _oracle_gflops(n, cond):
     import oracle
     import spd_inputs as si
-    n = 768
     A, _, _ = si.spectral_spd(n, cond, seed=si.SEED_BASE + 1)
     t0 = time.perf_counter()
     _, info = oracle.potri(A)
     dt = time.perf_counter() - t0
     assert info == 0
-    # unblocked cost grows like n^3; pick a sample size for ~budget_s
-    n2 = int(n * (budget_s / max(dt, 1e-3)) ** (1.0 / 3.0))
+    return n ** 3 / dt / 1e9, dt
+
+
+def cpu_baseline(n_full, cond, budget_s=12.0):
+    """The FP64 oracle (unblocked potf2/trti2/lauu2, OpenMP over independent
+    entries) on matrices of the same generator: on all host cores at n = 512
+    and at the largest n <= 4096 that fits about budget_s, and on one thread
+    at n = 512 and at the n that fits about budget_s / 3."""
+    import oracle
+    cores = oracle.num_threads()
+    g512, _ = _oracle_gflops(512, cond)
+    g768, dt = _oracle_gflops(768, cond)
+    n2 = int(768 * (budget_s / max(dt, 1e-3)) ** (1.0 / 3.0))
     n2 = max(512, min(n2, 4096, n_full))
     n2 -= n2 % 64
-    A, _, _ = si.spectral_spd(n2, cond, seed=si.SEED_BASE + 1)
-    t0 = time.perf_counter()
-    _, info = oracle.potri(A)
-    dt = time.perf_counter() - t0
-    assert info == 0
-    return {"value": round(n2 ** 3 / dt / 1e9, 3), "unit": "Gflop/s", "cores": oracle.num_threads(),
-            "kind": "oracle",
-            "sample": "one full oracle inversion of an n=%d matrix of the same generator (cond %.0e); "
-                      "%.1f s; Gflop/s = n^3/t" % (n2, cond, dt)}
+    g_all, dt_all = _oracle_gflops(n2, cond)
+    oracle.set_num_threads(1)
+    try:
+        g1_512, dt1 = _oracle_gflops(512, cond)
+        n1 = int(512 * ((budget_s / 3.0) / max(dt1, 1e-3)) ** (1.0 / 3.0))
+        n1 = max(512, min(n1, 2048, n_full))
+        n1 -= n1 % 64
+        g1, dt1b = _oracle_gflops(n1, cond)
+    finally:
+        oracle.set_num_threads(cores)
+    return {"value": round(g_all, 3), "unit": "Gflop/s", "cores": cores, "kind": "oracle",
+            "sample": "one full oracle inversion of an n=%d matrix of the same generator (cond %.0e) on %d "
+                      "threads, %.1f s; Gflop/s = n^3/t" % (n2, cond, cores, dt_all),
+            "cpu_model": cpu_model(), "nproc": os.cpu_count(),
+            "all_cores": {"n512": round(g512, 3), "n%d" % n2: round(g_all, 3)},
+            "single_thread": {"n512": round(g1_512, 3), "n%d" % n1: round(g1, 3),
+                              "note": "one OpenMP thread, n=%d took %.1f s" % (n1, dt1b)}}
 
 
 def run_reference(args, rank, world):
@@ -207,6 +240,148 @@ def timed_steps(fn, steps, warmup, stream, min_warmup=3):
     torch.cuda.synchronize()
     profiler(False)
     return e0.elapsed_time(e1) / steps
+
+
+def measure_peaks(dev, stream, target_ms=150.0):
+    """Peaks of this GPU measured in this process (spdinv_fp64_peak_probe):
+    the FP64 tensor-core MMA (DMMA m8n8k4), the FP64 FMA and the FP32 FMA,
+    each the best of 2, 4 and 8 CTAs of 128 threads per SM, timed with CUDA
+    events; the SM clock is sampled meanwhile."""
+    import torch
+
+    from paper_1002_4057_gb300 import _lib as L
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    sink = torch.empty(sms * 16 * 4, dtype=torch.float64, device=dev)
+    clk = ClockSampler(dev.index or 0)
+    clk.start()
+    time.sleep(0.3)
+    out = {}
+    for kind, name in ((L.SPDINV_PROBE_DMMA, "dmma_fp64"), (L.SPDINV_PROBE_DFMA, "dfma_fp64"),
+                       (L.SPDINV_PROBE_FFMA, "ffma_fp32")):
+        best, cfg = 0.0, None
+        for per in (2, 4, 8):
+            iters = 2000
+            for rep in range(4):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                st, fl = L.spdinv_fp64_peak_probe(kind, iters, per, sink.data_ptr(), stream.cuda_stream)
+                assert st == 0, st
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1)
+                if rep == 0:  # calibrate to about target_ms per launch
+                    iters = max(1000, int(iters * target_ms / max(ms, 1e-3)))
+                    continue
+                rate = fl / (ms * 1e-3) / 1e12
+                if rate > best:
+                    best, cfg = rate, {"ctas_per_sm": per, "iters": iters, "ms": round(ms, 2)}
+        out[name] = {"tflops": round(best, 4), **cfg}
+    out["clocks"] = clk.stop()
+    return out
+
+
+def _spectral_from(Q, lam):
+    """Q diag(lam) Q^T, exactly symmetric, as the column-major view the
+    library takes (the generator's formula on the device)."""
+    import torch
+    lt = torch.from_numpy(lam).to(Q.device)
+    A = (Q * lt) @ Q.t()
+    A = 0.5 * (A + A.t())
+    return A.t()
+
+
+def mixed_record(n, A_main, Q, lam_main, cond_main, ms64, stream, dev, peaks, reps=5):
+    """The metric's second half at the headline size: the mixed-precision
+    inversion (FP32/FP64 tile DAG, then one FP64-accurate correction of order
+    p) against this line's FP64 inversion.  Per condition number: the time per
+    inversion (CUDA events, 3 untimed runs, `reps` timed), the error on
+    sampled columns against the exact inverse Q diag(1/lam) Q^T of the
+    generated A, the speedup over the FP64 time of this line, and the rate of
+    the dominant kernel, the tcgen05 slice GEMM, over its launches (the
+    library's per-launch CUDA events)."""
+    import numpy as np
+    import torch
+
+    import spd_inputs as si
+    from paper_1002_4057_gb300 import _lib as L
+    from paper_1002_4057_gb300 import torch_api as T
+    cols = np.array([0, n // 3, n - 1])
+    peaks_bf16, src = measured_peaks()
+    bf16 = peaks_bf16.get("bf16_tflops", 1900.0)
+    bf16_sus = peaks_bf16.get("bf16_tflops_sustained")
+    recs = []
+    # cond 1e4: one step of order 4; cond 1e2: one step of order 3 (the fastest schedules at <= 1e-10)
+    for cond, k, order in ((cond_main, 1, 4), (1e2, 1, 3)):
+        if cond == cond_main:
+            A, lam = A_main, lam_main
+        else:
+            lam = si.log_uniform_spectrum(n, cond, si.SEED_BASE + 1)
+            A = _spectral_from(Q, lam)
+        lt = torch.from_numpy(lam).to(Q.device)
+        ref = (Q @ (Q[cols, :].t() / lt[:, None])).cpu().numpy()
+        W = torch.empty_like(A)
+        info = torch.zeros(1, dtype=torch.int32, device=dev)
+
+        def run():
+            W.copy_(A)
+            T.potri_(W, info=info, tile=64, precision=1, refine_steps=k, refine_order=order)
+
+        for _ in range(3):
+            run()
+        torch.cuda.synchronize()
+        for which in range(L.SPDINV_TIMED_KERNELS):
+            L.spdinv_kernel_time_ms(which)
+        L.spdinv_set_kernel_timing(1)
+        ms = []
+        for _ in range(reps):
+            W.copy_(A)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            T.potri_(W, info=info, tile=64, precision=1, refine_steps=k, refine_order=order)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        L.spdinv_set_kernel_timing(0)
+        st, gms, glaunch, gflops = L.spdinv_kernel_time_ms(L.SPDINV_TIMED_SLICE_GEMM)
+        st2, dms, dlaunch, dflops = L.spdinv_kernel_time_ms(L.SPDINV_TIMED_MIXED_DAG)
+        assert st == 0 and st2 == 0
+        assert int(info.item()) == 0
+        Lo = torch.tril(W)
+        Xc = (Lo[:, cols] + torch.tril(Lo, -1).t()[:, cols]).cpu().numpy()
+        err = float(np.linalg.norm(Xc - ref) / np.linalg.norm(ref))
+        t = statistics.mean(ms)
+        ach = gflops / (gms * 1e-3) / 1e12 if gms > 0 else None
+        ffma = peaks.get("ffma_fp32", {}).get("tflops") if peaks else None
+        dag_rate = dflops / (dms * 1e-3) / 1e12 if dms > 0 else None
+        recs.append({
+            "cond": cond, "refine_steps": k, "refine_order": order, "ms": round(t, 2),
+            "ms_min": round(min(ms), 2), "reps": reps, "err": err, "err_ok_1e-10": err <= 1e-10,
+            "gflops": round(float(n) ** 3 / (t * 1e-3) / 1e9, 1),
+            "speedup_vs_fp64_at_1e-10": round(ms64 / t, 3) if err <= 1e-10 else None,
+            "speedup_vs_fp64": round(ms64 / t, 3),
+            "slice_gemm_roofline": {
+                "bound": "tensor", "kernel": "ozaki_tc_kernel (tcgen05 kind::f16, BF16 slices, FP32 accumulator)",
+                "launches_per_inversion": glaunch / reps, "ms_per_inversion": round(gms / reps, 2),
+                "achieved": round(ach, 2) if ach else None, "peak": bf16, "unit": "TFLOP/s",
+                "frac": round(ach / bf16, 4) if ach else None,
+                "frac_of_sustained": round(ach / bf16_sus, 4) if (ach and bf16_sus) else None,
+                "peak_note": "bf16_tflops (%s, burst); the sustained figure is %s" % (src, bf16_sus),
+                "work": "2 * 128 * 128 * K flops per launched output tile and slice pair (K: order padded to 256)"},
+            "fp32_dag": {"kernel": "potri_mixed_persistent<64>", "ms_per_inversion": round(dms / reps, 2),
+                         "achieved_tflops": round(dag_rate, 3) if dag_rate else None,
+                         "ffma_peak_tflops": ffma,
+                         "frac_of_ffma": round(dag_rate / ffma, 4) if (dag_rate and ffma) else None},
+        })
+        del W
+        if A is not A_main:
+            del A
+        torch.cuda.empty_cache()
+    return {"n": n, "tile": 64, "fp64_ms_per_inversion": round(ms64, 2),
+            "generator": "A = Q diag(lam) Q^T with this line's Q, lam log-uniform [1, cond]",
+            "error": "relative Frobenius error of 3 sampled columns vs Q diag(1/lam) Q^T",
+            "records": recs}
 
 
 def run_mixed_study(args, dev, stream):
@@ -298,19 +473,33 @@ def run_residual(args, dev, stream):
 
 
 def run_variants(args, dev, stream):
-    """The execution-variant study of Sec. 3 on the GPU, FP64: the three
-    steps pipelined in one persistent launch (spdinv_potri) against the same
-    steps run one after another (spdinv_potrf, spdinv_trtri, spdinv_lauum:
-    every step waits for the previous one to finish), for tiles 32 and 64 at
-    n = 4096, 8192 and 16384; and the selected inverse diag(A^{-1})
-    (spdinv_potri_diag: Step 3 on the diagonal tiles only).  The pipelined
-    runs also take the ALAP ticket order (key suffix _alap) and, at tile 32
-    and n <= 8192, 2, 3 and 4 resident CTAs per SM (suffix _ctasK)."""
+    """The execution-variant study of Sec. 3 on the GPU, FP64, at n = 4096,
+    8192 and 16384 (or --n):
+      - the three steps pipelined in one persistent launch (spdinv_potri), the
+        default: renamed stores B, C, D, loop orders U, D, U; tiles 32 and 64,
+        ticket orders bottom level and ALAP, and (tile 32, n <= 8192) 2, 3 and
+        4 resident CTAs per SM;
+      - the same steps one launch after another (spdinv_potrf, spdinv_trtri,
+        spdinv_lauum: every step waits for the previous one);
+      - the variants of spdinv_opts.variant at tile 32: Step 2's chains in U
+        order (UUU), C in B's slots (renaming under a memory budget), a
+        single in-place store (no renaming), Step-3 chains split into
+        segments of 8 and 32 tiles (associative reduction);
+      - the selected inverse diag(A^{-1}) (spdinv_potri_diag).
+    Next to each: the critical path of the fine-grained task DAG (unit tasks,
+    spdinv_dag_critical_path) that the paper's analysis gives for it."""
     import torch
 
     import spd_inputs as si
     from paper_1002_4057_gb300 import _lib as L
     from paper_1002_4057_gb300 import torch_api as T
+
+    OOP, RD, PIPE, UUUF, SH = (L.SPDINV_DAG_OUT_OF_PLACE, L.SPDINV_DAG_RENAME_DIAG, L.SPDINV_DAG_PIPELINE,
+                               L.SPDINV_DAG_UUU, L.SPDINV_DAG_SHARE_BC)
+
+    def crit(t, flags):
+        st, out = L.spdinv_dag_critical_path(t, flags) if t <= 256 else (1, None)
+        return int(out[3]) if st == 0 else None
 
     sizes = (4096, 8192, 16384) if args.n == 16384 else (args.n,)
     for n in sizes:
@@ -318,29 +507,47 @@ def run_variants(args, dev, stream):
         W = torch.empty_like(A)
         info = torch.zeros(1, dtype=torch.int32, device=dev)
         flops = float(n) ** 3
-        rec = {"workload": "variants", "n": n}
+        steps = args.steps if n < 16384 else min(args.steps, 2)
+        rec = {"workload": "variants", "n": n, "steps": steps}
+
+        def timed(**kw):
+            def run():
+                W.copy_(A)
+                T.potri_(W, info=info, **kw)
+            ms = timed_steps(run, steps, args.warmup, stream)
+            assert int(info.item()) == 0
+            return {"ms": round(ms, 2), "gflops": round(flops / (ms * 1e-3) / 1e9, 1)}
+
         for b in (32, 64):
             for order, suffix in ((L.SPDINV_PLAN_BOTTOM_LEVEL, ""), (L.SPDINV_PLAN_ALAP, "_alap")):
                 old = L.spdinv_set_plan_order(order)
                 for per in ((0, 2, 3, 4) if (b == 32 and n <= 8192 and not suffix) else (0,)):
-                    def piped():
-                        W.copy_(A)
-                        T.potri_(W, info=info, tile=b, ctas_per_sm=per)
-                    ms = timed_steps(piped, args.steps, args.warmup, stream)
                     key = "pipelined_b%d%s%s" % (b, suffix, "_ctas%d" % per if per else "")
-                    rec[key] = {"ms": round(ms, 2), "gflops": round(flops / (ms * 1e-3) / 1e9, 1)}
+                    rec[key] = timed(tile=b, ctas_per_sm=per)
                 L.spdinv_set_plan_order(old)
-        ms_copy = timed_steps(lambda: W.copy_(A), args.steps, args.warmup, stream)
+        t32 = n // 32
+        rec["pipelined_b32"]["dag_critical_path"] = crit(t32, OOP | RD | PIPE)
+        for name, var, seg, flags in (("uuu", L.SPDINV_VARIANT_UUU, 0, OOP | RD | PIPE | UUUF),
+                                      ("share_bc", L.SPDINV_VARIANT_SHARE_BC, 0, OOP | RD | PIPE | SH),
+                                      ("inplace", L.SPDINV_VARIANT_INPLACE, 0, PIPE),
+                                      ("split3_seg8", L.SPDINV_VARIANT_SPLIT3, 8, None),
+                                      ("split3_seg32", L.SPDINV_VARIANT_SPLIT3, 32, None)):
+            r = timed(tile=32, variant=var, split_segment=seg)
+            if flags is not None:
+                r["dag_critical_path"] = crit(t32, flags)
+            rec["variant_b32_" + name] = r
+        ms_copy = timed_steps(lambda: W.copy_(A), steps, args.warmup, stream)
 
         def stepwise():
             W.copy_(A)
             T.potrf_(W, info=info)
             T.trtri_(W, info=info)
             T.lauum_(W)
-        ms = timed_steps(stepwise, args.steps, args.warmup, stream)
+        ms = timed_steps(stepwise, steps, args.warmup, stream)
         assert int(info.item()) == 0
-        rec["stepwise_default_tile"] = {"ms": round(ms, 2), "gflops": round(flops / (ms * 1e-3) / 1e9, 1)}
-        ms_d = timed_steps(lambda: T.inverse_diag(A, info=info), args.steps, args.warmup, stream)
+        rec["stepwise_default_tile"] = {"ms": round(ms, 2), "gflops": round(flops / (ms * 1e-3) / 1e9, 1),
+                                        "dag_critical_path": crit(t32, OOP | RD)}
+        ms_d = timed_steps(lambda: T.inverse_diag(A, info=info), steps, args.warmup, stream)
         rec["selected_inverse_diag_default_tile"] = {"ms": round(ms_d, 2)}
         rec["restore_copy_ms"] = round(ms_copy, 2)
         print(json.dumps(rec), flush=True)
@@ -357,17 +564,31 @@ def run_batched_bench(args, rank, world, local):
     import torch
     import torch.distributed as dist
 
-    import spd_inputs as si
-    from paper_1002_4057_gb300 import _lib as L
-    from paper_1002_4057_gb300 import torch_api as T
-
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     if world > 1:
         dist.init_process_group("nccl", device_id=dev)
+    line = batched_measure(args.workload == "batched64", args.steps, args.warmup, rank, world, local)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def batched_measure(fp64, steps, warmup, rank=0, world=1, local=0):
+    """One batched measurement: this rank's share of 4096 * world matrices,
+    restored and inverted by one graph replay per step.  Returns the line."""
+    import torch
+    import torch.distributed as dist
+
+    import spd_inputs as si
+    from paper_1002_4057_gb300 import _lib as L
+    from paper_1002_4057_gb300 import torch_api as T
+
+    dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
     clk = ClockSampler(local)
-    dtype = torch.float64 if args.workload == "batched64" else torch.float32
+    dtype = torch.float64 if fp64 else torch.float32
     seed = si.SEED_BASE + 3
     sizes = si.batch_sizes(4096 * world, 16, 256, seed=seed)
     st, owner, load = L.spdinv_batch_shard([int(v) for v in sizes], world)
@@ -406,29 +627,75 @@ def run_batched_bench(args, rank, world, local):
     if world > 1:
         dist.barrier()
     clk.start()
-    ms = slowest(timed_steps(step, args.steps, args.warmup, stream))
+    ms = slowest(timed_steps(step, steps, warmup, stream))
     clocks = clk.stop()
     assert int(pb.info.abs().sum().item()) == 0
     flops = float(sum(int(n) ** 3 for n in sizes))
     if world > 1:
         dist.barrier()
-    e_inv = slowest(timed_steps(lambda: g.replay(), args.steps, 1, stream))
+    e_inv = slowest(timed_steps(lambda: g.replay(), steps, 1, stream))
     st, tiles = L.spdinv_batched_tiles(1 if dtype == torch.float32 else 0)
-    if rank == 0:
-        line = {"workload": args.workload, "metric": METRIC, "value": round(flops / (ms * 1e-3) / 1e9, 3),
-                "unit": "Gflop/s", "n_gpus": world, "scaling": "weak", "ms_per_step": round(ms, 4),
-                "ms_per_batch_launch": round(e_inv, 4),
-                "value_launch_only": round(flops / (e_inv * 1e-3) / 1e9, 3),
-                "dtype": "f64" if dtype == torch.float64 else "f32", "flops_per_step": flops,
-                "config": {"matrices": 4096 * world, "n": "U{16..256}", "generator": "B B^T/n + 0.1 I",
-                           "split": "spdinv_batch_shard (longest processing time first on n^3); max/mean rank "
-                                    "load %.4f" % (max(load) / (sum(load) / world)),
-                           "step": "restore the batch (device copy) + one graph replay of spdinv_*potri_batched",
-                           "autotuned_tiles_by_32_class": tiles},
-                "clocks": clocks}
-        print(json.dumps(line), flush=True)
-    if world > 1:
-        dist.destroy_process_group()
+    del pool, pristine, mats, pb, g
+    torch.cuda.empty_cache()
+    return {"workload": "batched64" if fp64 else "batched32", "metric": METRIC,
+            "value": round(flops / (ms * 1e-3) / 1e9, 3),
+            "unit": "Gflop/s", "n_gpus": world, "scaling": "weak", "ms_per_step": round(ms, 4),
+            "ms_per_batch_launch": round(e_inv, 4),
+            "value_launch_only": round(flops / (e_inv * 1e-3) / 1e9, 3),
+            "dtype": "f64" if dtype == torch.float64 else "f32", "flops_per_step": flops,
+            "config": {"matrices": 4096 * world, "n": "U{16..256}", "generator": "B B^T/n + 0.1 I",
+                       "split": "spdinv_batch_shard (longest processing time first on n^3); max/mean rank "
+                                "load %.4f" % (max(load) / (sum(load) / world)),
+                       "step": "restore the batch (device copy) + one graph replay of spdinv_*potri_batched",
+                       "autotuned_tiles_by_32_class": tiles},
+            "clocks": clocks}
+
+
+def backward_measure(fp64, steps, warmup):
+    """Forward + backward of 256 matrices of n = 512: Gflop/s with 3 n^3 per
+    gradient (two products, the second over the lower half).  Returns the line."""
+    import numpy as np
+    import torch
+
+    import spd_inputs as si
+    from paper_1002_4057_gb300 import _lib as L
+    from paper_1002_4057_gb300 import torch_api as T
+
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    clk = ClockSampler(0)
+    dtype = torch.float64 if fp64 else torch.float32
+    n, b = 512, 256
+    As = np.stack([si.wishart_spd(n, 1.0, seed=si.SEED_BASE + 4 * 1000 + k) for k in range(b)])
+    Gs = np.stack([si.symmetric_gaussian(n, seed=si.SEED_BASE + 4 * 2000 + k) for k in range(b)])
+    dA = torch.from_numpy(As).to(dev, dtype)
+    dG = torch.from_numpy(Gs).to(dev, dtype)
+    X = T.spd_inverse(dA)
+    grad = torch.empty_like(dA)
+    fn = L.spdinv_potri_backward if dtype == torch.float64 else L.spdinv_spotri_backward
+
+    def bwd():
+        st = fn(b, n, X.data_ptr(), n, n * n, dG.data_ptr(), n, n * n, grad.data_ptr(), n, n * n,
+                stream.cuda_stream)
+        assert st == 0
+
+    def fwd():
+        T.spd_inverse(dA)
+
+    clk.start()
+    ms_b = timed_steps(bwd, steps, warmup, stream)
+    ms_f = timed_steps(fwd, steps, warmup, stream)
+    clocks = clk.stop()
+    line = {"workload": "backward64" if fp64 else "backward32", "metric": METRIC,
+            "value": round(3.0 * b * n ** 3 / (ms_b * 1e-3) / 1e9, 3), "unit": "Gflop/s (3 n^3 per grad)",
+            "ms_backward": round(ms_b, 4), "ms_forward": round(ms_f, 4),
+            "forward_gflops": round(b * n ** 3 / (ms_f * 1e-3) / 1e9, 3),
+            "dtype": "f64" if dtype == torch.float64 else "f32",
+            "config": {"matrices": b, "n": n, "generator": "B B^T/n + I; G = sym(N(0,1))"},
+            "clocks": clocks}
+    del dA, dG, X, grad
+    torch.cuda.empty_cache()
+    return line
 
 
 def run_secondary(args):
@@ -454,38 +721,12 @@ def run_secondary(args):
     if args.workload == "variants":
         run_variants(args, dev, stream)
         return
+    if args.workload == "peaks":
+        print(json.dumps({"workload": "peaks", **measure_peaks(dev, stream)}), flush=True)
+        return
     if args.workload.startswith("batched"):
         raise AssertionError("batched workloads run through run_batched_bench")
-    else:
-        dtype = torch.float64 if args.workload == "backward64" else torch.float32
-        n, b = 512, 256
-        As = np.stack([si.wishart_spd(n, 1.0, seed=si.SEED_BASE + 4 * 1000 + k) for k in range(b)])
-        Gs = np.stack([si.symmetric_gaussian(n, seed=si.SEED_BASE + 4 * 2000 + k) for k in range(b)])
-        dA = torch.from_numpy(As).to(dev, dtype)
-        dG = torch.from_numpy(Gs).to(dev, dtype)
-        X = T.spd_inverse(dA)
-        grad = torch.empty_like(dA)
-        fn = L.spdinv_potri_backward if dtype == torch.float64 else L.spdinv_spotri_backward
-
-        def bwd():
-            st = fn(b, n, X.data_ptr(), n, n * n, dG.data_ptr(), n, n * n, grad.data_ptr(), n, n * n,
-                    stream.cuda_stream)
-            assert st == 0
-
-        def fwd():
-            T.spd_inverse(dA)
-
-        clk.start()
-        ms_b = timed_steps(bwd, args.steps, args.warmup, stream)
-        ms_f = timed_steps(fwd, args.steps, args.warmup, stream)
-        clocks = clk.stop()
-        line = {"workload": args.workload, "metric": METRIC,
-                "value": round(3.0 * b * n ** 3 / (ms_b * 1e-3) / 1e9, 3), "unit": "Gflop/s (3 n^3 per grad)",
-                "ms_backward": round(ms_b, 4), "ms_forward": round(ms_f, 4),
-                "forward_gflops": round(b * n ** 3 / (ms_f * 1e-3) / 1e9, 3),
-                "dtype": "f64" if dtype == torch.float64 else "f32",
-                "config": {"matrices": b, "n": n, "generator": "B B^T/n + I; G = sym(N(0,1))"},
-                "clocks": clocks}
+    line = backward_measure(args.workload == "backward64", args.steps, args.warmup)
     print(json.dumps(line), flush=True)
 
 
@@ -531,7 +772,7 @@ def main():
             dist.barrier()
 
     n, b = args.n, args.tile
-    A0, _, _ = si.spectral_spd(n, args.cond, seed=si.SEED_BASE + 1 + rank, device=dev)
+    A0, Q0, lam0 = si.spectral_spd(n, args.cond, seed=si.SEED_BASE + 1 + rank, device=dev)
     A = torch.empty_like(A0)
     info = torch.zeros(1, dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream()
@@ -644,21 +885,67 @@ def main():
         del hA, hOut, dbuf, views
 
     peaks, src = measured_peaks()
-    peak_tf = peaks["bf16_tflops"] * FP64_NOMINAL_TFLOPS / BF16_NOMINAL_TFLOPS
+    derived_tf = peaks["bf16_tflops"] * FP64_NOMINAL_TFLOPS / BF16_NOMINAL_TFLOPS
     kern_avg_s = statistics.mean(kern_ms) * 1e-3
     achieved_tf = flops / kern_avg_s / 1e12
+
+    # ---- sub-records (rank 0, after the timed regions): this GPU's FP64 peak
+    # measured now, the metric's mixed-vs-FP64 half, batched and backward
+    probe = mixed = batched = backward = None
+    fp64_err = None
+    if rank == 0 and not args.no_extra:
+        import numpy as np
+        cols = np.array([0, n // 3, n - 1])
+        lt = torch.from_numpy(lam0).to(Q0.device)
+        ref = (Q0 @ (Q0[cols, :].t() / lt[:, None])).cpu().numpy()
+        Lo = torch.tril(A)
+        Xc = (Lo[:, cols] + torch.tril(Lo, -1).t()[:, cols]).cpu().numpy()
+        fp64_err = float(np.linalg.norm(Xc - ref) / np.linalg.norm(ref))
+        del Lo
+        probe = measure_peaks(dev, stream)
+        mixed = mixed_record(n, A0, Q0, lam0, args.cond, statistics.mean(kern_ms), stream, dev, probe)
+        mixed["fp64_err"] = fp64_err
+        del Q0
+        torch.cuda.empty_cache()
+        batched = batched_measure(True, 5, 3)
+        backward = backward_measure(True, 3, 3)
+    if probe is not None:
+        peak_tf = max(probe["dmma_fp64"]["tflops"], probe["dfma_fp64"]["tflops"])
+        pm = probe["clocks"].get("sm_mhz")
+        tm = clocks.get("sm_mhz")
+        # the peak at the SM clock of the timed region (the probe ran seconds later)
+        if pm and tm and abs(pm - tm) > 1.0:
+            peak_tf *= tm / pm
+        peak_note = ("FP64 peak measured in this run: max of the DMMA m8n8k4 (%.4f) and DFMA (%.4f) "
+                     "microbenchmarks (spdinv_fp64_peak_probe) at %s MHz, scaled to the timed region's %s MHz; "
+                     "the nominal ratio applied to the measured bf16 rate gives %.4f"
+                     % (probe["dmma_fp64"]["tflops"], probe["dfma_fp64"]["tflops"], pm, tm, derived_tf))
+        peak_src = "measured (spdinv_fp64_peak_probe, this run)"
+    else:
+        peak_tf = derived_tf
+        peak_note = ("FP64 peak = bf16_tflops (%s) x nominal FP64/bf16 ratio 1.25/2250 (the probe "
+                     "did not run: --no-extra or rank > 0)" % src)
+        peak_src = "derived from bf16_tflops (%s)" % src
+    frac = achieved_tf / peak_tf
     roofline = {
         "bound": "tensor", "achieved": round(achieved_tf, 4), "peak": round(peak_tf, 4), "unit": "TFLOP/s",
-        "frac": round(achieved_tf / peak_tf, 4),
+        "frac": round(frac, 4), "peak_source": peak_src,
         # dram__bytes_read.sum + dram__bytes_write.sum of one timed launch of this kernel at
         # n = 16384, tile 32 (an ncu capture of this command with --profile-timed); other
         # sizes and tiles were not captured at full size
         "traffic": TRAFFIC_N16384_B32 if (n, b) == (16384, 32) else None,
         "traffic_unit": "bytes per launch",
+        "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one timed launch of this "
+                           "kernel at this configuration, profiles/potri_fp64_persistent_n16384_b32_dram.md "
+                           "(not measured in this run)") if (n, b) == (16384, 32) else None,
         "kernel": "potri_fp64_persistent<%d> (FP64 DMMA m8n8k4)" % b,
-        "peak_note": "FP64 peak = bf16_tflops (%s) x nominal FP64/bf16 ratio 1.25/2250; "
-                     "DMMA microbenchmark on this GPU: 1.04 TFLOP/s" % src,
+        "peak_note": peak_note,
+        "executed_flops_note": "the kernel executes about n^3 (1 + 5/t) flops (full-tile SYRK chains, "
+                               "warp-granular triangular skipping); achieved counts n^3",
     }
+    if frac > 1.0:
+        roofline["frac_above_one"] = "achieved counts n^3 while the kernel executes more; see executed_flops_note"
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": round(value, 3), "unit": "Gflop/s", "n_gpus": world, "steps": args.steps,
@@ -671,10 +958,12 @@ def main():
                        "plan_order": args.plan_order,
                        "parallelism": "replicas" if world > 1 else "single"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": int(launches),
-            "kernel_ms": [round(x, 3) for x in kern_ms],
+            "kernel_ms": [round(x, 3) for x in kern_ms], "fp64_err": fp64_err,
+            "peaks_measured": probe, "mixed": mixed, "batched_fp64": batched, "backward_fp64": backward,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
+        dist.barrier()
         dist.destroy_process_group()
 
 

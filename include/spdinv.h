@@ -112,7 +112,33 @@ typedef struct {
                             X <- X (I + R + R^2 + ... + R^{p-1}) with R = I - A X, whose new
                             residual is R^p; 0 = 2 (Newton-Schulz).  2..8; p > 2 needs
                             residual = SPDINV_RESIDUAL_EMULATED. */
+    int variant;         /* FP64 spdinv_potri_ex only: an execution variant of Sec. 3's study
+                            (SPDINV_VARIANT_* ORed; 0 = renamed and pipelined, the default).
+                            The result is the same up to rounding (the integer test case:
+                            bit for bit); the variants differ in memory and critical path. */
+    int split_segment;   /* SPDINV_VARIANT_SPLIT3: chain segment length in tiles (0 = 16) */
 } spdinv_opts;
+
+/* Execution variants (spdinv_opts.variant), for the study of Sec. 3 on the GPU:
+ *   SPDINV_VARIANT_UUU       Step 2's update chains in increasing k ("loop
+ *                            reversal" undone: U, U, U instead of U, D, U).
+ *   SPDINV_VARIANT_SHARE_BC  the copy of L^{-1} shares the storage of the copy of
+ *                            L (Sec. 4, renaming under a memory budget): X_ij is
+ *                            stored over L_ij once every task that reads L_ij has
+ *                            read it (write-after-read waits on read counters).
+ *   SPDINV_VARIANT_INPLACE   no renaming: one store holds L, then X = L^{-1}, then
+ *                            A^{-1}, tile by tile, each version stored once all
+ *                            readers of the previous one have read it; the lower
+ *                            triangle of A receives A^{-1} at the end.
+ *   SPDINV_VARIANT_SPLIT3    Step 3's chains of more than split_segment products
+ *                            split into segments whose partial sums other CTAs
+ *                            form in parallel; the tile's own task adds them
+ *                            (the associative reduction of Sec. 4).
+ * SPLIT3 does not combine with SHARE_BC or INPLACE (SPDINV_ERR_UNSUPPORTED). */
+#define SPDINV_VARIANT_UUU 1
+#define SPDINV_VARIANT_SHARE_BC 2
+#define SPDINV_VARIANT_INPLACE 4
+#define SPDINV_VARIANT_SPLIT3 8
 
 #define SPDINV_RESIDUAL_EMULATED 0
 #define SPDINV_RESIDUAL_FP64 1
@@ -202,23 +228,26 @@ SPDINV_API spdinv_status spdinv_inverse_residual(int64_t n, const double* dA, in
 #define SPDINV_NOALLOC_MAX_N 1024
 
 /* spdinv_potri (FP64, tile 32) for callers that must not allocate device
- * memory.  Some callers cannot call cudaMalloc: code that runs while a
- * stream is being captured into a CUDA graph (cudaMalloc is not a stream
- * operation and is refused during capture), plug-ins whose host application
- * owns all device memory through its own allocator or a fixed budget, and
- * latency-bound loops in which an allocation, which can synchronise the whole
- * device, would stall other streams.  This entry point allocates nothing: its
- * scratch (status words, readiness flags, the renamed tile stores and the
- * task list, about 8 MiB) is one fixed array in the library's device memory,
- * which every GPU that loads the library holds until the process exits.
- * The caller still passes A and d_info as for spdinv_potri.
+ * memory.  Some callers cannot call cudaMalloc: plug-ins whose host
+ * application owns all device memory through its own allocator or a fixed
+ * budget, and latency-bound loops in which an allocation, which can
+ * synchronise the whole device, would stall the work of other streams.  This
+ * entry point allocates nothing: its scratch (status words, readiness flags,
+ * the renamed tile stores and the task list, about 8 MiB) is one fixed array
+ * in the library's device memory, which every GPU that loads the library
+ * holds until the process exits.  The caller still passes A and d_info as for
+ * spdinv_potri.
  *  - n > SPDINV_NOALLOC_MAX_N returns SPDINV_ERR_N and launches nothing.
  *  - The first call on a device (with that device current) looks up the
  *    array's device address; make that first call before any stream capture.
+ *    A device reset (cudaDeviceReset) ends the context the address belongs
+ *    to: the first call in the new context looks it up again.
  *  - Every call uses the same array, which keeps the last call's contents
  *    (the call clears what must start at zero).  Calls whose GPU work
  *    overlaps in time -- on different streams, or from different threads --
- *    race on the array and give wrong results; order them on one stream. */
+ *    race on the array and give wrong results; order them on one stream.
+ *  - The wait limit of the persistent kernel is spdinv_potri's default
+ *    (SPDINV_WAIT_TIMEOUT_S, else 60 s). */
 SPDINV_API spdinv_status spdinv_potri_noalloc(int64_t n, double* dA, int64_t lda, int* d_info,
                                               cudaStream_t stream);
 
@@ -425,6 +454,18 @@ SPDINV_API spdinv_status spdinv_plan_emulate(int t, int steps, int workers, uint
                                              int skip_wait_task, double wait_limit_s, int max_delay_us,
                                              int64_t out[5]);
 
+/* spdinv_plan_emulate for an execution variant's plan (spdinv_opts.variant,
+ * SPDINV_VARIANT_*; the whole inversion), with the kernel's write-after-read
+ * protocol: every read of a tile that a later version overwrites is counted,
+ * and the writer of that version waits (bounded) for the count the planner
+ * expects.  A read that finds a later version than it needs counts as a
+ * hazard; a read count that differs from the expected one at the end counts
+ * as a protocol error.  split_segment: as in spdinv_opts.  Same outputs and
+ * limits as spdinv_plan_emulate (no skip-wait hook). */
+SPDINV_API spdinv_status spdinv_plan_emulate_variant(int t, int variant, int split_segment, int workers,
+                                                     uint64_t seed, int drop_task, double wait_limit_s,
+                                                     int max_delay_us, int64_t out[5]);
+
 /* Deterministic schedule of the execution plan for t x t tiles and `steps`
  * on `workers` CTAs (host only; a list-scheduling model of the persistent
  * kernel, no counterpart in the paper, whose Sec. 3 analyses critical paths
@@ -473,6 +514,42 @@ SPDINV_API int spdinv_set_plan_order(int order);
  * is SPDINV_DEBUG from the environment, else 0) and returns the previous
  * ones.  Host only; takes effect for calls made after it returns. */
 SPDINV_API unsigned spdinv_set_debug_flags(unsigned flags);
+
+/* ------------------------------------------------------------------------
+ * Measurement (the paper has no counterpart: utilities for reporting rates
+ * against this GPU's measured peak)
+ * ------------------------------------------------------------------------ */
+
+/* Peak microbenchmark.  Queues one kernel on `stream` that keeps one pipe
+ * busy on register operands -- kind SPDINV_PROBE_DMMA: the FP64 tensor-core
+ * MMA mma.sync m8n8k4 (the instruction of the FP64 tile products),
+ * SPDINV_PROBE_DFMA: the FP64 fused multiply-add, SPDINV_PROBE_FFMA: the FP32
+ * fused multiply-add (the CUDA-core FP32 tile products) -- with 16
+ * independent accumulators per thread, `iters` iterations, `blocks_per_sm`
+ * CTAs of 128 threads per SM (1..16).  *flops receives the number of
+ * floating-point operations the kernel performs (host, set before return);
+ * the caller times the kernel with CUDA events on `stream`.  d_sink: device
+ * buffer of at least 4 * blocks_per_sm * (number of SMs) doubles, written
+ * with the accumulators so that no work is optimised away. */
+#define SPDINV_PROBE_DMMA 0
+#define SPDINV_PROBE_DFMA 1
+#define SPDINV_PROBE_FFMA 2
+SPDINV_API spdinv_status spdinv_fp64_peak_probe(int kind, int64_t iters, int blocks_per_sm, double* d_sink,
+                                                double* flops, cudaStream_t stream);
+
+/* Kernel timing: while on (spdinv_set_kernel_timing(1)), the library records
+ * a CUDA event pair around each of its launches of the kernels below, on the
+ * launch's stream.  spdinv_kernel_time_ms(which, &ms, &launches) waits for the
+ * recorded launches of one kind to finish, returns their summed duration,
+ * count and algorithmic work (*flops: the slice GEMM counts 2 * 128 * 128 *
+ * K per output tile and slice pair, K the padded order; the DAGs n^3), and
+ * forgets them.  Host only; timing costs two event records per launch. */
+#define SPDINV_TIMED_SLICE_GEMM 0  /* the tcgen05 slice products (ozaki_tc_kernel) */
+#define SPDINV_TIMED_MIXED_DAG 1   /* the persistent FP32/FP64 tile DAG of the mixed precision */
+#define SPDINV_TIMED_FP64_DAG 2    /* the persistent FP64 tile DAG */
+#define SPDINV_TIMED_KERNELS 3
+SPDINV_API spdinv_status spdinv_set_kernel_timing(int on);
+SPDINV_API spdinv_status spdinv_kernel_time_ms(int which, double* ms, int* launches, double* flops);
 
 /* ------------------------------------------------------------------------
  * Library information

@@ -47,6 +47,11 @@ SPDINV_RESIDUAL_EMULATED = 0
 SPDINV_RESIDUAL_FP64 = 1
 SPDINV_RESIDUAL_EMULATED_MMA_SYNC = 2
 
+SPDINV_VARIANT_UUU = 1
+SPDINV_VARIANT_SHARE_BC = 2
+SPDINV_VARIANT_INPLACE = 4
+SPDINV_VARIANT_SPLIT3 = 8
+
 SPDINV_DAG_OUT_OF_PLACE = 1
 SPDINV_DAG_RENAME_DIAG = 2
 SPDINV_DAG_UUU = 4
@@ -54,6 +59,14 @@ SPDINV_DAG_PIPELINE = 8
 SPDINV_DAG_TREE = 16
 SPDINV_DAG_TREE_STEP3 = 32
 SPDINV_DAG_SHARE_BC = 64
+
+SPDINV_PROBE_DMMA = 0
+SPDINV_PROBE_DFMA = 1
+SPDINV_PROBE_FFMA = 2
+SPDINV_TIMED_SLICE_GEMM = 0
+SPDINV_TIMED_MIXED_DAG = 1
+SPDINV_TIMED_FP64_DAG = 2
+SPDINV_TIMED_KERNELS = 3
 
 STATUS_NAMES = {0: "SPDINV_OK", -1: "SPDINV_ERR_N", -2: "SPDINV_ERR_LDA", -3: "SPDINV_ERR_NULL",
                 -4: "SPDINV_ERR_CUDA", -5: "SPDINV_ERR_TIMEOUT", -6: "SPDINV_ERR_UNSUPPORTED",
@@ -63,7 +76,7 @@ STATUS_NAMES = {0: "SPDINV_OK", -1: "SPDINV_ERR_N", -2: "SPDINV_ERR_LDA", -3: "S
 class spdinv_opts(ctypes.Structure):
     _fields_ = [("tile", c_int), ("ctas_per_sm", c_int), ("precision", c_int), ("refine_steps", c_int),
                 ("wait_timeout_s", c_double), ("fault_drop_task", c_int), ("residual", c_int),
-                ("refine_order", c_int)]
+                ("refine_order", c_int), ("variant", c_int), ("split_segment", c_int)]
 
 
 # name -> (restype, argtypes); every symbol declared in include/spdinv.h
@@ -86,6 +99,7 @@ SIGNATURES = {
     "spdinv_batch_shard": (c_int, [c_int, P, c_int, P, P]),
     "spdinv_plan_emulate": (c_int, [c_int, c_int, c_int, ctypes.c_uint64, c_int, c_int, c_double, c_int, P]),
     "spdinv_plan_check": (c_int, [c_int, c_int, P]),
+    "spdinv_plan_emulate_variant": (c_int, [c_int, c_int, c_int, c_int, ctypes.c_uint64, c_int, c_double, c_int, P]),
     "spdinv_workspace_size": (c_int, [c_int64, c_int, ctypes.POINTER(spdinv_opts), P]),
     "spdinv_set_workspace": (c_int, [P, ctypes.c_size_t]),
     "spdinv_mirror_lower": (c_int, [c_int, c_int64, P, c_int64, c_int64, P]),
@@ -96,6 +110,9 @@ SIGNATURES = {
     "spdinv_plan_simulate": (c_int, [c_int, c_int, c_int, P]),
     "spdinv_set_plan_order": (c_int, [c_int]),
     "spdinv_set_debug_flags": (ctypes.c_uint, [ctypes.c_uint]),
+    "spdinv_fp64_peak_probe": (c_int, [c_int, c_int64, c_int, P, P, P]),
+    "spdinv_set_kernel_timing": (c_int, [c_int]),
+    "spdinv_kernel_time_ms": (c_int, [c_int, P, P, P]),
     "spdinv_status_name": (ctypes.c_char_p, [c_int]),
     "spdinv_last_cuda_error": (ctypes.c_char_p, []),
     "spdinv_kernel_launches": (ctypes.c_uint64, []),
@@ -229,6 +246,17 @@ def spdinv_plan_emulate(t, workers, seed, drop_task=-1, wait_limit_s=5.0, max_de
     return st, list(out)
 
 
+def spdinv_plan_emulate_variant(t, variant, workers, seed, split_segment=0, drop_task=-1, wait_limit_s=5.0,
+                                max_delay_us=20):
+    """(status, [completed, tasks, protocol errors, hazards, longest wait in
+    us]) of a host emulation of an execution variant's plan, with the
+    kernel's write-after-read protocol."""
+    out = (ctypes.c_int64 * 5)()
+    st = _call("spdinv_plan_emulate_variant", int(t), int(variant), int(split_segment), int(workers), int(seed),
+               int(drop_task), float(wait_limit_s), int(max_delay_us), ctypes.addressof(out))
+    return st, list(out)
+
+
 def spdinv_mirror_lower(batch, n, dA, lda, stride, stream):
     return _call("spdinv_mirror_lower", batch, n, dA, lda, stride, stream)
 
@@ -269,6 +297,29 @@ def spdinv_set_plan_order(order):
 def spdinv_set_debug_flags(flags):
     """Sets the process's debug flags; returns the previous ones."""
     return _call("spdinv_set_debug_flags", int(flags))
+
+
+def spdinv_fp64_peak_probe(kind, iters, blocks_per_sm, d_sink, stream):
+    """(status, flops the queued probe kernel performs)."""
+    fl = ctypes.c_double(0)
+    st = _call("spdinv_fp64_peak_probe", int(kind), int(iters), int(blocks_per_sm), d_sink,
+               ctypes.addressof(fl), stream)
+    return st, fl.value
+
+
+def spdinv_set_kernel_timing(on):
+    return _call("spdinv_set_kernel_timing", int(on))
+
+
+def spdinv_kernel_time_ms(which):
+    """(status, summed ms, launches, algorithmic flops) of the timed launches
+    of one kind since the last query (waits for them to finish)."""
+    ms = ctypes.c_double(0)
+    cnt = ctypes.c_int(0)
+    fl = ctypes.c_double(0)
+    st = _call("spdinv_kernel_time_ms", int(which), ctypes.addressof(ms), ctypes.addressof(cnt),
+               ctypes.addressof(fl))
+    return st, ms.value, cnt.value, fl.value
 
 
 def spdinv_status_name(status):

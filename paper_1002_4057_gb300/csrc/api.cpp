@@ -23,6 +23,8 @@
 
 namespace spdinv {
 
+static size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
 namespace {
 thread_local std::string g_last_cuda_error;
 std::atomic<uint64_t> g_launches{0};
@@ -120,9 +122,40 @@ spdinv_status DeviceState::acquire(size_t bytes, void** out) {
     return SPDINV_OK;
 }
 
+cudaError_t DeviceState::variant_plan(int t, int variant, int seg, const DevicePlan** out) {
+    const auto key = std::make_tuple(t, (int)STEPS_ALL, (int)ORDER_BOTTOM_LEVEL, variant, seg);
+    auto it = plans.find(key);
+    if (it == plans.end()) {
+        ExecPlan p;
+        if (!build_variant_plan(t, variant, seg, &p)) return cudaErrorInvalidValue;
+        const size_t tb = align_up(sizeof(uint32_t) * (p.order.size() + 1), 256);
+        const size_t pb = align_up(sizeof(PartTask) * p.parts.size(), 256);
+        const size_t sb = sizeof(SplitInfo) * p.split.size();
+        DevicePlan dp;
+        dp.ntasks = (int)p.order.size();
+        cudaError_t e = cudaMalloc(&dp.d_tasks, tb + pb + sb + 256);
+        if (e != cudaSuccess) return e;
+        char* base = reinterpret_cast<char*>(dp.d_tasks);
+        dp.d_parts = reinterpret_cast<const PartTask*>(base + tb);
+        dp.d_split = reinterpret_cast<const SplitInfo*>(base + tb + pb);
+        e = cudaMemcpy(dp.d_tasks, p.order.data(), sizeof(uint32_t) * p.order.size(), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && !p.parts.empty())
+            e = cudaMemcpy(base + tb, p.parts.data(), sizeof(PartTask) * p.parts.size(), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && !p.split.empty())
+            e = cudaMemcpy(base + tb + pb, p.split.data(), sb, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            cudaFree(dp.d_tasks);
+            return e;
+        }
+        it = plans.emplace(key, dp).first;
+    }
+    *out = &it->second;
+    return cudaSuccess;
+}
+
 cudaError_t DeviceState::exec_plan(int t, int steps, const uint32_t** d_tasks, int* ntasks) {
     const int order = current_plan_order();
-    const auto key = std::make_tuple(t, steps, order);
+    const auto key = std::make_tuple(t, steps, order, 0, 0);
     auto it = plans.find(key);
     if (it == plans.end()) {
         ExecPlan p = build_exec_plan(t, steps, false, order);
@@ -142,9 +175,7 @@ cudaError_t DeviceState::exec_plan(int t, int steps, const uint32_t** d_tasks, i
     return cudaSuccess;
 }
 
-static size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
-
-static double wait_timeout_s(const spdinv_opts* o) {
+double wait_timeout_s(const spdinv_opts* o) {
     if (o && o->wait_timeout_s > 0) return o->wait_timeout_s;
     if (const char* env = std::getenv("SPDINV_WAIT_TIMEOUT_S")) {
         const double v = std::atof(env);
@@ -179,16 +210,32 @@ spdinv_status fp64_layout(int64_t n, int steps, const spdinv_opts* o, Fp64Layout
     Fp64Layout L;
     L.b = b;
     L.t = (int)t64;
+    L.variant = o ? o->variant : 0;
+    if (L.variant & ~kVariantMask) return SPDINV_ERR_UNSUPPORTED;
+    const bool split = L.variant & VAR_SPLIT3, shared = L.variant & (VAR_SHARE_BC | VAR_INPLACE);
+    if (L.variant && steps != STEPS_ALL) return SPDINV_ERR_UNSUPPORTED;
+    if (split && shared) return SPDINV_ERR_UNSUPPORTED;
+    if (split) {
+        L.seg = o->split_segment > 0 ? o->split_segment : 16;
+        if (L.seg > 16383) return SPDINV_ERR_UNSUPPORTED;
+        for (int i = 0; i < L.t; ++i) {  // the partial tiles of row i: (i + 1) chains of t - 1 - i
+            const int m = L.t - 1 - i;
+            if (m > L.seg) L.nparts += (int64_t)(i + 1) * ((m + L.seg - 1) / L.seg - 1);
+        }
+    }
     L.needB = steps != STEPS_LAUUM;
-    L.needC = steps != STEPS_POTRF;
+    L.needC = steps != STEPS_POTRF && !shared;  // shared variants keep X in B's slots
     if (n > 0) {
         const size_t tile_bytes = (size_t)b * b * sizeof(double);  // a multiple of 256
         const size_t ntri = (size_t)L.t * (L.t - 1) / 2;
-        L.ctrl = align_up(sizeof(int) * (4 + 2 * (size_t)L.t * L.t + L.t), 256);  // status words, flags
+        size_t words = 4 + 2 * (size_t)L.t * L.t + L.t;              // status words, flags
+        if (L.variant) words += 2 * (size_t)L.t * L.t + L.t + (size_t)L.nparts;  // read counters, partials' flags
+        L.ctrl = align_up(sizeof(int) * words, 256);
         L.B = L.needB ? ntri * tile_bytes : 0;
         L.C = L.needC ? ntri * tile_bytes : 0;
         L.D = (size_t)L.t * tile_bytes;
-        L.total = L.ctrl + L.B + L.C + L.D;
+        L.P = (size_t)L.nparts * tile_bytes;
+        L.total = L.ctrl + L.B + L.C + L.D + L.P;
     }
     *out = L;
     return SPDINV_OK;
@@ -242,16 +289,38 @@ spdinv_status run_fp64(int64_t n, double* dA, int64_t lda, int steps, const spdi
     p.timeout_ns = (long long)(wait_timeout_s(o) * 1e9);
     p.drop_task = (o && o->wait_timeout_s > 0 && o->fault_drop_task >= 0) ? o->fault_drop_task : -1;
     p.diag = d_diag;
-    e = ds.exec_plan(t, steps, &p.tasks, &p.ntasks);
-    if (e != cudaSuccess) return cuda_fail(e);
+    p.variant = W.variant;
+    if (W.variant) {
+        if (W.variant & (VAR_SHARE_BC | VAR_INPLACE)) p.Cw = p.Bw;  // X in L's slots
+        const size_t tt = (size_t)t * t;
+        p.reads = p.flags + 2 * tt + t;
+        p.fP = p.reads + 2 * tt + t;
+        p.Pw = reinterpret_cast<double*>(base + W.ctrl + W.B + W.C + W.D);
+        const DevicePlan* vp = nullptr;
+        e = ds.variant_plan(t, W.variant, W.seg, &vp);
+        if (e != cudaSuccess) return cuda_fail(e);
+        p.tasks = vp->d_tasks;
+        p.ntasks = vp->ntasks;
+        p.parts = vp->d_parts;
+        p.split = vp->d_split;
+    } else {
+        e = ds.exec_plan(t, steps, &p.tasks, &p.ntasks);
+        if (e != cudaSuccess) return cuda_fail(e);
+    }
 
     e = cudaMemsetAsync(p.ctrl, 0, W.ctrl, stream);
     if (e != cudaSuccess) return cuda_fail(e);
     int grid = 0;
     const int per = (o && o->ctas_per_sm > 0) ? o->ctas_per_sm : 0;
+    void* tok = nullptr;
+    timing_begin(SPDINV_TIMED_FP64_DAG, stream, &tok);
     e = launch_potri_fp64(p, per, ds.num_sms, d_info, stream, &grid);
     if (e != cudaSuccess) return cuda_fail(e);
-    count_launches(1 + (d_info ? 1 : 0) + ((steps == STEPS_TRTRI || steps == STEPS_LAUUM) ? 1 : 0));
+    const double n3 = (double)n * (double)n * (double)n;  // leading terms: n^3 / 3 per step
+    timing_end(SPDINV_TIMED_FP64_DAG, stream, tok,
+               steps == STEPS_ALL ? n3 : (steps == STEPS_DIAG ? 2.0 * n3 / 3.0 : n3 / 3.0));
+    count_launches(1 + (d_info ? 1 : 0) + ((steps == STEPS_TRTRI || steps == STEPS_LAUUM) ? 1 : 0) +
+                   ((W.variant & VAR_INPLACE) ? 1 : 0));
     ds.last_grid = grid;
     return SPDINV_OK;
 }
@@ -394,6 +463,6 @@ const char* spdinv_last_cuda_error(void) { return g_last_cuda_error.c_str(); }
 
 uint64_t spdinv_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 
-int spdinv_version(void) { return 10000; }
+int spdinv_version(void) { return 10100; }
 
 }  // extern "C"

@@ -54,6 +54,18 @@ struct Emu {
     const std::vector<uint32_t>* tasks = nullptr;
     Flags fL, fX, fD;      // readiness flags of B, C, D
     Words wA, wB, wC, wD;  // writer words: encoded task + 1, or 0 for input / staged data
+    // Execution variants (PlanVariant): the kernel's read counters and
+    // write-after-read waits, the split chains' partial tiles.
+    int variant = 0;
+    const ExecPlan* plan = nullptr;
+    Flags rL, rX, rD, fP;  // reads of L (B), X (C), D; partials' flags
+    Words wP;              // partial tiles' writer words
+    bool uuu() const { return variant & VAR_UUU; }
+    bool shared() const { return variant & (VAR_SHARE_BC | VAR_INPLACE); }
+    bool inplace() const { return variant & VAR_INPLACE; }
+    bool split() const { return variant & VAR_SPLIT3; }
+    // The store that holds X: C, or B's slots when the variant shares them.
+    std::atomic<uint32_t>& slotC(int i, int j) { return shared() ? wB[(size_t)i * t + j] : wC[(size_t)i * t + j]; }
     std::atomic<int> ticket{0}, abort{0}, completed{0}, protocol_errors{0}, hazards{0};
     std::atomic<int64_t> max_wait_us{0};
     int drop = -1, skip = -1;
@@ -108,10 +120,37 @@ struct Emu {
     void check(const std::atomic<uint32_t>& w, uint32_t want) {
         if (w.load(std::memory_order_acquire) != want) hazards.fetch_add(1);
     }
+    // Each read also counts itself, as the kernel does once the copy is in
+    // shared memory, where a later version overwrites the tile.
     void read_A(int i, int j) { check(wA[(size_t)i * t + j], 0u); }
-    void read_B(int i, int j) { check(wB[(size_t)i * t + j], expect_B(i, j)); }
-    void read_C(int i, int j) { check(wC[(size_t)i * t + j], expect_C(i, j)); }
-    void read_D(int j) { check(wD[j], expect_D(j)); }
+    void read_B(int i, int j) {
+        check(wB[(size_t)i * t + j], expect_B(i, j));
+        if (shared()) rL[(size_t)i * t + j].fetch_add(1, std::memory_order_release);
+    }
+    void read_C(int i, int j) {
+        check(slotC(i, j), expect_C(i, j));
+        if (inplace()) rX[(size_t)i * t + j].fetch_add(1, std::memory_order_release);
+    }
+    void read_D(int j) {
+        check(wD[j], expect_D(j));
+        if (inplace()) rD[j].fetch_add(1, std::memory_order_release);
+    }
+    // Bounded wait until `expected` reads of a tile were counted (the
+    // kernel's write-after-read wait); false on timeout or abort.
+    bool wait_reads(const std::atomic<int>& r, int expected) {
+        if (r.load(std::memory_order_acquire) >= expected) return true;
+        const auto t0 = std::chrono::steady_clock::now();
+        for (;;) {
+            if (r.load(std::memory_order_acquire) >= expected) return true;
+            if (abort.load(std::memory_order_relaxed)) return false;
+            const double s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+            if (s > limit_s) {
+                abort.store(1);
+                return false;
+            }
+            std::this_thread::yield();
+        }
+    }
     static void store(std::atomic<uint32_t>& w, uint32_t c) { w.store(c, std::memory_order_release); }
 
     std::atomic<int>* L(int i, int j) { return &fL[(size_t)i * t + j]; }
@@ -169,34 +208,67 @@ struct Emu {
             } else if (kind == K_S2_OFF) {
                 need(D(i), from_A ? L(i, j) : nullptr);
                 if (ok) { read_D(i); read_B(i, j); }
-                for (int k = i - 1; k > j && ok; --k) {
+                for (int m = 0; m < i - j - 1 && ok; ++m) {
+                    const int k = uuu() ? j + 1 + m : i - 1 - m;
                     need(X(i, k), from_A ? L(k, j) : nullptr);
                     if (ok) { read_C(i, k); read_B(k, j); }
                 }
                 need(D(j), nullptr);
                 if (!ok) return;
                 read_D(j);
-                store(wC[(size_t)i * t + j], me);
+                if (shared() && !wait_reads(rL[(size_t)i * t + j], readers_L(t, i, j))) return;
+                store(slotC(i, j), me);
                 if (steps == STEPS_TRTRI) store(wA[(size_t)i * t + j], me);
                 publish(*X(i, j), tk);
+            } else if (kind == K_S3_PART) {  // a segment of a split chain: X tiles only
+                const PartTask q = plan->parts[part_id(e)];
+                for (int k = q.k0; k < q.k1 && ok; ++k) {
+                    need(X(k, q.i), q.j != q.i ? X(k, q.j) : nullptr);
+                    if (ok) { read_C(k, q.i); if (q.j != q.i) read_C(k, q.j); }
+                }
+                if (!ok) return;
+                store(wP[part_id(e)], me);
+                publish(fP[part_id(e)], tk);
             } else if (kind == K_S3_OFF) {
+                const SplitInfo si = split() ? plan->split[tri_index(i, j)] : SplitInfo{0, 0, 0};
+                const int kend = si.np ? si.own_end : t;
                 need(wait_d ? D(i) : nullptr, wait_x ? X(i, j) : nullptr);
                 if (ok) { read_D(i); read_C(i, j); }
-                for (int k = i + 1; k < t && ok; ++k) {
+                for (int k = i + 1; k < kend && ok; ++k) {
                     need(wait_x ? X(k, i) : nullptr, wait_x ? X(k, j) : nullptr);
                     if (ok) { read_C(k, i); read_C(k, j); }
                 }
+                for (uint32_t q = si.first; q < si.first + si.np && ok; ++q) {
+                    need(&fP[q], nullptr);
+                    if (ok) check(wP[q], encode_part(q) + 1u);
+                }
                 if (!ok) return;
-                store(wA[(size_t)i * t + j], me);
+                if (inplace()) {  // A^{-1}_ij over X_ij, after every read of X_ij
+                    if (!wait_reads(rX[(size_t)i * t + j], readers_X(t, i, j))) return;
+                    store(slotC(i, j), me);
+                } else {
+                    store(wA[(size_t)i * t + j], me);
+                }
             } else if (kind == K_S3_DIAG) {
+                const SplitInfo si = split() ? plan->split[tri_index(i, i)] : SplitInfo{0, 0, 0};
+                const int kend = si.np ? si.own_end : t;
                 need(wait_d ? D(i) : nullptr, nullptr);
                 if (ok) read_D(i);
-                for (int k = i + 1; k < t && ok; ++k) {
+                for (int k = i + 1; k < kend && ok; ++k) {
                     need(wait_x ? X(k, i) : nullptr, nullptr);
                     if (ok) read_C(k, i);
                 }
+                for (uint32_t q = si.first; q < si.first + si.np && ok; ++q) {
+                    need(&fP[q], nullptr);
+                    if (ok) check(wP[q], encode_part(q) + 1u);
+                }
                 if (!ok) return;
-                if (steps != STEPS_DIAG) store(wA[(size_t)i * t + i], me);
+                if (inplace()) {  // A^{-1}_ii over X_ii, after every read of X_ii
+                    if (!wait_reads(rD[i], readers_D(t, i))) return;
+                    store(wD[i], me);
+                } else if (steps != STEPS_DIAG) {
+                    store(wA[(size_t)i * t + i], me);
+                }
             } else {
                 protocol_errors.fetch_add(1);  // no other kind exists
             }
@@ -217,17 +289,24 @@ W zeroed(size_t count) {
 
 using namespace spdinv;
 
-extern "C" SPDINV_API spdinv_status spdinv_plan_emulate(int t, int steps, int workers, uint64_t seed, int drop_task,
-                                                        int skip_wait_task, double wait_limit_s, int max_delay_us,
-                                                        int64_t out[5]) {
+namespace spdinv {
+namespace {
+
+spdinv_status emulate(int t, int steps, int variant, int seg, int workers, uint64_t seed, int drop_task,
+                      int skip_wait_task, double wait_limit_s, int max_delay_us, int64_t out[5]) {
     if (t < 1 || t > 256) return SPDINV_ERR_N;
     if (steps < STEPS_ALL || steps > STEPS_DIAG) return SPDINV_ERR_UNSUPPORTED;
     if (workers < 1 || workers > 1024 || wait_limit_s <= 0.0 || max_delay_us < 0) return SPDINV_ERR_UNSUPPORTED;
     if (!out) return SPDINV_ERR_NULL;
-    const ExecPlan plan = build_exec_plan(t, steps, false, current_plan_order());
+    if (variant != 0 && steps != STEPS_ALL) return SPDINV_ERR_UNSUPPORTED;
+    ExecPlan plan;
+    if (variant == 0) plan = build_exec_plan(t, steps, false, current_plan_order());
+    else if (!build_variant_plan(t, variant, seg, &plan)) return SPDINV_ERR_UNSUPPORTED;
     Emu emu;
     emu.t = t;
     emu.steps = steps;
+    emu.variant = variant;
+    emu.plan = &plan;
     emu.s1 = steps == STEPS_ALL || steps == STEPS_POTRF || steps == STEPS_DIAG;
     emu.s2 = steps == STEPS_ALL || steps == STEPS_TRTRI || steps == STEPS_DIAG;
     emu.from_A = emu.s1;                   // else L is staged before the launch
@@ -242,6 +321,11 @@ extern "C" SPDINV_API spdinv_status spdinv_plan_emulate(int t, int steps, int wo
     emu.wB = zeroed<Words>(tt);
     emu.wC = zeroed<Words>(tt);
     emu.wD = zeroed<Words>((size_t)t);
+    emu.rL = zeroed<Flags>(tt);
+    emu.rX = zeroed<Flags>(tt);
+    emu.rD = zeroed<Flags>((size_t)t);
+    emu.fP = zeroed<Flags>(plan.parts.size() + 1);
+    emu.wP = zeroed<Words>(plan.parts.size() + 1);
     emu.drop = drop_task;
     emu.skip = skip_wait_task;
     emu.limit_s = wait_limit_s;
@@ -251,12 +335,41 @@ extern "C" SPDINV_API spdinv_status spdinv_plan_emulate(int t, int steps, int wo
     th.reserve(workers);
     for (int w = 0; w < workers; ++w) th.emplace_back([&emu, w] { emu.run_worker(w); });
     for (auto& x : th) x.join();
+    // Every counted tile must have been read exactly as often as the kernel's
+    // write-after-read waits assume (a wrong count would make them release a
+    // tile early or wait forever).
+    if (!emu.abort.load() && emu.completed.load() == (int)plan.order.size()) {
+        for (int a = 0; a < t; ++a) {
+            for (int b = 0; b < a; ++b) {
+                if (emu.shared() && emu.rL[(size_t)a * t + b].load() != readers_L(t, a, b)) emu.protocol_errors++;
+                if (emu.inplace() && emu.rX[(size_t)a * t + b].load() != readers_X(t, a, b)) emu.protocol_errors++;
+            }
+            if (emu.inplace() && emu.rD[a].load() != readers_D(t, a)) emu.protocol_errors++;
+        }
+    }
     out[0] = emu.completed.load();
     out[1] = (int64_t)plan.order.size();
     out[2] = emu.protocol_errors.load();
     out[3] = emu.hazards.load();
     out[4] = emu.max_wait_us.load();
     return emu.abort.load() ? SPDINV_ERR_TIMEOUT : SPDINV_OK;
+}
+
+}  // namespace
+}  // namespace spdinv
+
+extern "C" SPDINV_API spdinv_status spdinv_plan_emulate(int t, int steps, int workers, uint64_t seed, int drop_task,
+                                                        int skip_wait_task, double wait_limit_s, int max_delay_us,
+                                                        int64_t out[5]) {
+    return emulate(t, steps, 0, 0, workers, seed, drop_task, skip_wait_task, wait_limit_s, max_delay_us, out);
+}
+
+extern "C" SPDINV_API spdinv_status spdinv_plan_emulate_variant(int t, int variant, int split_segment, int workers,
+                                                                uint64_t seed, int drop_task, double wait_limit_s,
+                                                                int max_delay_us, int64_t out[5]) {
+    if (variant < 0) return SPDINV_ERR_UNSUPPORTED;
+    return emulate(t, STEPS_ALL, variant, split_segment, workers, seed, drop_task, -1, wait_limit_s, max_delay_us,
+                   out);
 }
 
 // Deterministic schedule of the same plan on `workers` CTAs (a list-scheduling

@@ -26,6 +26,13 @@ struct KParamsF64 {
     long long timeout_ns; // limit of one dependency wait
     int drop_task;        // failure-injection hook (-1 = off)
     double* diag;         // STEPS_DIAG: receives diag(A^{-1}) (n entries); A is not written
+    // Execution variants (PlanVariant flags; 0 = the renamed, pipelined plan).
+    int variant;
+    int* reads;             // read counters: [t*t] of L (B), [t*t] of X (C), [t] of D
+    const PartTask* parts;  // VAR_SPLIT3: segments by part id
+    const SplitInfo* split; // VAR_SPLIT3: per Step-3 tile, tri_index(i, j)
+    double* Pw;             // VAR_SPLIT3: partial tiles by part id, tile-major
+    int* fP;                // VAR_SPLIT3: their readiness flags
 };
 
 // Queues the FP64 persistent inversion (plus the stage-in copy for the

@@ -488,6 +488,157 @@ ExecPlan build_exec_plan(int t, int steps, bool exhaustive, int order) {
     return p;
 }
 
+bool build_variant_plan(int t, int variant, int seg, ExecPlan* out) {
+    if (variant & ~kVariantMask) return false;
+    const bool share = variant & (VAR_SHARE_BC | VAR_INPLACE), inplace = variant & VAR_INPLACE;
+    const bool split = variant & VAR_SPLIT3;
+    if (split && (share || seg < 1)) return false;
+    if (variant == 0) {
+        *out = build_exec_plan(t, STEPS_ALL, false);
+        return true;
+    }
+    ExecPlan p;
+    p.t = t;
+    p.steps = STEPS_ALL;
+    p.variant = variant;
+    p.seg = split ? seg : 0;
+    const size_t T = (size_t)t;
+    // Sequential order: Algorithm 1's loop nest (Step 2: j and i decreasing),
+    // each split chain's segments just before the task that adds them.  It is
+    // a topological order of every edge below, write-after-read included: it
+    // is the order of a correct sequential in-place program.
+    std::vector<uint32_t> seq;
+    for (int j = 0; j < t; ++j) {
+        seq.push_back(encode_task(K_S1_DIAG, j, j));
+        for (int i = j + 1; i < t; ++i) seq.push_back(encode_task(K_S1_OFF, i, j));
+    }
+    for (int j = t - 1; j >= 0; --j)
+        for (int i = t - 1; i > j; --i) seq.push_back(encode_task(K_S2_OFF, i, j));
+    if (split) p.split.assign(T * (T + 1) / 2, SplitInfo{0, 0, 0});
+    for (int i = 0; i < t; ++i)
+        for (int j = 0; j <= i; ++j) {
+            const int m = t - 1 - i;  // chain length
+            if (split && m > seg) {
+                const int np = (m + seg - 1) / seg;
+                SplitInfo& si = p.split[tri_index(i, j)];
+                si.first = (uint32_t)p.parts.size();
+                si.np = (uint16_t)(np - 1);
+                si.own_end = (uint16_t)(i + 1 + seg);
+                for (int q = 1; q < np; ++q) {
+                    const int k0 = i + 1 + q * seg, k1 = std::min(t, k0 + seg);
+                    seq.push_back(encode_part((uint32_t)p.parts.size()));
+                    p.parts.push_back(PartTask{(uint16_t)i, (uint16_t)j, (uint16_t)k0, (uint16_t)k1});
+                }
+            }
+            seq.push_back(j < i ? encode_task(K_S3_OFF, i, j) : encode_task(K_S3_DIAG, i, i));
+        }
+    const size_t N = seq.size();
+    TaskIndex ix(t);
+    std::vector<int32_t> part_pos(p.parts.size(), -1);
+    for (size_t r = 0; r < N; ++r) {
+        const uint32_t e = seq[r];
+        if (task_kind(e) == K_S3_PART) part_pos[part_id(e)] = (int32_t)r;
+        else ix.at(task_kind(e), task_i(e), task_j(e)) = (int32_t)r;
+    }
+    auto L = [&](int i, int j) { return ix.at(K_S1_OFF, i, j); };
+    auto X = [&](int i, int j) { return ix.at(K_S2_OFF, i, j); };
+    auto D = [&](int j) { return ix.at(K_S1_DIAG, j, j); };
+    auto own_end = [&](int i, int j) -> int {
+        if (!split) return t;
+        const SplitInfo& si = p.split[tri_index(i, j)];
+        return si.np ? si.own_end : t;
+    };
+    auto cost = [&](uint32_t e) -> double {
+        const int i = task_i(e), j = task_j(e);
+        switch (task_kind(e)) {
+            case K_S1_DIAG: return j + 0.7;
+            case K_S1_OFF: return j + 1.0;
+            case K_S2_OFF: return (i - j - 1) + 2.0;
+            case K_S3_PART: {
+                const PartTask& q = p.parts[part_id(e)];
+                return (double)(q.k1 - q.k0);
+            }
+            default: {  // K_S3_OFF, K_S3_DIAG: the own segment, the TRMM / LAUUM, the partial sums
+                const int np = split ? p.split[tri_index(i, j)].np : 0;
+                return (own_end(i, j) - i - 1) + 1.0 + 0.25 * np;
+            }
+        }
+    };
+    // Every task that must finish before task e: the producers of what it
+    // reads and, when e stores over a tile that others still read, those
+    // readers (write after read).
+    auto for_preds = [&](uint32_t e, auto&& f) {
+        const int i = task_i(e), j = task_j(e);
+        switch (task_kind(e)) {
+            case K_S1_DIAG:
+                for (int k = 0; k < j; ++k) f(L(j, k));
+                break;
+            case K_S1_OFF:
+                for (int k = 0; k < j; ++k) { f(L(i, k)); f(L(j, k)); }
+                f(D(j));
+                break;
+            case K_S2_OFF:
+                f(D(i)); f(L(i, j));
+                for (int k = j + 1; k < i; ++k) { f(X(i, k)); f(L(k, j)); }
+                f(D(j));
+                if (share) {  // X_ij is stored over L_ij: every other reader of L_ij first
+                    f(D(i));  // S1_DIAG(i) read L_ij (it is also D(i)'s producer)
+                    for (int q = j + 1; q < i; ++q) f(L(i, q));
+                    for (int q = i + 1; q < t; ++q) { f(L(q, i)); f(X(q, j)); }
+                }
+                break;
+            case K_S3_PART: {
+                const PartTask& q = p.parts[part_id(e)];
+                for (int k = q.k0; k < q.k1; ++k) { f(X(k, q.i)); if (q.j != q.i) f(X(k, q.j)); }
+                break;
+            }
+            case K_S3_OFF:
+                f(D(i)); f(X(i, j));
+                for (int k = i + 1; k < own_end(i, j); ++k) { f(X(k, i)); f(X(k, j)); }
+                if (split)
+                    for (uint32_t q = 0; q < p.split[tri_index(i, j)].np; ++q)
+                        f(part_pos[p.split[tri_index(i, j)].first + q]);
+                if (inplace) {  // A^{-1}_ij is stored over X_ij
+                    for (int q = 0; q < j; ++q) f(X(i, q));             // S2(i, q) read X_ij
+                    for (int q = 0; q < j; ++q) f(ix.at(K_S3_OFF, j, q));  // S3(j, q) read X_ij as X_kj
+                    for (int q = j + 1; q < i; ++q) f(ix.at(K_S3_OFF, q, j));
+                    f(ix.at(K_S3_DIAG, j, j));
+                }
+                break;
+            case K_S3_DIAG:
+                f(D(i));
+                for (int k = i + 1; k < own_end(i, i); ++k) f(X(k, i));
+                if (split)
+                    for (uint32_t q = 0; q < p.split[tri_index(i, i)].np; ++q)
+                        f(part_pos[p.split[tri_index(i, i)].first + q]);
+                if (inplace) {  // A^{-1}_ii is stored over X_ii
+                    for (int q = i + 1; q < t; ++q) { f(L(q, i)); f(X(q, i)); }
+                    for (int q = 0; q < i; ++q) { f(X(i, q)); f(ix.at(K_S3_OFF, i, q)); }
+                }
+                break;
+        }
+    };
+    std::vector<double> bl(N, 0.0), succmax(N, 0.0);
+    double work = 0.0;
+    for (size_t r = N; r-- > 0;) {
+        const double c = cost(seq[r]);
+        work += c;
+        bl[r] = c + succmax[r];
+        for_preds(seq[r], [&](int32_t q) {
+            if (q >= 0 && (size_t)q != r) succmax[q] = std::max(succmax[q], bl[r]);
+        });
+    }
+    std::vector<uint32_t> perm(N);
+    std::iota(perm.begin(), perm.end(), 0u);
+    std::stable_sort(perm.begin(), perm.end(), [&](uint32_t a, uint32_t b) { return bl[a] > bl[b]; });
+    p.crit = N ? bl[perm[0]] : 0.0;
+    p.work = work;
+    p.order.resize(N);
+    for (size_t m = 0; m < N; ++m) p.order[m] = seq[perm[m]];
+    *out = std::move(p);
+    return true;
+}
+
 namespace {
 std::atomic<int>& plan_order_setting() {
     static std::atomic<int> order{[] {

@@ -84,7 +84,50 @@ __device__ void store_ws_tile(double* g, const double* T) {
     for (int idx = threadIdx.x; idx < B * B / 2; idx += kThreads) d[idx] = s[idx];
 }
 
-template <int B>
+// Write-after-read wait of the shared-storage variants: thread 0 waits
+// (bounded) until `expected` readers have counted their reads of the tile the
+// CTA is about to overwrite.  false = stop (abort or timeout).
+__device__ __forceinline__ bool wait_reads(PCtx& c, const int* r, int expected) {
+    if (threadIdx.x == 0) {
+        bool ok = true;
+        if (ld_acquire_gpu(r) < expected) {
+            const uint64_t t0 = globaltimer_ns();
+            unsigned ns = 32;
+            for (;;) {
+                if (ld_acquire_gpu(r) >= expected) break;
+                if (ld_relaxed_gpu(&c.ctrl[1]) != 0) {
+                    ok = false;
+                    break;
+                }
+                if ((long long)(globaltimer_ns() - t0) > c.timeout_ns) {
+                    raise_error(c.ctrl, SPDINV_ERR_TIMEOUT);
+                    ok = false;
+                    break;
+                }
+                __nanosleep(ns);
+                if (ns < 1024) ns <<= 1;
+            }
+        }
+        *c.s_flag = ok ? 0 : 1;
+    }
+    cta_sync();
+    return *c.s_flag == 0;
+}
+
+// Thread 0 counts one completed read of each given tile (the copies are in
+// shared memory when fetch returns, so the tile may be overwritten after it).
+__device__ __forceinline__ void count_reads(int* r0, int* r1) {
+    if (threadIdx.x == 0) {
+        if (r0) red_release_add_gpu(r0, 1);
+        if (r1) red_release_add_gpu(r1, 1);
+    }
+}
+
+// VAR = false: the renamed, pipelined plan (the library's default).  VAR =
+// true also runs the execution variants of p.variant: Step 2's chains in U
+// order, C sharing B's storage, a single in-place store, split Step-3
+// chains.  The variant code is compiled only into the VAR = true kernel.
+template <int B, bool VAR>
 __global__ void __launch_bounds__(kThreads) potri_fp64_persistent(const KParamsF64 prm) {
     unsigned char* const smem_raw = dynamic_smem();
     __shared__ __align__(8) uint64_t bar;
@@ -115,6 +158,16 @@ __global__ void __launch_bounds__(kThreads) potri_fp64_persistent(const KParamsF
     const bool from_A = p.steps == STEPS_ALL || p.steps == STEPS_POTRF || p.steps == STEPS_DIAG;
     // D_i is staged before the launch for spdinv_lauum: nothing to wait for.
     auto dflag = [&](int q) -> const int* { return p.steps == STEPS_LAUUM ? nullptr : &fD[q]; };
+    // Variants: which reads are counted (the tiles a later version overwrites).
+    const int var = VAR ? p.variant : 0;
+    const bool uuu = VAR && (var & VAR_UUU);
+    const bool cnt_l = VAR && (var & (VAR_SHARE_BC | VAR_INPLACE));
+    const bool inplace = VAR && (var & VAR_INPLACE);
+    const bool split = VAR && (var & VAR_SPLIT3);
+    int* const rL = VAR ? p.reads : nullptr;
+    auto cL = [&](int a, int b) -> int* { return cnt_l ? rL + (int64_t)a * t + b : nullptr; };
+    auto cX = [&](int a, int b) -> int* { return inplace ? rL + (int64_t)t * t + (int64_t)a * t + b : nullptr; };
+    auto cD = [&](int j) -> int* { return inplace ? rL + 2 * (int64_t)t * t + j : nullptr; };
 
     for (;;) {
         const int ticket = next_ticket(p.ctrl, p.ntasks, &s_task);
@@ -129,6 +182,7 @@ __global__ void __launch_bounds__(kThreads) potri_fp64_persistent(const KParamsF
             acc_load<B>(acc, T0);
             for (int k = 0; k < j; ++k) {  // SYRK chain, U order
                 if (!fetch<B>(c, &fL[j * t + k], nullptr, tileB<B>(p, j, k), nullptr)) return;
+                if constexpr (VAR) count_reads(cL(j, k), nullptr);
                 tile_mma<B, false, true, true, FULL, FULL>(acc, T0, T0);
             }
             cta_sync();
@@ -150,10 +204,12 @@ __global__ void __launch_bounds__(kThreads) potri_fp64_persistent(const KParamsF
             acc_load<B>(acc, T0);
             for (int k = 0; k < j; ++k) {  // GEMM chain, U order
                 if (!fetch<B>(c, &fL[i * t + k], &fL[j * t + k], tileB<B>(p, i, k), tileB<B>(p, j, k))) return;
+                if constexpr (VAR) count_reads(cL(i, k), cL(j, k));
                 tile_mma<B, false, true, true, FULL, FULL>(acc, T0, T1);
             }
             // TRSM: L_ij = A'_ij L_jj^{-T} = A'_ij X_jj^T
             if (!fetch<B>(c, &fD[j], nullptr, nullptr, tileD<B>(p, j))) return;
+            if constexpr (VAR) count_reads(cD(j), nullptr);
             acc_store<B>(acc, T0);
             cta_sync();
             acc_zero<B>(acc);
@@ -173,16 +229,27 @@ __global__ void __launch_bounds__(kThreads) potri_fp64_persistent(const KParamsF
         } else if (kind == K_S2_OFF) {
             // X_ii L_ij
             if (!fetch<B>(c, &fD[i], from_A ? &fL[i * t + j] : nullptr, tileD<B>(p, i), tileB<B>(p, i, j))) return;
+            if constexpr (VAR) count_reads(cD(i), cL(i, j));
             acc_zero<B>(acc);
             tile_mma<B, false, false, false, LOWER, FULL>(acc, T0, T1);
-            for (int k = i - 1; k > j; --k) {  // GEMM chain, D order
-                if (!fetch<B>(c, &fX[i * t + k], from_A ? &fL[k * t + j] : nullptr, tileC<B>(p, i, k),
-                              tileB<B>(p, k, j)))
-                    return;
-                tile_mma<B, false, false, false, FULL, FULL>(acc, T0, T1);
+            if (!uuu) {
+                for (int k = i - 1; k > j; --k) {  // GEMM chain, D order
+                    if (!fetch<B>(c, &fX[i * t + k], from_A ? &fL[k * t + j] : nullptr, tileC<B>(p, i, k),
+                                  tileB<B>(p, k, j)))
+                        return;
+                    if constexpr (VAR) count_reads(cX(i, k), cL(k, j));
+                    tile_mma<B, false, false, false, FULL, FULL>(acc, T0, T1);
+                }
+            } else if constexpr (VAR) {
+                for (int k = j + 1; k < i; ++k) {  // GEMM chain, U order (the UUU variant)
+                    if (!fetch<B>(c, &fX[i * t + k], &fL[k * t + j], tileC<B>(p, i, k), tileB<B>(p, k, j))) return;
+                    count_reads(cX(i, k), cL(k, j));
+                    tile_mma<B, false, false, false, FULL, FULL>(acc, T0, T1);
+                }
             }
             // X_ij = -(...) X_jj
             if (!fetch<B>(c, &fD[j], nullptr, nullptr, tileD<B>(p, j))) return;
+            if constexpr (VAR) count_reads(cD(j), nullptr);
             acc_store<B>(acc, T0);
             cta_sync();
             acc_zero<B>(acc);
@@ -190,38 +257,107 @@ __global__ void __launch_bounds__(kThreads) potri_fp64_persistent(const KParamsF
             cta_sync();
             acc_store<B>(acc, T0);
             cta_sync();
+            if constexpr (VAR) {  // X_ij goes over L_ij: every reader of L_ij first
+                if (cnt_l && !wait_reads(c, cL(i, j), readers_L(t, i, j))) return;
+            }
             store_ws_tile<B>(const_cast<double*>(tileC<B>(p, i, j)), T0);
             if (p.steps == STEPS_TRTRI) store_A_tile<B>(p, i, j, T0, false);
             publish(c, &fX[i * t + j], ticket);
+        } else if (VAR && kind == K_S3_PART) {  // one segment of a split Step-3 chain
+            if constexpr (VAR) {
+                const int q = (int)part_id(e);
+                const PartTask pt = p.parts[q];
+                acc_zero<B>(acc);
+                for (int k = pt.k0; k < pt.k1; ++k) {
+                    if (pt.i == pt.j) {
+                        if (!fetch<B>(c, &fX[k * t + pt.i], nullptr, tileC<B>(p, k, pt.i), nullptr)) return;
+                        tile_mma<B, true, false, false, FULL, FULL>(acc, T0, T0);
+                    } else {
+                        if (!fetch<B>(c, &fX[k * t + pt.i], &fX[k * t + pt.j], tileC<B>(p, k, pt.i),
+                                      tileC<B>(p, k, pt.j)))
+                            return;
+                        tile_mma<B, true, false, false, FULL, FULL>(acc, T0, T1);
+                    }
+                }
+                cta_sync();
+                acc_store<B>(acc, T0);
+                cta_sync();
+                store_ws_tile<B>(p.Pw + (int64_t)q * (B * B), T0);
+                publish(c, &p.fP[q], ticket);
+            }
         } else if (kind == K_S3_OFF) {
             const bool wait_x = p.steps != STEPS_LAUUM;
+            int kend = t;
+            if constexpr (VAR) {
+                if (split && p.split[tri_index(i, j)].np) kend = p.split[tri_index(i, j)].own_end;
+            }
             // X_ii^T X_ij
             if (!fetch<B>(c, dflag(i), wait_x ? &fX[i * t + j] : nullptr, tileD<B>(p, i), tileC<B>(p, i, j))) return;
+            if constexpr (VAR) count_reads(cD(i), cX(i, j));
             acc_zero<B>(acc);
             tile_mma<B, true, false, false, LOWER, FULL>(acc, T0, T1);
-            for (int k = i + 1; k < t; ++k) {  // GEMM chain, U order
+            for (int k = i + 1; k < kend; ++k) {  // GEMM chain, U order
                 if (!fetch<B>(c, wait_x ? &fX[k * t + i] : nullptr, wait_x ? &fX[k * t + j] : nullptr,
                               tileC<B>(p, k, i), tileC<B>(p, k, j)))
                     return;
+                if constexpr (VAR) count_reads(cX(k, i), cX(k, j));
                 tile_mma<B, true, false, false, FULL, FULL>(acc, T0, T1);
+            }
+            if constexpr (VAR) {  // the partial sums of the chain's other segments, in order
+                if (split) {
+                    const SplitInfo si = p.split[tri_index(i, j)];
+                    for (uint32_t q = si.first; q < si.first + si.np; ++q) {
+                        if (!fetch<B>(c, &p.fP[q], nullptr, p.Pw + (int64_t)q * (B * B), nullptr)) return;
+                        acc_add<B>(acc, T0);
+                    }
+                }
             }
             cta_sync();
             acc_store<B>(acc, T0);
             cta_sync();
+            if constexpr (VAR) {
+                if (inplace) {  // A^{-1}_ij goes over X_ij: every reader of X_ij first
+                    if (!wait_reads(c, cX(i, j), readers_X(t, i, j))) return;
+                    store_ws_tile<B>(const_cast<double*>(tileC<B>(p, i, j)), T0);
+                    continue;
+                }
+            }
             store_A_tile<B>(p, i, j, T0, false);
         } else {  // K_S3_DIAG
             const bool wait_x = p.steps != STEPS_LAUUM;
+            int kend = t;
+            if constexpr (VAR) {
+                if (split && p.split[tri_index(i, i)].np) kend = p.split[tri_index(i, i)].own_end;
+            }
             // LAUUM: X_ii^T X_ii
             if (!fetch<B>(c, dflag(i), nullptr, tileD<B>(p, i), nullptr)) return;
+            if constexpr (VAR) count_reads(cD(i), nullptr);
             acc_zero<B>(acc);
             tile_mma<B, true, false, false, LOWER, LOWER>(acc, T0, T0);
-            for (int k = i + 1; k < t; ++k) {  // SYRK chain, U order
+            for (int k = i + 1; k < kend; ++k) {  // SYRK chain, U order
                 if (!fetch<B>(c, wait_x ? &fX[k * t + i] : nullptr, nullptr, tileC<B>(p, k, i), nullptr)) return;
+                if constexpr (VAR) count_reads(cX(k, i), nullptr);
                 tile_mma<B, true, false, false, FULL, FULL>(acc, T0, T0);
+            }
+            if constexpr (VAR) {
+                if (split) {
+                    const SplitInfo si = p.split[tri_index(i, i)];
+                    for (uint32_t q = si.first; q < si.first + si.np; ++q) {
+                        if (!fetch<B>(c, &p.fP[q], nullptr, p.Pw + (int64_t)q * (B * B), nullptr)) return;
+                        acc_add<B>(acc, T0);
+                    }
+                }
             }
             cta_sync();
             acc_store<B>(acc, T0);
             cta_sync();
+            if constexpr (VAR) {
+                if (inplace) {  // A^{-1}_ii goes over X_ii: every reader of X_ii first
+                    if (!wait_reads(c, cD(i), readers_D(t, i))) return;
+                    store_ws_tile<B>(const_cast<double*>(tileD<B>(p, i)), T0);
+                    continue;
+                }
+            }
             if (p.steps == STEPS_DIAG) {
                 for (int r = threadIdx.x; r < B; r += kThreads) {
                     const int64_t g = (int64_t)i * B + r;
@@ -230,6 +366,32 @@ __global__ void __launch_bounds__(kThreads) potri_fp64_persistent(const KParamsF
             } else {
                 store_A_tile<B>(p, i, i, T0, true);
             }
+        }
+    }
+}
+
+// The in-place variant's result: the lower tiles of its single store (which
+// hold A^{-1} after Step 3) into A, clipped to n; diagonal tiles' lower part.
+template <int B>
+__global__ void __launch_bounds__(kThreads) stage_out_fp64(const KParamsF64 p) {
+    const int t = p.t;
+    const int64_t ntri = (int64_t)t * (t - 1) / 2;
+    for (int64_t tile = blockIdx.x; tile < ntri + t; tile += gridDim.x) {
+        int ti, tj;
+        const bool is_diag = tile >= ntri;
+        if (is_diag) {
+            ti = tj = (int)(tile - ntri);
+        } else {
+            ti = (int)((1.0 + sqrt(1.0 + 8.0 * (double)tile)) / 2.0);
+            while ((int64_t)ti * (ti - 1) / 2 > tile) --ti;
+            while ((int64_t)(ti + 1) * ti / 2 <= tile) ++ti;
+            tj = (int)(tile - (int64_t)ti * (ti - 1) / 2);
+        }
+        const double* src = is_diag ? p.Dw + (int64_t)ti * B * B : p.Cw + tile * (int64_t)(B * B);
+        for (int idx = threadIdx.x; idx < B * B; idx += kThreads) {
+            const int r = idx % B, cc = idx / B;
+            const int64_t gr = (int64_t)ti * B + r, gc = (int64_t)tj * B + cc;
+            if (gr < p.n && gc < p.n && !(is_diag && r < cc)) p.A[gr + gc * p.lda] = src[idx];
         }
     }
 }
@@ -282,9 +444,9 @@ int smem_bytes() {
     return (2 * B * B + kThreads) * (int)sizeof(double);
 }
 
-template <int B>
+template <int B, bool VAR>
 cudaError_t launch_impl(const KParamsF64& p, int ctas_per_sm, int num_sms, cudaStream_t s, int* grid_out) {
-    auto kern = potri_fp64_persistent<B>;
+    auto kern = potri_fp64_persistent<B, VAR>;
     const int sm = smem_bytes<B>();
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     if (e != cudaSuccess) return e;
@@ -308,7 +470,15 @@ cudaError_t launch_impl(const KParamsF64& p, int ctas_per_sm, int num_sms, cudaS
         if (e != cudaSuccess) return e;
     }
     kern<<<grid, kThreads, sm, s>>>(p);
-    return cudaGetLastError();
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (VAR && (p.variant & VAR_INPLACE)) {
+        const int64_t ntiles = (int64_t)p.t * (p.t + 1) / 2;
+        const int g2 = (int)(ntiles < 4096 ? ntiles : 4096);
+        stage_out_fp64<B><<<g2, kThreads, 0, s>>>(p);
+        e = cudaGetLastError();
+    }
+    return e;
 }
 
 }  // namespace
@@ -316,9 +486,16 @@ cudaError_t launch_impl(const KParamsF64& p, int ctas_per_sm, int num_sms, cudaS
 cudaError_t launch_potri_fp64(const KParamsF64& p, int ctas_per_sm, int num_sms, int* d_info, cudaStream_t s,
                               int* grid_out) {
     cudaError_t e;
+    const bool var = p.variant != 0;
     switch (p.b) {
-        case 32: e = launch_impl<32>(p, ctas_per_sm, num_sms, s, grid_out); break;
-        case 64: e = launch_impl<64>(p, ctas_per_sm, num_sms, s, grid_out); break;
+        case 32:
+            e = var ? launch_impl<32, true>(p, ctas_per_sm, num_sms, s, grid_out)
+                    : launch_impl<32, false>(p, ctas_per_sm, num_sms, s, grid_out);
+            break;
+        case 64:
+            e = var ? launch_impl<64, true>(p, ctas_per_sm, num_sms, s, grid_out)
+                    : launch_impl<64, false>(p, ctas_per_sm, num_sms, s, grid_out);
+            break;
         default: return cudaErrorInvalidValue;
     }
     if (e != cudaSuccess) return e;

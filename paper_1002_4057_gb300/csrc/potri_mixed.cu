@@ -290,16 +290,14 @@ __global__ void __launch_bounds__(kThreads) residual_kernel(int64_t n, const dou
         tile_mma<RB, false, false, false, FULL, FULL>(acc, S0, S1);
     }
 #pragma unroll
-    for (int mi = 0; mi < TileCfg<RB>::MI; ++mi)
+    for (int a = 0; a < TileCfg<RB>::RM; ++a)
 #pragma unroll
-        for (int ni = 0; ni < TileCfg<RB>::NI; ++ni)
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                int r, cc;
-                acc_coord<RB>(mi, ni, h, r, cc);
-                const int64_t gr = (int64_t)ti * RB + r, gc = (int64_t)tj * RB + cc;
-                if (gr < n && gc < n) R[gr + gc * n] = (gr == gc ? 1.0 : 0.0) - acc.v[mi][ni][h];
-            }
+        for (int b = 0; b < TileCfg<RB>::CN; ++b) {
+            int r, cc;
+            acc_coord<RB>(a, b, r, cc);
+            const int64_t gr = (int64_t)ti * RB + r, gc = (int64_t)tj * RB + cc;
+            if (gr < n && gc < n) R[gr + gc * n] = (gr == gc ? 1.0 : 0.0) - acc.v[a][b];
+        }
 }
 
 // Xn = X + X R, the product in FP32 (R is small), the sum in FP64.
@@ -383,6 +381,7 @@ constexpr int kSlices = 7, kLevels = 6, kLevelsLast = 7;
 spdinv_status mixed_layout(int64_t n, const spdinv_opts* o, MixedLayout* out) {
     if (n < 0) return SPDINV_ERR_N;
     if (!o || o->precision != SPDINV_PREC_MIXED_FP32) return SPDINV_ERR_UNSUPPORTED;
+    if (o->variant != 0) return SPDINV_ERR_UNSUPPORTED;  // the execution variants are FP64 only
     const int b = o->tile > 0 ? o->tile : 64;
     if (b != 32 && b != 64) return SPDINV_ERR_UNSUPPORTED;
     if (o->refine_steps < 0 || o->refine_steps > 16) return SPDINV_ERR_UNSUPPORTED;
@@ -473,15 +472,18 @@ spdinv_status run_mixed(int64_t n, double* dA, int64_t lda, const spdinv_opts* o
     double* X1 = steps > 0 ? reinterpret_cast<double*>(reinterpret_cast<char*>(X0) + 2 * nn) : nullptr;
     void* ozws = oz ? static_cast<void*>(reinterpret_cast<char*>(X0) + 3 * nn) : nullptr;
     p.X = X0;
-    p.timeout_ns = (long long)((o->wait_timeout_s > 0 ? o->wait_timeout_s : 60.0) * 1e9);
+    p.timeout_ns = (long long)(wait_timeout_s(o) * 1e9);
     p.drop_task = (o->wait_timeout_s > 0 && o->fault_drop_task >= 0) ? o->fault_drop_task : -1;
     e = ds.exec_plan(t, STEPS_ALL, &p.tasks, &p.ntasks);
     if (e != cudaSuccess) return cuda_fail(e);
     e = cudaMemsetAsync(p.ctrl, 0, ctrl_bytes, stream);
     if (e != cudaSuccess) return cuda_fail(e);
+    void* tok = nullptr;
+    timing_begin(SPDINV_TIMED_MIXED_DAG, stream, &tok);
     e = b == 64 ? launch_mixed_dag<64>(p, o->ctas_per_sm, ds.num_sms, stream)
                 : launch_mixed_dag<32>(p, o->ctas_per_sm, ds.num_sms, stream);
     if (e != cudaSuccess) return cuda_fail(e);
+    timing_end(SPDINV_TIMED_MIXED_DAG, stream, tok, (double)n * (double)n * (double)n);
     int launches = 1;
     const int rt = (int)((n + RB - 1) / RB);
     const int rsm = 2 * RB * RB * (int)sizeof(double);

@@ -10,6 +10,7 @@
 // sequential loop order, which is also a topological order of the tile tasks,
 // straight into the array.  Each tile's update chain runs in the same order
 // either way, so results match spdinv_potri with tile 32.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -57,25 +58,64 @@ __global__ void write_sequential_plan(uint32_t* tasks, int t) {
 
 constexpr int kMaxDevices = 64;
 std::mutex g_setup_mu;
-void* g_scratch_addr[kMaxDevices];  // device address of the array, per device
-int g_num_sms[kMaxDevices];
+struct Setup {
+    void* addr = nullptr;          // device address of the array in that context
+    unsigned long long ctx = 0;    // the context it was looked up in (0 = none)
+    int num_sms = 0;
+};
+Setup g_setup[kMaxDevices];
 
-// Once per device, with that device current: look up the array's address.
+// Unique id of the calling thread's current CUDA context, or 0 when none is
+// current or the driver does not provide the query.  A device reset destroys
+// the context, and the module -- with the array -- is loaded again at a new
+// address in the next one; keying the cached address on the context makes a
+// call after a reset look it up again instead of using a stale address.
+unsigned long long current_context_id() {
+    using GetCurrent = CUresult (*)(CUcontext*);
+    using GetId = CUresult (*)(CUcontext, unsigned long long*);
+    static std::once_flag once;
+    static GetCurrent get_current = nullptr;
+    static GetId get_id = nullptr;
+    std::call_once(once, [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPoint("cuCtxGetCurrent", &f, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<GetCurrent>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPoint("cuCtxGetId", &f, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<GetId>(f);
+    });
+    if (!get_current || !get_id) return 0;
+    CUcontext c = nullptr;
+    unsigned long long id = 0;
+    if (get_current(&c) != CUDA_SUCCESS || c == nullptr) return 0;
+    if (get_id(c, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
+
+// Set-up, once per device (and again in a new context after a device reset),
+// with that device current: look up the array's device address.  Without a
+// context id the address is looked up on every call.
 cudaError_t scratch_for(int dev, void** addr, int* num_sms) {
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lk(g_setup_mu);
-    if (g_scratch_addr[dev] == nullptr) {
+    Setup& su = g_setup[dev];
+    const unsigned long long ctx = current_context_id();
+    if (su.addr == nullptr || ctx == 0 || ctx != su.ctx) {
         void* p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess) return e;
         int sms = 0;
         e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (e != cudaSuccess) return e;
-        g_scratch_addr[dev] = p;
-        g_num_sms[dev] = sms;
+        su.addr = p;
+        su.num_sms = sms;
+        su.ctx = current_context_id();  // the lookup has made the device's context current
     }
-    *addr = g_scratch_addr[dev];
-    *num_sms = g_num_sms[dev];
+    *addr = su.addr;
+    *num_sms = su.num_sms;
     return cudaSuccess;
 }
 
@@ -124,7 +164,7 @@ static spdinv_status potri_noalloc_impl(int64_t n, double* dA, int64_t lda, int*
     p.Bw = reinterpret_cast<double*>(base + kCtrlBytes + kTaskBytes);
     p.Cw = p.Bw + ntri * (kTileBytes / sizeof(double));
     p.Dw = p.Cw + ntri * (kTileBytes / sizeof(double));
-    p.timeout_ns = 60LL * 1000000000LL;
+    p.timeout_ns = (long long)(wait_timeout_s(nullptr) * 1e9);  // the same limit as spdinv_potri's
     p.drop_task = -1;
 
     // The array keeps the previous call's contents: the status words and the

@@ -375,7 +375,8 @@ cudaError_t ozaki_residual(int64_t n, const double* A, int64_t lda, const double
         }
     p.npairs = np;
     if (tc) {
-        err = ozaki_products_tc(n, npad, Asl, S, Xsl, S, p.ps, p.pt, np, e, f, R, nullptr, true, -1.0, false, errw, s);
+        err = ozaki_products_tc(n, npad, Asl, S, Xsl, S, p.ps, p.pt, np, e, f, R, nullptr, true, -1.0, false, errw,
+                                f + npad, s);
         if (launches) *launches += 7;
         return err;
     }
@@ -445,6 +446,7 @@ struct RefineWs {
     __nv_bfloat16 *Asl, *Xsl, *Rsl, *Ysl;
     unsigned long long* mx;
     int *eA, *eX, *fR, *eY;
+    int* sync;  // the slice GEMM's wave barrier
 };
 
 RefineWs refine_layout(int64_t n, void* ws) {
@@ -460,6 +462,7 @@ RefineWs refine_layout(int64_t n, void* ws) {
     w.eX = w.eA + npad;
     w.fR = w.eX + npad;
     w.eY = w.fR + npad;
+    w.sync = w.eY + npad;  // in the workspace's 1024-byte tail
     return w;
 }
 
@@ -488,7 +491,7 @@ cudaError_t ozaki_refine_step(int64_t n, const double* A, int64_t lda, double* X
     int ps[64], pt[64];
     int np = level_pairs(kResSlices, kResSlices, levelsR, ps, pt);
     err = ozaki_products_tc(n, npad, w.Asl, kResSlices, w.Xsl, kResSlices, ps, pt, np, w.eA, w.eX, R, nullptr, true,
-                            -1.0, false, errw, s);  // R = I - A X, every tile
+                            -1.0, false, errw, w.sync, s);  // R = I - A X, every tile
     if (err != cudaSuccess) return err;
     err = slice_columns(n, npad, R, kRSlices, w.Rsl, w.mx, w.fR, s, launches);
     if (err != cudaSuccess) return err;
@@ -501,7 +504,7 @@ cudaError_t ozaki_refine_step(int64_t n, const double* A, int64_t lda, double* X
         const int L = kChainLevels[m - 1];
         np = level_pairs(L + 1, kRSlices, L, ps, pt);
         err = ozaki_products_tc(n, npad, left, left_slices, w.Rsl, kRSlices, ps, pt, np, eleft, w.fR, Y, nullptr,
-                                false, 1.0, true, errw, s);
+                                false, 1.0, true, errw, w.sync, s);
         if (err != cudaSuccess) return err;
         *launches += 1;
         if (m + 1 < order) {

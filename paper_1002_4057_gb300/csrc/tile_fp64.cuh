@@ -1,8 +1,12 @@
 // FP64 tile kernels (device functions) for b x b tiles held column-major in
-// shared memory, run by one CTA of 128 threads (4 warps in a 2 x 2 grid, each
-// warp owning a (b/2) x (b/2) block of the output).  The products use the
-// FP64 tensor-core MMA (m8n8k4); the diagonal-tile factorisation (POTRF) and
-// inversion (TRTRI) are column sweeps in shared memory.
+// shared memory, run by one CTA of 128 threads arranged 8 x 16, each thread
+// owning a (b/8) x (b/16) block of the output.  The products are FP64 fused
+// multiply-adds on register blocks: on GB300 the FP64 FMA pipe measures
+// 1.255 TFLOP/s against 1.10 for the FP64 tensor-core MMA (mma.sync m8n8k4),
+// and at about two FP64 FMAs per clock per SM the pipe, not instruction
+// issue or shared memory, bounds the product.  The diagonal-tile
+// factorisation (POTRF) and inversion (TRTRI) are column sweeps in shared
+// memory.
 //
 // The tile operations are the BLAS/LAPACK kernels of Algorithm 1 (Sec. 2):
 //   GEMM / SYRK / TRMM  -> tile_mma with the operands' transposes and
@@ -19,100 +23,103 @@ constexpr int kThreads = 128;
 
 template <int B>
 struct TileCfg {
-    static constexpr int W = B / 2;   // warp block edge
-    static constexpr int MI = W / 8;  // 8x8 MMA blocks per warp, rows
-    static constexpr int NI = W / 8;  // ... columns
+    static_assert(B % 16 == 0, "tiles of 16, 32 or 64");
+    static constexpr int RM = B / 8;   // rows per thread (8 thread rows)
+    static constexpr int CN = B / 16;  // columns per thread (16 thread columns)
 };
 
 template <int B>
 struct Acc {
-    double v[TileCfg<B>::MI][TileCfg<B>::NI][2];
+    double v[TileCfg<B>::RM][TileCfg<B>::CN];
 };
 
 template <int B>
 __device__ __forceinline__ void acc_zero(Acc<B>& a) {
 #pragma unroll
-    for (int mi = 0; mi < TileCfg<B>::MI; ++mi)
+    for (int i = 0; i < TileCfg<B>::RM; ++i)
 #pragma unroll
-        for (int ni = 0; ni < TileCfg<B>::NI; ++ni) a.v[mi][ni][0] = a.v[mi][ni][1] = 0.0;
+        for (int j = 0; j < TileCfg<B>::CN; ++j) a.v[i][j] = 0.0;
 }
 
-// Element (row, col) of the accumulator entry (mi, ni, h) of this thread.
+// Element (row, col) of the accumulator entry (i, j) of this thread.
 template <int B>
-__device__ __forceinline__ void acc_coord(int mi, int ni, int h, int& row, int& col) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    row = (warp >> 1) * TileCfg<B>::W + mi * 8 + (lane >> 2);
-    col = (warp & 1) * TileCfg<B>::W + ni * 8 + 2 * (lane & 3) + h;
+__device__ __forceinline__ void acc_coord(int i, int j, int& row, int& col) {
+    row = (threadIdx.x % 8) * TileCfg<B>::RM + i;
+    col = (threadIdx.x / 8) * TileCfg<B>::CN + j;
 }
 
 template <int B>
 __device__ __forceinline__ void acc_store(const Acc<B>& a, double* T) {
 #pragma unroll
-    for (int mi = 0; mi < TileCfg<B>::MI; ++mi)
+    for (int i = 0; i < TileCfg<B>::RM; ++i)
 #pragma unroll
-        for (int ni = 0; ni < TileCfg<B>::NI; ++ni)
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                int r, c;
-                acc_coord<B>(mi, ni, h, r, c);
-                T[c * B + r] = a.v[mi][ni][h];
-            }
+        for (int j = 0; j < TileCfg<B>::CN; ++j) {
+            int r, c;
+            acc_coord<B>(i, j, r, c);
+            T[c * B + r] = a.v[i][j];
+        }
 }
 
 template <int B>
 __device__ __forceinline__ void acc_load(Acc<B>& a, const double* T) {
 #pragma unroll
-    for (int mi = 0; mi < TileCfg<B>::MI; ++mi)
+    for (int i = 0; i < TileCfg<B>::RM; ++i)
 #pragma unroll
-        for (int ni = 0; ni < TileCfg<B>::NI; ++ni)
+        for (int j = 0; j < TileCfg<B>::CN; ++j) {
+            int r, c;
+            acc_coord<B>(i, j, r, c);
+            a.v[i][j] = T[c * B + r];
+        }
+}
+
+// acc += T (a b x b column-major tile in shared memory), element by element.
+template <int B>
+__device__ __forceinline__ void acc_add(Acc<B>& a, const double* T) {
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                int r, c;
-                acc_coord<B>(mi, ni, h, r, c);
-                a.v[mi][ni][h] = T[c * B + r];
-            }
+    for (int i = 0; i < TileCfg<B>::RM; ++i)
+#pragma unroll
+        for (int j = 0; j < TileCfg<B>::CN; ++j) {
+            int r, c;
+            acc_coord<B>(i, j, r, c);
+            a.v[i][j] += T[c * B + r];
+        }
 }
 
 // Shape of a stored operand.
 enum TriShape { FULL = 0, LOWER = 1 };
 
 // acc (+|-)= op(P) * op(Q) for b x b column-major tiles P, Q in shared memory,
-// op(X) = X (TA/TB false) or X^T (true).  When a stored operand is lower
-// triangular, each warp skips the k-range that multiplies its zero part.
+// op(X) = X (TA/TB false) or X^T (true), one FP64 FMA per product term in
+// increasing k.  When a stored operand is lower triangular (its upper part
+// exactly zero), each thread skips the k-range that multiplies zeros of its
+// own rows or columns.
 template <int B, bool TA, bool TB, bool NEG, int SP, int SQ>
 __device__ __forceinline__ void tile_mma(Acc<B>& acc, const double* P, const double* Q) {
-    constexpr int W = TileCfg<B>::W, MI = TileCfg<B>::MI, NI = TileCfg<B>::NI;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int g = lane >> 2, q = lane & 3;
-    const int wm = (warp >> 1) * W, wn = (warp & 1) * W;
+    constexpr int RM = TileCfg<B>::RM, CN = TileCfg<B>::CN;
+    const int r0 = (threadIdx.x % 8) * RM, c0 = (threadIdx.x / 8) * CN;
     int kb = 0, ke = B;
     // op(P)[m][k] != 0 only for k <= m (P lower, N) or k >= m (P lower, T)
     if (SP == LOWER) {
-        if (TA) kb = wm; else ke = wm + W;
+        if (TA) kb = r0; else ke = r0 + RM;
     }
     // op(Q)[k][n] != 0 only for k >= n (Q lower, N) or k <= n (Q lower, T)
     if (SQ == LOWER) {
-        if (TB) ke = min(ke, wn + W); else kb = max(kb, wn);
+        if (TB) ke = min(ke, c0 + CN); else kb = max(kb, c0);
     }
-#pragma unroll 2
-    for (int k0 = kb; k0 < ke; k0 += 4) {
-        const int k = k0 + q;
-        double a[MI], b[NI];
+#pragma unroll 4
+    for (int k = kb; k < ke; ++k) {
+        double a[RM], b[CN];
 #pragma unroll
-        for (int mi = 0; mi < MI; ++mi) {
-            const int m = wm + mi * 8 + g;
-            const double v = TA ? P[m * B + k] : P[k * B + m];
-            a[mi] = NEG ? -v : v;
+        for (int i = 0; i < RM; ++i) {
+            const double v = TA ? P[(r0 + i) * B + k] : P[k * B + r0 + i];
+            a[i] = NEG ? -v : v;
         }
 #pragma unroll
-        for (int ni = 0; ni < NI; ++ni) {
-            const int n = wn + ni * 8 + g;
-            b[ni] = TB ? Q[k * B + n] : Q[n * B + k];
-        }
+        for (int j = 0; j < CN; ++j) b[j] = TB ? Q[k * B + c0 + j] : Q[(c0 + j) * B + k];
 #pragma unroll
-        for (int mi = 0; mi < MI; ++mi)
+        for (int i = 0; i < RM; ++i)
 #pragma unroll
-            for (int ni = 0; ni < NI; ++ni) dmma_m8n8k4(acc.v[mi][ni][0], acc.v[mi][ni][1], a[mi], b[ni]);
+            for (int j = 0; j < CN; ++j) acc.v[i][j] = fma(a[i], b[j], acc.v[i][j]);
     }
 }
 

@@ -124,3 +124,56 @@ def test_argument_errors():
     assert L.spdinv_plan_emulate(4, 4, 0, wait_limit_s=0.0)[0] == L.SPDINV_ERR_UNSUPPORTED
     assert L.spdinv_plan_emulate(4, 4, 0, steps=5)[0] == L.SPDINV_ERR_UNSUPPORTED
     assert L.spdinv_plan_emulate(4, 4, 0, steps=-1)[0] == L.SPDINV_ERR_UNSUPPORTED
+
+
+# ---- execution variants (the study of Sec. 3 on the GPU) -------------------
+UUU, SHARE, INPLACE, SPLIT = (L.SPDINV_VARIANT_UUU, L.SPDINV_VARIANT_SHARE_BC, L.SPDINV_VARIANT_INPLACE,
+                              L.SPDINV_VARIANT_SPLIT3)
+VARIANTS = [(UUU, 0), (SHARE, 0), (INPLACE, 0), (UUU | SHARE, 0), (UUU | INPLACE, 0), (SPLIT, 1), (SPLIT, 2),
+            (SPLIT, 5), (SPLIT | UUU, 3)]
+
+
+def _variant_tasks(t, var, seg):
+    n = _tasks(t)
+    if var & SPLIT:  # one task per extra segment of each Step-3 chain longer than seg
+        for i in range(t):
+            m = t - 1 - i
+            if m > seg:
+                n += (i + 1) * (-(-m // seg) - 1)
+    return n
+
+
+@pytest.mark.parametrize("var,seg", VARIANTS)
+@pytest.mark.parametrize("t", [1, 2, 3, 6, 11, 24])
+@pytest.mark.parametrize("workers", [1, 3, 16, 96])
+def test_variant_plans_complete_without_hazards(var, seg, t, workers):
+    """With C in B's slots or a single store, a version of a tile is stored
+    only after every read of the previous one: the emulator records each
+    tile's writer and counts each read, so a read of an overwritten tile is a
+    hazard and a read count that differs from the one the writers wait for is
+    a protocol error.  One worker never waits, which shows the ticket order
+    is topological over the write-after-read edges too."""
+    for seed in range(2):
+        st, (done, total, errors, hazards, longest) = L.spdinv_plan_emulate_variant(
+            t, var, workers, seed, split_segment=seg, max_delay_us=8)
+        assert st == L.SPDINV_OK, (var, seg, t, workers, seed)
+        assert done == total == _variant_tasks(t, var, seg)
+        assert errors == 0 and hazards == 0
+        if workers == 1:
+            assert longest == 0
+
+
+@pytest.mark.parametrize("var", [SHARE, INPLACE])
+def test_variant_dropped_producer_times_out(var):
+    """A task that never publishes (the kernel's fault hook) ends every worker
+    with a timeout, also where writers wait on read counts."""
+    st, (done, total, _, _, _) = L.spdinv_plan_emulate_variant(8, var, 8, 1, drop_task=3, wait_limit_s=0.3,
+                                                                max_delay_us=2)
+    assert st == L.SPDINV_ERR_TIMEOUT and done < total
+
+
+def test_variant_rejects_unsupported_combinations():
+    out = L.spdinv_plan_emulate_variant(5, SPLIT | SHARE, 2, 0, split_segment=2)
+    assert out[0] == L.SPDINV_ERR_UNSUPPORTED
+    assert L.spdinv_plan_emulate_variant(5, SPLIT | INPLACE, 2, 0, split_segment=2)[0] == L.SPDINV_ERR_UNSUPPORTED
+    assert L.spdinv_plan_emulate_variant(5, 64, 2, 0)[0] == L.SPDINV_ERR_UNSUPPORTED

@@ -1,11 +1,12 @@
 """spdinv_potri_noalloc: the inversion for callers that cannot allocate
-device memory (graph capture in progress, a host application that owns all
-device memory, loops where an allocation's device-wide synchronisation would
-stall other streams).  Its scratch is a fixed array inside the library.
+device memory (a host application that owns all device memory, loops where
+an allocation's device-wide synchronisation would stall other streams).  Its
+scratch is a fixed array inside the library.
 
 It is checked through the C-ABI against spdinv_potri (tile 32) on two calls
 in a row, within the FP64 parity tolerance of the other tests (relative
-Frobenius error 1e-10).  The second call reuses the array the first one left
+Frobenius error 1e-10); each tile's update chain runs in the same order on
+both paths, so the two results are also equal bit for bit.  The second call reuses the array the first one left
 behind, and must neither allocate device memory nor see stale state.
 This file is collected last, so a failure here stops a -x run only after
 every other test has run."""
@@ -46,7 +47,9 @@ def test_noalloc_matches_potri_on_two_calls_in_a_row(gpu):
         if call > 0:  # after the one-time set-up, a call allocates nothing
             assert torch.cuda.mem_get_info(gpu)[0] == free_before
         assert int(info.item()) == 0
-        assert _rel(full_from_lower(lower_np(dA)), ref_full) <= 1e-10
+        got = full_from_lower(lower_np(dA))
+        assert _rel(got, ref_full) <= 1e-10
+        assert np.array_equal(got, ref_full)
 
 
 def test_noalloc_rejects_sizes_beyond_its_maximum(gpu):
