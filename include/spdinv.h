@@ -85,9 +85,14 @@ typedef enum {
 /* Precision of the bulk tile updates (GEMM/SYRK/TRMM). */
 typedef enum {
     SPDINV_PREC_FP64 = 0,         /* every operation in native FP64 (DMMA tensor cores) */
-    SPDINV_PREC_MIXED_FP32 = 1,   /* bulk updates FP32; diagonal POTRF/TRTRI and the residual FP64 */
-    SPDINV_PREC_MIXED_BF16X3 = 2  /* reserved: bulk updates as three BF16 products (returns
-                                     SPDINV_ERR_UNSUPPORTED in this version) */
+    SPDINV_PREC_MIXED_FP32 = 1,   /* bulk updates FP32 (FMA on the CUDA cores); diagonal POTRF/TRTRI
+                                     and the residual FP64 */
+    SPDINV_PREC_MIXED_BF16X3 = 2, /* as MIXED_FP32, the bulk updates on the BF16 tensor cores as three
+                                     products of two-term BF16 splits (hi hi + hi lo + lo hi, FP32
+                                     accumulation): about 2^-16 relative per product */
+    SPDINV_PREC_MIXED_TF32X3 = 3  /* as MIXED_FP32, the bulk updates on the TF32 tensor cores as three
+                                     products of two-term TF32 splits (3xTF32, FP32 accumulation):
+                                     about 2^-21 relative per product, near FP32 */
 } spdinv_precision;
 
 /* Options for spdinv_potri_ex.  Zero-initialise and set what you need. */

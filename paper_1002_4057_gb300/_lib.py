@@ -28,6 +28,7 @@ SPDINV_ERR_WORKSPACE = -7
 SPDINV_PREC_FP64 = 0
 SPDINV_PREC_MIXED_FP32 = 1
 SPDINV_PREC_MIXED_BF16X3 = 2
+SPDINV_PREC_MIXED_TF32X3 = 3
 
 SPDINV_NOALLOC_MAX_N = 1024
 

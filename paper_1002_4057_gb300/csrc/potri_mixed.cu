@@ -29,6 +29,7 @@
 #include "ozaki.h"
 #include "persist.cuh"
 #include "tile_f32.cuh"
+#include "tile_tc32.cuh"
 #include "tile_fp64.cuh"
 
 namespace spdinv {
@@ -119,7 +120,10 @@ __device__ void store_X(const KParamsMixed& p, int ti, int tj, const float* T) {
     }
 }
 
-template <int B>
+// ACC: the bulk tile products' accumulator, which selects their arithmetic --
+// Acc32<B> FP32 FMA on the CUDA cores, AccTC<B, SplitTF32> three TF32 MMAs
+// (3xTF32), AccTC<B, SplitBF16> three BF16 MMAs (BF16x3).
+template <int B, class ACC>
 __global__ void __launch_bounds__(kThreads) potri_mixed_persistent(const KParamsMixed prm) {
     unsigned char* const smem_raw = dynamic_smem();
     __shared__ __align__(8) uint64_t bar;
@@ -156,7 +160,7 @@ __global__ void __launch_bounds__(kThreads) potri_mixed_persistent(const KParams
         if (ticket < 0) return;
         const uint32_t e = p.tasks[ticket];
         const int kind = (int)task_kind(e), i = (int)task_i(e), j = (int)task_j(e);
-        Acc32<B> acc;
+        ACC acc;
 
         if (kind == K_S1_DIAG) {
             load_A32<B>(p, j, j, T0, true);
@@ -352,9 +356,9 @@ int mixed_smem() {
     return 2 * round_up128(padded_tile<B>() * (int)sizeof(float)) + (B * B + kThreads) * (int)sizeof(double);
 }
 
-template <int B>
+template <int B, class ACC>
 cudaError_t launch_mixed_dag(const KParamsMixed& p, int ctas_per_sm, int num_sms, cudaStream_t s) {
-    auto kern = potri_mixed_persistent<B>;
+    auto kern = potri_mixed_persistent<B, ACC>;
     const int sm = mixed_smem<B>();
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     if (e != cudaSuccess) return e;
@@ -380,7 +384,9 @@ constexpr int kSlices = 7, kLevels = 6, kLevelsLast = 7;
 
 spdinv_status mixed_layout(int64_t n, const spdinv_opts* o, MixedLayout* out) {
     if (n < 0) return SPDINV_ERR_N;
-    if (!o || o->precision != SPDINV_PREC_MIXED_FP32) return SPDINV_ERR_UNSUPPORTED;
+    if (!o || (o->precision != SPDINV_PREC_MIXED_FP32 && o->precision != SPDINV_PREC_MIXED_BF16X3 &&
+               o->precision != SPDINV_PREC_MIXED_TF32X3))
+        return SPDINV_ERR_UNSUPPORTED;
     if (o->variant != 0) return SPDINV_ERR_UNSUPPORTED;  // the execution variants are FP64 only
     const int b = o->tile > 0 ? o->tile : 64;
     if (b != 32 && b != 64) return SPDINV_ERR_UNSUPPORTED;
@@ -480,8 +486,19 @@ spdinv_status run_mixed(int64_t n, double* dA, int64_t lda, const spdinv_opts* o
     if (e != cudaSuccess) return cuda_fail(e);
     void* tok = nullptr;
     timing_begin(SPDINV_TIMED_MIXED_DAG, stream, &tok);
-    e = b == 64 ? launch_mixed_dag<64>(p, o->ctas_per_sm, ds.num_sms, stream)
-                : launch_mixed_dag<32>(p, o->ctas_per_sm, ds.num_sms, stream);
+    switch (o->precision) {
+        case SPDINV_PREC_MIXED_TF32X3:
+            e = b == 64 ? launch_mixed_dag<64, AccTC<64, SplitTF32>>(p, o->ctas_per_sm, ds.num_sms, stream)
+                        : launch_mixed_dag<32, AccTC<32, SplitTF32>>(p, o->ctas_per_sm, ds.num_sms, stream);
+            break;
+        case SPDINV_PREC_MIXED_BF16X3:
+            e = b == 64 ? launch_mixed_dag<64, AccTC<64, SplitBF16>>(p, o->ctas_per_sm, ds.num_sms, stream)
+                        : launch_mixed_dag<32, AccTC<32, SplitBF16>>(p, o->ctas_per_sm, ds.num_sms, stream);
+            break;
+        default:
+            e = b == 64 ? launch_mixed_dag<64, Acc32<64>>(p, o->ctas_per_sm, ds.num_sms, stream)
+                        : launch_mixed_dag<32, Acc32<32>>(p, o->ctas_per_sm, ds.num_sms, stream);
+    }
     if (e != cudaSuccess) return cuda_fail(e);
     timing_end(SPDINV_TIMED_MIXED_DAG, stream, tok, (double)n * (double)n * (double)n);
     int launches = 1;

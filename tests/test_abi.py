@@ -92,7 +92,7 @@ def test_potri_ex_option_errors(lib):
         L.spdinv_opts(64, 0, mixed, -1, 0.0, -1, 0, 0),
         L.spdinv_opts(64, 0, mixed, 1, 0.0, -1, 5, 0),   # residual path
         L.spdinv_opts(64, 0, mixed, 1, 0.0, -1, -1, 0),
-        L.spdinv_opts(64, 0, 2, 1, 0.0, -1, 0, 0),       # reserved precision
+        L.spdinv_opts(64, 0, 4, 1, 0.0, -1, 0, 0),       # unknown precision
         L.spdinv_opts(64, 0, 7, 1, 0.0, -1, 0, 0),
     ]
     for o in bad:
@@ -236,7 +236,9 @@ def test_workspace_size_errors(lib):
     assert f(10, 6)[0] == L.SPDINV_ERR_UNSUPPORTED
     assert f(10, -1)[0] == L.SPDINV_ERR_UNSUPPORTED
     assert f(10, 0, L.spdinv_opts(48, 0, 0, 0, 0.0, -1, 0, 0))[0] == L.SPDINV_ERR_UNSUPPORTED
-    assert f(10, 0, L.spdinv_opts(0, 0, 2, 0, 0.0, -1, 0, 0))[0] == L.SPDINV_ERR_UNSUPPORTED  # reserved BF16x3
+    assert f(10, 0, L.spdinv_opts(0, 0, 4, 0, 0.0, -1, 0, 0))[0] == L.SPDINV_ERR_UNSUPPORTED  # unknown precision
+    assert f(10, 0, L.spdinv_opts(0, 0, 2, 0, 0.0, -1, 0, 0))[0] == L.SPDINV_OK  # BF16x3
+    assert f(10, 0, L.spdinv_opts(0, 0, 3, 0, 0.0, -1, 0, 0))[0] == L.SPDINV_OK  # 3xTF32
     assert f(10, 0, L.spdinv_opts(0, 0, 1, 1, 0.0, -1, 0, 9))[0] == L.SPDINV_ERR_UNSUPPORTED  # order 9
     assert f(10, 5, L.spdinv_opts(0, 0, 0, 0, 0.0, -1, 7, 0))[0] == L.SPDINV_ERR_UNSUPPORTED  # residual path
     assert f(32 * 16384, 0, L.spdinv_opts(32, 0, 0, 0, 0.0, -1, 0, 0))[0] == L.SPDINV_ERR_N

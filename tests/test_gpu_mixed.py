@@ -213,3 +213,84 @@ def test_torch_wrappers_of_residual_and_noalloc(gpu):
     assert int(T.potri_noalloc_(dA).item()) == 0
     M, _ = oracle.potri(A)
     assert oracle.rel_frobenius(full_from_lower(lower_np(dA)), oracle.symmetrize_lower(M)) <= 1e-10
+
+
+# ---- the bulk updates on the tensor cores: 3xTF32 and BF16x3 splits --------
+TF32X3, BF16X3 = 3, 2
+
+
+def _run_prec(T, A, gpu, prec, steps, order=0, tile=64):
+    dA = to_dev(A, gpu)
+    info = T.potri_(dA, precision=prec, refine_steps=steps, tile=tile, refine_order=order)
+    import torch
+    torch.cuda.synchronize()
+    return dA, int(info.item())
+
+
+@pytest.mark.parametrize("tile", [32, 64])
+@pytest.mark.parametrize("n", [1, 100, 513, 1000])
+def test_tf32x3_matches_fp32_accuracy_and_refines(gpu, n, tile):
+    """3xTF32 products keep about 21 of FP32's 24 bits per product: the
+    unrefined result stays within a small factor of the FP32 one (both
+    against the oracle), and one order-4 correction reaches 1e-10 at cond
+    1e4, as with FP32 updates."""
+    from paper_1002_4057_gb300 import torch_api as T
+    A, _, _ = si.spectral_spd(n, 1e4, seed=si.SEED_BASE + 11 + n)
+    M, _ = oracle.potri(A)
+    ref = oracle.symmetrize_lower(M)
+    d32, i32 = _run_prec(T, A, gpu, MIXED, 0, tile=tile)
+    dtc, itc = _run_prec(T, A, gpu, TF32X3, 0, tile=tile)
+    assert i32 == 0 and itc == 0
+    e32 = oracle.rel_frobenius(full_from_lower(lower_np(d32)), ref)
+    etc = oracle.rel_frobenius(full_from_lower(lower_np(dtc)), ref)
+    print("n=%d tile=%d cond 1e4 unrefined: FP32 %.2e, 3xTF32 %.2e" % (n, tile, e32, etc))
+    assert etc <= max(16 * e32, 1e-12) and etc <= 1e-2
+    dA, info = _run_prec(T, A, gpu, TF32X3, 1, order=4, tile=tile)
+    assert info == 0
+    e = oracle.rel_frobenius(full_from_lower(lower_np(dA)), ref)
+    print("  3xTF32 + one order-4 step: %.2e" % e)
+    assert e <= 1e-10
+
+
+@pytest.mark.parametrize("n", [1, 100, 513, 1000])
+def test_bf16x3_error_and_refinement(gpu, n):
+    """BF16x3 keeps about 16 bits per product: the unrefined result's error is
+    larger (stated), and at cond 1e2 two corrections of order 3 reach 1e-10."""
+    from paper_1002_4057_gb300 import torch_api as T
+    A, _, _ = si.spectral_spd(n, 1e2, seed=si.SEED_BASE + 13 + n)
+    M, _ = oracle.potri(A)
+    ref = oracle.symmetrize_lower(M)
+    d0, i0 = _run_prec(T, A, gpu, BF16X3, 0)
+    assert i0 == 0
+    e0 = oracle.rel_frobenius(full_from_lower(lower_np(d0)), ref)
+    dA, info = _run_prec(T, A, gpu, BF16X3, 2, order=3)
+    assert info == 0
+    e2 = oracle.rel_frobenius(full_from_lower(lower_np(dA)), ref)
+    print("n=%d cond 1e2: BF16x3 unrefined %.2e, two order-3 steps %.2e" % (n, e0, e2))
+    assert e0 <= 5e-2
+    assert e2 <= 1e-10
+
+
+@pytest.mark.parametrize("prec", [TF32X3, BF16X3])
+def test_split_precisions_exact_on_integer_case(gpu, prec):
+    """Entries of the integer test matrix are small integers: their high
+    parts are exact and the low parts zero, so every product is exact and the
+    result bitwise."""
+    from paper_1002_4057_gb300 import torch_api as T
+    n = 700
+    A, s = si.bidiag_integer_spd(n, seed=3)
+    for steps, order in ((0, 0), (1, 4)):
+        dA, info = _run_prec(T, A, gpu, prec, steps, order=order)
+        assert info == 0
+        assert np.array_equal(lower_np(dA), np.tril(cf.bidiag_inverse(s)))
+
+
+@pytest.mark.parametrize("prec", [TF32X3, BF16X3])
+def test_split_precisions_report_the_failing_column(gpu, prec):
+    from paper_1002_4057_gb300 import torch_api as T
+    n = 300
+    A, _, _ = si.spectral_spd(n, 1e2, seed=5)
+    A[150, 150] = -1.0
+    _, oinfo = oracle.potri(A)
+    _, info = _run_prec(T, A, gpu, prec, 1)
+    assert oinfo > 0 and info == oinfo
