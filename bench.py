@@ -30,6 +30,10 @@ sys.path.insert(0, ROOT)
 METRIC = "POTRI Gflop/s (n^3/inv) & % tensor peak; mixed vs FP64 speedup at 1e-10 err"
 TRAFFIC_N16384_B32 = 793344264192 + 3259657472  # DRAM bytes read + written, one launch (ncu)
 BF16_NOMINAL_TFLOPS = 2250.0
+# precision of the mixed-precision records: SPDINV_PREC_MIXED_TF32X3, the bulk
+# tile updates as 3xTF32 tensor-core products (more accurate than FP32 FMA on
+# the unrefined result at n = 16384, cond 1e4: 2.0e-4 vs 5.7e-4, and 20 ms faster)
+MIXED_PREC = 3
 FP64_NOMINAL_TFLOPS = 1.25
 
 
@@ -55,13 +59,14 @@ def parse():
                          "ncu --profile-from-start off (warm-up, tuning and set-up launches are then not captured)")
     ap.add_argument("--workload", default="fp64",
                     choices=["fp64", "batched64", "batched32", "backward64", "backward32", "mixed", "residual",
-                             "variants", "peaks"],
+                             "variants", "peaks", "trace"],
                     help="fp64 (default, the headline line): one n x n FP64 inversion per step; "
                          "batched*: 4096 matrices per GPU, n ~ U{16..256}, one graph-captured launch per step "
                          "(with N GPUs the 4096 N matrices are split by spdinv_batch_shard); "
                          "backward*: forward + backward of 256 matrices n = 512; "
                          "variants: pipelined vs step-by-step (barriered) execution and the tile size; "
                          "peaks: the FP64 MMA / FMA and FP32 FMA microbenchmarks")
+    ap.add_argument("--trace-out", default="", help="trace workload: write a Chrome trace JSON here")
     ap.add_argument("--no-extra", action="store_true",
                     help="default line without its mixed-precision, batched and backward sub-records")
     return ap.parse_args()
@@ -325,7 +330,7 @@ def mixed_record(n, A_main, Q, lam_main, cond_main, ms64, stream, dev, peaks, re
 
         def run():
             W.copy_(A)
-            T.potri_(W, info=info, tile=64, precision=1, refine_steps=k, refine_order=order)
+            T.potri_(W, info=info, tile=64, precision=MIXED_PREC, refine_steps=k, refine_order=order)
 
         for _ in range(3):
             run()
@@ -339,7 +344,7 @@ def mixed_record(n, A_main, Q, lam_main, cond_main, ms64, stream, dev, peaks, re
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            T.potri_(W, info=info, tile=64, precision=1, refine_steps=k, refine_order=order)
+            T.potri_(W, info=info, tile=64, precision=MIXED_PREC, refine_steps=k, refine_order=order)
             e1.record(stream)
             torch.cuda.synchronize()
             ms.append(e0.elapsed_time(e1))
@@ -369,16 +374,19 @@ def mixed_record(n, A_main, Q, lam_main, cond_main, ms64, stream, dev, peaks, re
                 "frac_of_sustained": round(ach / bf16_sus, 4) if (ach and bf16_sus) else None,
                 "peak_note": "bf16_tflops (%s, burst); the sustained figure is %s" % (src, bf16_sus),
                 "work": "2 * 128 * 128 * K flops per launched output tile and slice pair (K: order padded to 256)"},
-            "fp32_dag": {"kernel": "potri_mixed_persistent<64>", "ms_per_inversion": round(dms / reps, 2),
+            "fp32_dag": {"kernel": "potri_mixed_persistent<64> (bulk updates 3xTF32 on mma.sync)",
+                         "ms_per_inversion": round(dms / reps, 2),
                          "achieved_tflops": round(dag_rate, 3) if dag_rate else None,
-                         "ffma_peak_tflops": ffma,
-                         "frac_of_ffma": round(dag_rate / ffma, 4) if (dag_rate and ffma) else None},
+                         "note": "n^3 per factorisation; the bulk products run as three TF32 mma.sync "
+                                 "products (TF32 mma.sync measures about 304 TFLOP/s on this GPU, so about 101 "
+                                 "FP32-equivalent), the diagonal POTRF/TRTRI in FP64",
+                         "ffma_peak_tflops": ffma},
         })
         del W
         if A is not A_main:
             del A
         torch.cuda.empty_cache()
-    return {"n": n, "tile": 64, "fp64_ms_per_inversion": round(ms64, 2),
+    return {"n": n, "tile": 64, "precision": "SPDINV_PREC_MIXED_TF32X3", "fp64_ms_per_inversion": round(ms64, 2),
             "generator": "A = Q diag(lam) Q^T with this line's Q, lam log-uniform [1, cond]",
             "error": "relative Frobenius error of 3 sampled columns vs Q diag(1/lam) Q^T",
             "records": recs}
@@ -428,7 +436,7 @@ def run_mixed_study(args, dev, stream):
         for k, order in schedules[cond]:
             def mixed():
                 W.copy_(A)
-                T.potri_(W, info=info, tile=64, precision=1, refine_steps=k, refine_order=order)
+                T.potri_(W, info=info, tile=64, precision=MIXED_PREC, refine_steps=k, refine_order=order)
             ms = timed_steps(mixed, 1, 1, stream, mw)
             assert int(info.item()) == 0
             e = err_of(W)
@@ -553,6 +561,108 @@ def run_variants(args, dev, stream):
         print(json.dumps(rec), flush=True)
         del A, W
         torch.cuda.empty_cache()
+
+
+def trace_summary(rec, t):
+    """Per-task trace of one persistent FP64 inversion -> makespan, CTA busy
+    fraction, time per task kind, when each step ran, and the achieved
+    critical path: from the task that finished last, repeatedly the producer
+    (of a tile it read) that finished last, back to a task with none."""
+    import numpy as np
+    kind = rec["task"] >> 28
+    ti = (rec["task"] >> 14) & 0x3FFF
+    tj = rec["task"] & 0x3FFF
+    t0 = rec["t_start_ns"].astype(np.int64)
+    t1 = rec["t_end_ns"].astype(np.int64)
+    base = int(t0.min())
+    t0, t1 = t0 - base, t1 - base
+    makespan = int(t1.max())
+    ctas = len(np.unique(rec["cta"]))
+    names = {0: "s1_diag", 1: "s1_off", 3: "s2_off", 4: "s3_diag", 5: "s3_off", 6: "s3_part"}
+    by_kind = {}
+    for k, nm in names.items():
+        m = kind == k
+        if m.any():
+            d = (t1[m] - t0[m]) / 1e3
+            by_kind[nm] = {"tasks": int(m.sum()), "mean_us": round(float(d.mean()), 2),
+                           "first_start_ms": round(float(t0[m].min()) / 1e6, 3),
+                           "last_end_ms": round(float(t1[m].max()) / 1e6, 3)}
+    index = {}
+    for r in range(len(rec)):
+        if kind[r] != 6:
+            index[(int(kind[r]), int(ti[r]), int(tj[r]))] = r
+
+    def preds(r):
+        k, i, j = int(kind[r]), int(ti[r]), int(tj[r])
+        L = lambda a, b: index.get((1, a, b))  # noqa: E731
+        X = lambda a, b: index.get((3, a, b))  # noqa: E731
+        D = lambda a: index.get((0, a, a))     # noqa: E731
+        if k == 0:
+            out = [L(j, q) for q in range(j)]
+        elif k == 1:
+            out = [L(i, q) for q in range(j)] + [L(j, q) for q in range(j)] + [D(j)]
+        elif k == 3:
+            out = [D(i), L(i, j), D(j)] + [X(i, q) for q in range(j + 1, i)] + [L(q, j) for q in range(j + 1, i)]
+        elif k == 5:
+            out = [D(i), X(i, j)] + [X(q, i) for q in range(i + 1, t)] + [X(q, j) for q in range(i + 1, t)]
+        elif k == 4:
+            out = [D(i)] + [X(q, i) for q in range(i + 1, t)]
+        else:
+            out = []
+        return [p for p in out if p is not None]
+
+    r = int(np.argmax(t1))
+    path = [r]
+    while True:
+        ps = preds(r)
+        if not ps:
+            break
+        r = max(ps, key=lambda q: t1[q])
+        path.append(r)
+    busy = float((t1 - t0).sum())
+    return {"t": t, "tasks": int(len(rec)), "ctas": ctas, "makespan_ms": round(makespan / 1e6, 3),
+            "busy_fraction": round(busy / (ctas * makespan), 4), "by_kind": by_kind,
+            "critical_path_tasks": len(path),
+            "critical_path_work_ms": round(float(sum(t1[q] - t0[q] for q in path)) / 1e6, 3),
+            "critical_path_kinds": {names[k]: int(sum(1 for q in path if kind[q] == k)) for k in names
+                                    if any(kind[q] == k for q in path)}}
+
+
+def run_trace(args, dev, stream):
+    """Per-task trace of the persistent FP64 kernel at n (spdinv_set_trace):
+    the summary of trace_summary for the default plan and, with --plan-order
+    alap, the ALAP order; --trace-out writes the records as a Chrome trace
+    (one row per CTA)."""
+    import torch
+
+    import spd_inputs as si
+    from paper_1002_4057_gb300 import _lib as L
+    from paper_1002_4057_gb300 import torch_api as T
+
+    n, b = args.n, args.tile
+    A0, _, _ = si.spectral_spd(n, args.cond, seed=si.SEED_BASE + 1, device=dev)
+    A = torch.empty_like(A0)
+    for _ in range(2):  # warm up the plan and the kernel
+        A.copy_(A0)
+        T.potri_(A, tile=b, ctas_per_sm=args.ctas_per_sm)
+    A.copy_(A0)
+    info, rec = T.traced_potri_(A, tile=b, ctas_per_sm=args.ctas_per_sm)
+    assert int(info.item()) == 0
+    st, tasks, _ = L.spdinv_plan_tasks(n, b, 0)
+    rec = rec[:len(tasks)]
+    out = {"workload": "trace", "n": n, "tile": b, "ctas_per_sm": args.ctas_per_sm or "default",
+           **trace_summary(rec, (n + b - 1) // b)}
+    print(json.dumps(out), flush=True)
+    if args.trace_out:
+        ev = []
+        base = int(rec["t_start_ns"].min())
+        for r in rec:
+            k = int(r["task"] >> 28)
+            ev.append({"name": "k%d(%d,%d)" % (k, (r["task"] >> 14) & 0x3FFF, r["task"] & 0x3FFF), "ph": "X",
+                       "ts": (int(r["t_start_ns"]) - base) / 1e3, "dur": (int(r["t_end_ns"]) - int(r["t_start_ns"])) / 1e3,
+                       "pid": 0, "tid": int(r["cta"])})
+        with open(args.trace_out, "w") as f:
+            json.dump({"traceEvents": ev}, f)
 
 
 def run_batched_bench(args, rank, world, local):
@@ -720,6 +830,9 @@ def run_secondary(args):
         return
     if args.workload == "variants":
         run_variants(args, dev, stream)
+        return
+    if args.workload == "trace":
+        run_trace(args, dev, stream)
         return
     if args.workload == "peaks":
         print(json.dumps({"workload": "peaks", **measure_peaks(dev, stream)}), flush=True)

@@ -84,7 +84,7 @@ typedef enum {
 
 /* Precision of the bulk tile updates (GEMM/SYRK/TRMM). */
 typedef enum {
-    SPDINV_PREC_FP64 = 0,         /* every operation in native FP64 (DMMA tensor cores) */
+    SPDINV_PREC_FP64 = 0,         /* every operation in native FP64 (FMA on the FP64 pipe) */
     SPDINV_PREC_MIXED_FP32 = 1,   /* bulk updates FP32 (FMA on the CUDA cores); diagonal POTRF/TRTRI
                                      and the residual FP64 */
     SPDINV_PREC_MIXED_BF16X3 = 2, /* as MIXED_FP32, the bulk updates on the BF16 tensor cores as three
@@ -555,6 +555,26 @@ SPDINV_API spdinv_status spdinv_fp64_peak_probe(int kind, int64_t iters, int blo
 #define SPDINV_TIMED_KERNELS 3
 SPDINV_API spdinv_status spdinv_set_kernel_timing(int on);
 SPDINV_API spdinv_status spdinv_kernel_time_ms(int which, double* ms, int* launches, double* flops);
+
+/* Per-task trace of the persistent FP64 kernel (the paper has no
+ * counterpart).  While a trace buffer is set for the current
+ * device, every FP64 single-matrix call (spdinv_potrf, _trtri, _lauum,
+ * _potri, _potri_ex, _potri_diag) runs the kernel's tracing build and writes
+ * one record per task, at index = its ticket (the position in the plan's
+ * order): the task word (kind << 28 | i << 14 | j; kind 6 = a split-chain
+ * segment with its id in the low 28 bits), the SM and CTA that ran it, and
+ * the global timer (ns) when the CTA took it and when it finished it.  The
+ * tracing build is the variant build of the kernel: a traced run measures
+ * that build, within a few percent of the default one.
+ * spdinv_set_trace(d_records, capacity): device array of `capacity` records
+ * (NULL = off).  A call whose plan has more tasks than `capacity` returns
+ * SPDINV_ERR_WORKSPACE and launches nothing.  The caller owns the buffer;
+ * records of tasks that did not run (after an error) are left as they were. */
+typedef struct {
+    uint32_t task, sm, ticket, cta;
+    uint64_t t_start_ns, t_end_ns;
+} spdinv_trace_record;
+SPDINV_API spdinv_status spdinv_set_trace(spdinv_trace_record* d_records, int64_t capacity);
 
 /* ------------------------------------------------------------------------
  * Library information

@@ -113,6 +113,7 @@ SIGNATURES = {
     "spdinv_set_debug_flags": (ctypes.c_uint, [ctypes.c_uint]),
     "spdinv_fp64_peak_probe": (c_int, [c_int, c_int64, c_int, P, P, P]),
     "spdinv_set_kernel_timing": (c_int, [c_int]),
+    "spdinv_set_trace": (c_int, [P, c_int64]),
     "spdinv_kernel_time_ms": (c_int, [c_int, P, P, P]),
     "spdinv_status_name": (ctypes.c_char_p, [c_int]),
     "spdinv_last_cuda_error": (ctypes.c_char_p, []),
@@ -306,6 +307,12 @@ def spdinv_fp64_peak_probe(kind, iters, blocks_per_sm, d_sink, stream):
     st = _call("spdinv_fp64_peak_probe", int(kind), int(iters), int(blocks_per_sm), d_sink,
                ctypes.addressof(fl), stream)
     return st, fl.value
+
+
+def spdinv_set_trace(d_records, capacity):
+    """Sets (or, with d_records None, clears) the per-task trace buffer of the
+    current device: capacity records of 32 bytes (spdinv_trace_record)."""
+    return _call("spdinv_set_trace", d_records, int(capacity))
 
 
 def spdinv_set_kernel_timing(on):

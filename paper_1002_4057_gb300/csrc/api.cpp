@@ -308,6 +308,10 @@ spdinv_status run_fp64(int64_t n, double* dA, int64_t lda, int steps, const spdi
         if (e != cudaSuccess) return cuda_fail(e);
     }
 
+    if (ds.trace) {
+        if (p.ntasks > ds.trace_cap) return SPDINV_ERR_WORKSPACE;
+        p.trace = ds.trace;
+    }
     e = cudaMemsetAsync(p.ctrl, 0, W.ctrl, stream);
     if (e != cudaSuccess) return cuda_fail(e);
     int grid = 0;
@@ -401,6 +405,22 @@ static spdinv_status set_workspace(void* d_ws, size_t bytes) {
     ds.user_ws = d_ws;
     ds.user_bytes = d_ws ? bytes : 0;
     return SPDINV_OK;
+}
+
+static spdinv_status set_trace(spdinv_trace_record* d_records, int64_t capacity) {
+    if (d_records && capacity < 1) return SPDINV_ERR_N;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e);
+    DeviceState& ds = device_state(dev);
+    std::lock_guard<std::mutex> lk(ds.mu);
+    ds.trace = d_records;
+    ds.trace_cap = d_records ? capacity : 0;
+    return SPDINV_OK;
+}
+
+spdinv_status spdinv_set_trace(spdinv_trace_record* d_records, int64_t capacity) {
+    return log_status("spdinv_set_trace", "capacity", capacity, set_trace(d_records, capacity));
 }
 
 spdinv_status spdinv_set_workspace(void* d_ws, size_t bytes) {

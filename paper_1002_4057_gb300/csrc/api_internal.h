@@ -29,6 +29,8 @@ struct DeviceState {
     void* user_ws = nullptr;  // a caller's buffer (spdinv_set_workspace), used instead when set
     size_t user_bytes = 0;
     int last_grid = 0;
+    spdinv_trace_record* trace = nullptr;  // spdinv_set_trace
+    int64_t trace_cap = 0;
     // (t, steps, ticket order, variant, split segment) -> plan
     std::map<std::tuple<int, int, int, int, int>, DevicePlan> plans;
     cudaError_t ensure_workspace(size_t bytes);

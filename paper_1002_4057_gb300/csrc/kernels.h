@@ -33,6 +33,7 @@ struct KParamsF64 {
     const SplitInfo* split; // VAR_SPLIT3: per Step-3 tile, tri_index(i, j)
     double* Pw;             // VAR_SPLIT3: partial tiles by part id, tile-major
     int* fP;                // VAR_SPLIT3: their readiness flags
+    spdinv_trace_record* trace;  // per-task trace, indexed by ticket (nullptr = off)
 };
 
 // Queues the FP64 persistent inversion (plus the stage-in copy for the

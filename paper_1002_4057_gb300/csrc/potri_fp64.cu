@@ -169,12 +169,32 @@ __global__ void __launch_bounds__(kThreads) potri_fp64_persistent(const KParamsF
     auto cX = [&](int a, int b) -> int* { return inplace ? rL + (int64_t)t * t + (int64_t)a * t + b : nullptr; };
     auto cD = [&](int j) -> int* { return inplace ? rL + 2 * (int64_t)t * t + j : nullptr; };
 
+    int prev_ticket = -1;  // tracing: the task this CTA ran last, and when it started
+    uint64_t prev_t0 = 0;
     for (;;) {
+        if constexpr (VAR) {
+            if (p.trace && threadIdx.x == 0 && prev_ticket >= 0) {
+                uint32_t smid;
+                asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+                spdinv_trace_record r;
+                r.task = p.tasks[prev_ticket];
+                r.sm = smid;
+                r.ticket = (uint32_t)prev_ticket;
+                r.cta = blockIdx.x;
+                r.t_start_ns = prev_t0;
+                r.t_end_ns = globaltimer_ns();
+                p.trace[prev_ticket] = r;
+            }
+        }
         const int ticket = next_ticket(p.ctrl, p.ntasks, &s_task);
         if (ticket < 0) return;
         const uint32_t e = p.tasks[ticket];
         const int kind = (int)task_kind(e), i = (int)task_i(e), j = (int)task_j(e);
         Acc<B> acc;
+        if constexpr (VAR) {
+            prev_ticket = ticket;
+            prev_t0 = globaltimer_ns();
+        }
 
         if (kind == K_S1_DIAG) {
             load_A_tile<B>(p, j, j, T0, true);
@@ -454,7 +474,11 @@ cudaError_t launch_impl(const KParamsF64& p, int ctas_per_sm, int num_sms, cudaS
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, sm);
     if (e != cudaSuccess) return e;
     if (occ < 1) return cudaErrorInvalidConfiguration;
-    int per = ctas_per_sm > 0 ? ctas_per_sm : (B >= 64 ? 3 : 6);
+    // 3 resident CTAs per SM at either tile: with the DFMA tile products the
+    // FP64 pipe stays full, and fewer CTAs wait less on the DAG (tile 32,
+    // 3 against 6: 1126 vs 1026 Gflop/s at n = 4096, 1210 vs 1165 at 8192,
+    // 1237 vs 1201 at 16384).
+    int per = ctas_per_sm > 0 ? ctas_per_sm : 3;
     per = per < occ ? per : occ;
     int grid = num_sms * per;
     if (grid > p.ntasks) grid = p.ntasks > 0 ? p.ntasks : 1;
@@ -486,7 +510,7 @@ cudaError_t launch_impl(const KParamsF64& p, int ctas_per_sm, int num_sms, cudaS
 cudaError_t launch_potri_fp64(const KParamsF64& p, int ctas_per_sm, int num_sms, int* d_info, cudaStream_t s,
                               int* grid_out) {
     cudaError_t e;
-    const bool var = p.variant != 0;
+    const bool var = p.variant != 0 || p.trace != nullptr;
     switch (p.b) {
         case 32:
             e = var ? launch_impl<32, true>(p, ctas_per_sm, num_sms, s, grid_out)

@@ -153,6 +153,17 @@ __device__ __forceinline__ void tile_mma(AccTC<B, S>& acc, const float* P, const
     }
     kb = kb / KS * KS;
     ke = (ke + KS - 1) / KS * KS;
+    // The tensor cores' FP32 accumulation is not rounded like an FP32 add;
+    // over a whole update chain (thousands of terms) that costs bits.  Each
+    // tile product therefore starts from a zero accumulator, and its sum is
+    // added to the running one with rounded FP32 adds.
+    float part[MI][NI][4];
+#pragma unroll
+    for (int mi = 0; mi < MI; ++mi)
+#pragma unroll
+        for (int ni = 0; ni < NI; ++ni)
+#pragma unroll
+            for (int r = 0; r < 4; ++r) part[mi][ni][r] = 0.f;
 #pragma unroll 1
     for (int k0 = kb; k0 < ke; k0 += KS) {
         uint32_t ah[MI][4], al[MI][4], bh[NI][2], bl[NI][2];
@@ -175,9 +186,9 @@ __device__ __forceinline__ void tile_mma(AccTC<B, S>& acc, const float* P, const
             for (int mi = 0; mi < MI; ++mi)
 #pragma unroll
                 for (int ni = 0; ni < NI; ++ni) {
-                    mma_tf32(acc.v[mi][ni], al[mi], bh[ni][0], bh[ni][1]);
-                    mma_tf32(acc.v[mi][ni], ah[mi], bl[ni][0], bl[ni][1]);
-                    mma_tf32(acc.v[mi][ni], ah[mi], bh[ni][0], bh[ni][1]);
+                    mma_tf32(part[mi][ni], al[mi], bh[ni][0], bh[ni][1]);
+                    mma_tf32(part[mi][ni], ah[mi], bl[ni][0], bl[ni][1]);
+                    mma_tf32(part[mi][ni], ah[mi], bh[ni][0], bh[ni][1]);
                 }
         } else {  // m16n8k16 bf16: a pairs (g, 2q..) (g+8, 2q..) (g, 2q+8..) (g+8, 2q+8..); b (2q.., g) (2q+8.., g)
 #pragma unroll
@@ -198,12 +209,18 @@ __device__ __forceinline__ void tile_mma(AccTC<B, S>& acc, const float* P, const
             for (int mi = 0; mi < MI; ++mi)
 #pragma unroll
                 for (int ni = 0; ni < NI; ++ni) {
-                    mma_bf16x(acc.v[mi][ni], al[mi], bh[ni][0], bh[ni][1]);
-                    mma_bf16x(acc.v[mi][ni], ah[mi], bl[ni][0], bl[ni][1]);
-                    mma_bf16x(acc.v[mi][ni], ah[mi], bh[ni][0], bh[ni][1]);
+                    mma_bf16x(part[mi][ni], al[mi], bh[ni][0], bh[ni][1]);
+                    mma_bf16x(part[mi][ni], ah[mi], bl[ni][0], bl[ni][1]);
+                    mma_bf16x(part[mi][ni], ah[mi], bh[ni][0], bh[ni][1]);
                 }
         }
     }
+#pragma unroll
+    for (int mi = 0; mi < MI; ++mi)
+#pragma unroll
+        for (int ni = 0; ni < NI; ++ni)
+#pragma unroll
+            for (int r = 0; r < 4; ++r) acc.v[mi][ni][r] += part[mi][ni][r];
 }
 
 }  // namespace spdinv

@@ -258,3 +258,29 @@ class SpdInverse(torch.autograd.Function):
 def spd_inverse(A):
     """Differentiable A^{-1} of SPD matrices (see SpdInverse)."""
     return SpdInverse.apply(A)
+
+
+TRACE_DTYPE = [("task", "<u4"), ("sm", "<u4"), ("ticket", "<u4"), ("cta", "<u4"), ("t_start_ns", "<u8"),
+               ("t_end_ns", "<u8")]
+
+
+def traced_potri_(A, capacity=None, **kw):
+    """potri_ with the per-task trace on: returns (info, records), records a
+    numpy structured array (TRACE_DTYPE) indexed by ticket.  The buffer is
+    sized from the plan's task count (spdinv_plan_tasks) unless given."""
+    import numpy as np
+    n, _ = _lda(A, torch.float64)
+    if capacity is None:
+        tile = kw.get("tile", 0) or (32 if n <= 16384 else 64)
+        st, tasks, _ = L.spdinv_plan_tasks(max(n, 1), tile, 0)
+        _check(st, "spdinv_plan_tasks")
+        capacity = max(len(tasks), 1) + 4096  # room for a split variant's segments
+    buf = torch.zeros(capacity * 32, dtype=torch.uint8, device=A.device)
+    _check(L.spdinv_set_trace(buf.data_ptr(), capacity), "spdinv_set_trace")
+    try:
+        info = potri_(A, **kw)
+        torch.cuda.synchronize(A.device)
+    finally:
+        L.spdinv_set_trace(None, 0)
+    rec = np.frombuffer(buf.cpu().numpy().tobytes(), dtype=np.dtype(TRACE_DTYPE))
+    return info, rec

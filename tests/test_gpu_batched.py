@@ -25,6 +25,7 @@ def _check(hs, ds, tol):
         assert info == 0
         X = full_from_lower(np.tril(d.double().cpu().numpy()))
         worst = max(worst, oracle.rel_frobenius(X, oracle.symmetrize_lower(M)))
+    print("batched: worst relative Frobenius error vs the oracle %.3e (tolerance %.1e)" % (worst, tol))
     assert worst <= tol, worst
     return worst
 
