@@ -526,7 +526,7 @@ def run_variants(args, dev, stream):
             assert int(info.item()) == 0
             return {"ms": round(ms, 2), "gflops": round(flops / (ms * 1e-3) / 1e9, 1)}
 
-        for b in (32, 64):
+        for b in (32, 64, 128):
             for order, suffix in ((L.SPDINV_PLAN_BOTTOM_LEVEL, ""), (L.SPDINV_PLAN_ALAP, "_alap")):
                 old = L.spdinv_set_plan_order(order)
                 for per in ((0, 2, 3, 4) if (b == 32 and n <= 8192 and not suffix) else (0,)):
@@ -564,16 +564,20 @@ def run_variants(args, dev, stream):
 
 
 def trace_summary(rec, t):
-    """Per-task trace of one persistent FP64 inversion -> makespan, CTA busy
-    fraction, time per task kind, when each step ran, and the achieved
-    critical path: from the task that finished last, repeatedly the producer
-    (of a tile it read) that finished last, back to a task with none."""
+    """Per-task trace of one persistent FP64 inversion -> makespan, the
+    fractions of CTA time spent working and waiting for input tiles, time per
+    task kind, when each step ran, and the achieved critical path: from the
+    task that finished last, repeatedly the producer (of a tile it read) that
+    finished last, back to a task with none; its length in tasks and the
+    work (task time minus wait) along it."""
     import numpy as np
     kind = rec["task"] >> 28
     ti = (rec["task"] >> 14) & 0x3FFF
     tj = rec["task"] & 0x3FFF
     t0 = rec["t_start_ns"].astype(np.int64)
     t1 = rec["t_end_ns"].astype(np.int64)
+    tw = rec["t_wait_ns"].astype(np.int64)
+    work = (t1 - t0) - tw  # time a task's CTA computed (or copied) rather than waited
     base = int(t0.min())
     t0, t1 = t0 - base, t1 - base
     makespan = int(t1.max())
@@ -585,6 +589,7 @@ def trace_summary(rec, t):
         if m.any():
             d = (t1[m] - t0[m]) / 1e3
             by_kind[nm] = {"tasks": int(m.sum()), "mean_us": round(float(d.mean()), 2),
+                           "mean_wait_us": round(float(tw[m].mean()) / 1e3, 2),
                            "first_start_ms": round(float(t0[m].min()) / 1e6, 3),
                            "last_end_ms": round(float(t1[m].max()) / 1e6, 3)}
     index = {}
@@ -619,11 +624,12 @@ def trace_summary(rec, t):
             break
         r = max(ps, key=lambda q: t1[q])
         path.append(r)
-    busy = float((t1 - t0).sum())
+    busy = float(work.sum())
     return {"t": t, "tasks": int(len(rec)), "ctas": ctas, "makespan_ms": round(makespan / 1e6, 3),
-            "busy_fraction": round(busy / (ctas * makespan), 4), "by_kind": by_kind,
+            "work_fraction": round(busy / (ctas * makespan), 4),
+            "wait_fraction": round(float(tw.sum()) / (ctas * makespan), 4), "by_kind": by_kind,
             "critical_path_tasks": len(path),
-            "critical_path_work_ms": round(float(sum(t1[q] - t0[q] for q in path)) / 1e6, 3),
+            "critical_path_work_ms": round(float(sum(work[q] for q in path)) / 1e6, 3),
             "critical_path_kinds": {names[k]: int(sum(1 for q in path if kind[q] == k)) for k in names
                                     if any(kind[q] == k for q in path)}}
 

@@ -563,16 +563,20 @@ SPDINV_API spdinv_status spdinv_kernel_time_ms(int which, double* ms, int* launc
  * one record per task, at index = its ticket (the position in the plan's
  * order): the task word (kind << 28 | i << 14 | j; kind 6 = a split-chain
  * segment with its id in the low 28 bits), the SM and CTA that ran it, and
- * the global timer (ns) when the CTA took it and when it finished it.  The
+ * the global timer (ns) when the CTA took it and when it finished it, and
+ * the part of that time spent waiting for input tiles' flags.  The
  * tracing build is the variant build of the kernel: a traced run measures
  * that build, within a few percent of the default one.
  * spdinv_set_trace(d_records, capacity): device array of `capacity` records
+ * (48 bytes each)
  * (NULL = off).  A call whose plan has more tasks than `capacity` returns
  * SPDINV_ERR_WORKSPACE and launches nothing.  The caller owns the buffer;
  * records of tasks that did not run (after an error) are left as they were. */
 typedef struct {
     uint32_t task, sm, ticket, cta;
     uint64_t t_start_ns, t_end_ns;
+    uint64_t t_wait_ns;  /* of that time, spent waiting for the flags of input tiles */
+    uint64_t reserved;
 } spdinv_trace_record;
 SPDINV_API spdinv_status spdinv_set_trace(spdinv_trace_record* d_records, int64_t capacity);
 

@@ -311,7 +311,7 @@ def spdinv_fp64_peak_probe(kind, iters, blocks_per_sm, d_sink, stream):
 
 def spdinv_set_trace(d_records, capacity):
     """Sets (or, with d_records None, clears) the per-task trace buffer of the
-    current device: capacity records of 32 bytes (spdinv_trace_record)."""
+    current device: capacity records of 48 bytes (spdinv_trace_record)."""
     return _call("spdinv_set_trace", d_records, int(capacity))
 
 

@@ -203,7 +203,9 @@ static int default_tile(int64_t n) {
 spdinv_status fp64_layout(int64_t n, int steps, const spdinv_opts* o, Fp64Layout* out) {
     if (n < 0) return SPDINV_ERR_N;
     const int b = (o && o->tile > 0) ? o->tile : default_tile(n);
-    if (b != 32 && b != 64) return SPDINV_ERR_UNSUPPORTED;
+    if (b != 32 && b != 64 && b != 128) return SPDINV_ERR_UNSUPPORTED;
+    // tile 128: the whole inversion, default variant, no trace (potri_fp64_b128.cu)
+    if (b == 128 && (steps != STEPS_ALL || (o && o->variant != 0))) return SPDINV_ERR_UNSUPPORTED;
     if (o && o->precision != SPDINV_PREC_FP64) return SPDINV_ERR_UNSUPPORTED;
     const int64_t t64 = (n + b - 1) / b;
     if (t64 > 16383) return SPDINV_ERR_N;
@@ -309,6 +311,7 @@ spdinv_status run_fp64(int64_t n, double* dA, int64_t lda, int steps, const spdi
     }
 
     if (ds.trace) {
+        if (b == 128) return SPDINV_ERR_UNSUPPORTED;
         if (p.ntasks > ds.trace_cap) return SPDINV_ERR_WORKSPACE;
         p.trace = ds.trace;
     }

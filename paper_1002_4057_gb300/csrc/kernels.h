@@ -40,5 +40,8 @@ struct KParamsF64 {
 // standalone TRTRI / LAUUM and, with d_info, the status write).
 cudaError_t launch_potri_fp64(const KParamsF64& p, int ctas_per_sm, int num_sms, int* d_info, cudaStream_t s,
                               int* grid_out);
+// The b = 128 kernel (potri_fp64_b128.cu): the whole inversion only, one
+// 256-thread CTA per SM.
+cudaError_t launch_potri_fp64_b128(const KParamsF64& p, int num_sms, cudaStream_t s, int* grid_out);
 
 }  // namespace spdinv

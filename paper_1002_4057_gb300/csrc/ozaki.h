@@ -21,12 +21,11 @@ cudaError_t ozaki_residual(int64_t n, const double* A, int64_t lda, const double
 // sum of the pairs' products, where base is the given matrix, or the identity
 // (identity = true) or zero when base is nullptr.  SA / SB: slice planes held
 // by the two operands.  lower: only the 128 x 128 output tiles on and below
-// the diagonal (products known to be symmetric).  sync: one device int of
-// workspace for the persistent form's wave barrier (zeroed here, on s).
+// the diagonal (products known to be symmetric).  The planes are atom-major
+// (residual_ozaki.cu, plane_index).
 cudaError_t ozaki_products_tc(int64_t n, int64_t npad, const void* Asl, int SA, const void* Xsl, int SB,
                               const int* ps, const int* pt, int npairs, const int* e, const int* f, double* R,
-                              const double* base, bool identity, double sign, bool lower, int* err, int* sync,
-                              cudaStream_t s);
+                              const double* base, bool identity, double sign, bool lower, int* err, cudaStream_t s);
 
 // Workspace bytes of ozaki_refine_step for order n.
 size_t ozaki_refine_workspace_bytes(int64_t n);

@@ -29,6 +29,7 @@ struct PCtx {
     int* ctrl;         // [0] ticket, [1] abort, [2] error, [3] info
     long long timeout_ns;
     int drop_task;
+    uint64_t* wait_ns;  // tracing: thread 0 adds the time it waits on flags here (nullptr = off)
 };
 
 __device__ __forceinline__ void raise_error(int* ctrl, int code) {
@@ -105,8 +106,10 @@ __device__ __forceinline__ bool fetch(PCtx& c, const int* f0, const int* f1, con
     if (threadIdx.x == 0) {
         const uintptr_t ga = reinterpret_cast<uintptr_t>(g0) | reinterpret_cast<uintptr_t>(g1);
         if ((ga & 15u) != 0 || (bytes & 15u) != 0) raise_error(c.ctrl, SPDINV_ERR_UNSUPPORTED);
+        const uint64_t w0 = c.wait_ns ? globaltimer_ns() : 0;
         const bool ok = (ga & 15u) == 0 && (bytes & 15u) == 0 && wait_flag(f0, c.ctrl, c.timeout_ns) &&
                         wait_flag(f1, c.ctrl, c.timeout_ns);
+        if (c.wait_ns) *c.wait_ns += globaltimer_ns() - w0;
         *c.s_flag = ok ? 0 : 1;
         if (ok) {
             fence_proxy_async_global();

@@ -145,6 +145,8 @@ __global__ void __launch_bounds__(kThreads) potri_fp64_persistent(const KParamsF
     c.ctrl = p.ctrl;
     c.timeout_ns = p.timeout_ns;
     c.drop_task = p.drop_task;
+    uint64_t wait_acc = 0;  // tracing: flag-wait time of the current task (thread 0)
+    c.wait_ns = (VAR && p.trace) ? &wait_acc : nullptr;
     if (threadIdx.x == 0) {
         mbar_init(&bar, 1);
         fence_proxy_async_shared();
@@ -183,6 +185,8 @@ __global__ void __launch_bounds__(kThreads) potri_fp64_persistent(const KParamsF
                 r.cta = blockIdx.x;
                 r.t_start_ns = prev_t0;
                 r.t_end_ns = globaltimer_ns();
+                r.t_wait_ns = wait_acc;
+                r.reserved = 0;
                 p.trace[prev_ticket] = r;
             }
         }
@@ -194,6 +198,7 @@ __global__ void __launch_bounds__(kThreads) potri_fp64_persistent(const KParamsF
         if constexpr (VAR) {
             prev_ticket = ticket;
             prev_t0 = globaltimer_ns();
+            wait_acc = 0;
         }
 
         if (kind == K_S1_DIAG) {
@@ -519,6 +524,10 @@ cudaError_t launch_potri_fp64(const KParamsF64& p, int ctas_per_sm, int num_sms,
         case 64:
             e = var ? launch_impl<64, true>(p, ctas_per_sm, num_sms, s, grid_out)
                     : launch_impl<64, false>(p, ctas_per_sm, num_sms, s, grid_out);
+            break;
+        case 128:
+            if (var) return cudaErrorInvalidValue;
+            e = launch_potri_fp64_b128(p, num_sms, s, grid_out);
             break;
         default: return cudaErrorInvalidValue;
     }

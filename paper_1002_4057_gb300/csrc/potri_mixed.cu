@@ -144,6 +144,7 @@ __global__ void __launch_bounds__(kThreads) potri_mixed_persistent(const KParams
     c.ctrl = p.ctrl;
     c.timeout_ns = p.timeout_ns;
     c.drop_task = p.drop_task;
+    c.wait_ns = nullptr;
     if (threadIdx.x == 0) {
         mbar_init(&bar, 1);
         fence_proxy_async_shared();

@@ -41,6 +41,16 @@ constexpr int LDS = BK + 8;  // shared row stride (bf16): 80 bytes, conflict-fre
 constexpr int CHUNK_TILES = 256 / BK;  // exact FP32 sums of 8-bit slice products
 constexpr int FLUSH_TILES = 128 * CHUNK_TILES;  // INT32 headroom: 128 chunks of 256 x 128^2 = 2^29
 
+// Layout of a slice plane (npad x npad BF16 digits of one slice): "atom
+// major" -- for each 64-deep K atom (one 128-byte row of the tensor cores'
+// swizzled operand tiles), the atom's 64 entries of every row, row after row.
+// Element (row r, k) of a plane sits at (k / 64 * npad + r) * 64 + k % 64, so
+// the tensor-core path fetches a 128-row tile two atoms deep (32 KB) with one
+// 3-D TMA operation.
+__device__ __forceinline__ int64_t plane_index(int64_t npad, int64_t r, int64_t k) {
+    return ((k >> 6) * npad + r) * 64 + (k & 63);
+}
+
 // Positive doubles order like their bit patterns, so the maxima are kept as
 // 64-bit integers updated with atomicMax.
 __device__ __forceinline__ unsigned long long dbits(double v) { return (unsigned long long)__double_as_longlong(v); }
@@ -135,7 +145,7 @@ __global__ void slice_A_kernel(int64_t n, int64_t npad, const double* A, int64_t
         double v = tile[tx][r];
         if (ti == tj && k > i) v = tile[r][tx];  // upper part of a diagonal tile: mirror
         const int ei = i < n ? e[i] : 0;
-        cut(v, ei, S, Asl + i * npad + k, plane);
+        cut(v, ei, S, Asl + plane_index(npad, i, k), plane);
     }
     if (ti != tj) {
         // mirrored tile: (i, k) = (tj*32 + r, ti*32 + c), value A(ti*32 + c, tj*32 + r)
@@ -143,7 +153,7 @@ __global__ void slice_A_kernel(int64_t n, int64_t npad, const double* A, int64_t
             const int64_t i = tj * 32 + r, k = ti * 32 + tx;
             const double v = tile[r][tx];
             const int ei = i < n ? e[i] : 0;
-            cut(v, ei, S, Asl + i * npad + k, plane);
+            cut(v, ei, S, Asl + plane_index(npad, i, k), plane);
         }
     }
 }
@@ -155,7 +165,7 @@ __global__ void slice_X_kernel(int64_t n, int64_t npad, const double* X, const i
     const int fj = j < n ? f[j] : 0;
     for (int64_t k = threadIdx.x; k < npad; k += blockDim.x) {
         const double v = (j < n && k < n) ? X[k + j * n] : 0.0;
-        cut(v, fj, S, Xsl + j * npad + k, plane);
+        cut(v, fj, S, Xsl + plane_index(npad, j, k), plane);
     }
 }
 
@@ -206,18 +216,19 @@ __global__ void __launch_bounds__(THREADS, 1) ozaki_residual_kernel(const OzPara
 
     auto load_stage = [&](int step, int stage) {
         const int pair = step / ktiles, kt = step - pair * ktiles;
-        const __nv_bfloat16* a = p.Asl + p.ps[pair] * plane + m0 * p.npad + (int64_t)kt * BK;
-        const __nv_bfloat16* b = p.Xsl + p.pt[pair] * plane + n0 * p.npad + (int64_t)kt * BK;
+        // BK = 32 entries of a row lie inside one 64-deep atom: contiguous
+        const __nv_bfloat16* a = p.Asl + p.ps[pair] * plane + plane_index(p.npad, m0, (int64_t)kt * BK);
+        const __nv_bfloat16* b = p.Xsl + p.pt[pair] * plane + plane_index(p.npad, n0, (int64_t)kt * BK);
         __nv_bfloat16* da = sA + stage * BM * LDS;
         __nv_bfloat16* db = sB + stage * BN * LDS;
 #pragma unroll
         for (int u = 0; u < 2; ++u) {  // A: 128 rows x 4 chunks of 16 bytes
             const int c = tid + u * THREADS, row = c >> 2, col = (c & 3) * 8;
-            cp_async16(da + row * LDS + col, a + row * p.npad + col);
+            cp_async16(da + row * LDS + col, a + row * 64 + col);
         }
         {  // B: 64 rows x 4 chunks
             const int row = tid >> 2, col = (tid & 3) * 8;
-            cp_async16(db + row * LDS + col, b + row * p.npad + col);
+            cp_async16(db + row * LDS + col, b + row * 64 + col);
         }
     };
 
@@ -375,8 +386,7 @@ cudaError_t ozaki_residual(int64_t n, const double* A, int64_t lda, const double
         }
     p.npairs = np;
     if (tc) {
-        err = ozaki_products_tc(n, npad, Asl, S, Xsl, S, p.ps, p.pt, np, e, f, R, nullptr, true, -1.0, false, errw,
-                                f + npad, s);
+        err = ozaki_products_tc(n, npad, Asl, S, Xsl, S, p.ps, p.pt, np, e, f, R, nullptr, true, -1.0, false, errw, s);
         if (launches) *launches += 7;
         return err;
     }
@@ -446,7 +456,6 @@ struct RefineWs {
     __nv_bfloat16 *Asl, *Xsl, *Rsl, *Ysl;
     unsigned long long* mx;
     int *eA, *eX, *fR, *eY;
-    int* sync;  // the slice GEMM's wave barrier
 };
 
 RefineWs refine_layout(int64_t n, void* ws) {
@@ -462,7 +471,6 @@ RefineWs refine_layout(int64_t n, void* ws) {
     w.eX = w.eA + npad;
     w.fR = w.eX + npad;
     w.eY = w.fR + npad;
-    w.sync = w.eY + npad;  // in the workspace's 1024-byte tail
     return w;
 }
 
@@ -491,7 +499,7 @@ cudaError_t ozaki_refine_step(int64_t n, const double* A, int64_t lda, double* X
     int ps[64], pt[64];
     int np = level_pairs(kResSlices, kResSlices, levelsR, ps, pt);
     err = ozaki_products_tc(n, npad, w.Asl, kResSlices, w.Xsl, kResSlices, ps, pt, np, w.eA, w.eX, R, nullptr, true,
-                            -1.0, false, errw, w.sync, s);  // R = I - A X, every tile
+                            -1.0, false, errw, s);  // R = I - A X, every tile
     if (err != cudaSuccess) return err;
     err = slice_columns(n, npad, R, kRSlices, w.Rsl, w.mx, w.fR, s, launches);
     if (err != cudaSuccess) return err;
@@ -504,7 +512,7 @@ cudaError_t ozaki_refine_step(int64_t n, const double* A, int64_t lda, double* X
         const int L = kChainLevels[m - 1];
         np = level_pairs(L + 1, kRSlices, L, ps, pt);
         err = ozaki_products_tc(n, npad, left, left_slices, w.Rsl, kRSlices, ps, pt, np, eleft, w.fR, Y, nullptr,
-                                false, 1.0, true, errw, w.sync, s);
+                                false, 1.0, true, errw, s);
         if (err != cudaSuccess) return err;
         *launches += 1;
         if (m + 1 < order) {

@@ -29,7 +29,6 @@
 #include <cuda_runtime.h>
 
 #include <cstdlib>
-#include <cstring>
 #include <mutex>
 
 #include "api_internal.h"
@@ -39,8 +38,12 @@
 namespace spdinv {
 namespace {
 
-constexpr int TM = 128, TN = 128, TK = 64;  // output tile; K per stage = one 128-byte swizzle row of bf16
-constexpr int NSTAGE = 6;  // 1.5 exact 256-deep chunks' worth of copies run ahead of the MMAs
+constexpr int TM = 128, TN = 128;
+constexpr int ATOM = 64;                 // K entries of one 128-byte swizzle row of bf16
+constexpr int ATOMS = 2;                 // atoms per stage: one 3-D TMA operation per operand
+constexpr int TK = ATOM * ATOMS;         // K per stage
+constexpr int NSTAGE = 3;                // 192 KB of copies in flight
+constexpr int ATOM_BYTES = TM * ATOM * 2;  // one 128-row atom tile, 16 KB
 constexpr int A_BYTES = TM * TK * 2, B_BYTES = TN * TK * 2, STAGE_BYTES = A_BYTES + B_BYTES;
 constexpr int CHUNK_STAGES = 1024 / TK;  // exact FP32 chunk: 1024 products of balanced 8-bit digits (<= 2^24)
 constexpr int TMEM_COLS = 512;          // two 128-column FP32 accumulators + INT64 level sums (256 columns)
@@ -67,8 +70,6 @@ struct TcParams {
     double* R;
     int* err;
     long long timeout_ns;
-    int* wave;            // persistent kernel: the wave barrier's arrival counter (zero at launch)
-    int prefetch;         // persistent kernel: stages ahead that the operand owners prefetch into L2 (0 = off)
 };
 
 // Shared-memory matrix descriptor of a K-major tile written by TMA with
@@ -77,11 +78,14 @@ __device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
     return (uint64_t)((saddr >> 4) & 0x3FFFu) | (1ull << 16) | (64ull << 32) | (1ull << 46) | (2ull << 61);
 }
 
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* tm, int x, int y, uint64_t* bar) {
+// One TMA operation: a box of ATOMS atoms x 128 rows x 64 entries of the
+// atom-major slice planes (x: entry, y: row, z: plane * (npad / 64) + atom),
+// landing as ATOMS consecutive 16 KB swizzled atom tiles.
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* tm, int y, int z, uint64_t* bar) {
     asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
             smem_u32(dst)),
-        "l"(reinterpret_cast<uint64_t>(tm)), "r"(x), "r"(y), "r"(smem_u32(bar))
+        "l"(reinterpret_cast<uint64_t>(tm)), "r"(0), "r"(y), "r"(z), "r"(smem_u32(bar))
         : "memory");
 }
 
@@ -219,7 +223,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     __shared__ uint32_t tmem_slot;
     __shared__ volatile int s_abort;
     __shared__ int s_f[TN];
-    __shared__ int s_ya[64], s_yb[64];  // per pair: row of the A and X slice planes' tiles
+    __shared__ int s_za[64], s_zb[64];  // per pair: first atom plane of the A and X slices
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int tile_m, tile_n;
     block_of((int)blockIdx.x, p.tiles, p.tiles, p.lower != 0, tile_m, tile_n);
@@ -244,8 +248,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     }
     for (int j = threadIdx.x; j < TN; j += NTHREADS) s_f[j] = (n0 + j < p.n) ? p.f[n0 + j] : 0;
     for (int q = threadIdx.x; q < p.npairs; q += NTHREADS) {
-        s_ya[q] = (int)(p.ps[q] * p.npad + m0);
-        s_yb[q] = (int)(p.pt[q] * p.npad + n0);
+        s_za[q] = (int)(p.ps[q] * (p.npad / ATOM));
+        s_zb[q] = (int)(p.pt[q] * (p.npad / ATOM));
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
@@ -267,8 +271,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 const int pair = it / kstages, kt = it - pair * kstages;
                 unsigned char* st = smem + s * STAGE_BYTES;
                 mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
-                tma_load_2d(st, &tmA, kt * TK, s_ya[pair], &full[s]);
-                tma_load_2d(st + A_BYTES, &tmB, kt * TK, s_yb[pair], &full[s]);
+                tma_load_3d(st, &tmA, (int)m0, s_za[pair] + kt * ATOMS, &full[s]);
+                tma_load_3d(st + A_BYTES, &tmB, (int)n0, s_zb[pair] + kt * ATOMS, &full[s]);
             }
             if (s_abort)  // let the copies already issued land before the CTA leaves
                 for (int k = it - NSTAGE > 0 ? it - NSTAGE : 0; k < it; ++k)
@@ -293,10 +297,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     }
                     tc_fence_after();
                     const uint32_t sa = smem_u32(smem + s * STAGE_BYTES);
-                    const uint64_t da = sdesc_sw128(sa), db = sdesc_sw128(sa + A_BYTES);
 #pragma unroll
-                    for (int k = 0; k < TK / 16; ++k)  // +32 bytes per K=16 inside the swizzle row
-                        umma_bf16(d, da + 2 * k, db + 2 * k, (q | k) != 0);
+                    for (int a = 0; a < ATOMS; ++a) {  // each atom: a 128-row swizzled tile of 64 entries
+                        const uint64_t da = sdesc_sw128(sa + a * ATOM_BYTES);
+                        const uint64_t db = sdesc_sw128(sa + A_BYTES + a * ATOM_BYTES);
+#pragma unroll
+                        for (int k = 0; k < ATOM / 16; ++k)  // +32 bytes per K=16 inside the swizzle row
+                            umma_bf16(d, da + 2 * k, db + 2 * k, (q | a | k) != 0);
+                    }
                     umma_commit(&empty[s]);
                 }
                 if (!ok) break;
@@ -391,65 +399,85 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     }
 }
 
-// L2 prefetch of one box of a tensor map (no shared memory, no completion).
-__device__ __forceinline__ void tma_prefetch_2d(const CUtensorMap* tm, int x, int y) {
-    asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global [%0, {%1, %2}];" ::"l"(reinterpret_cast<uint64_t>(tm)),
-                 "r"(x), "r"(y)
-                 : "memory");
+
+// ---- the wide form: 128 x 256 output tiles ---------------------------------
+// Per flop of MMA work it brings three quarters of the operand bytes of the
+// 128 x 128 tile: with about 190 KB of copies in flight per SM and the copy
+// latency under load, that, not the tensor pipe, sets the rate.  The FP32
+// accumulator (256 columns) is single-buffered and the INT32 level sums take
+// the other 256 tensor-memory columns; while the epilogue drains a chunk the
+// copies keep filling the ring.
+constexpr int WN = 256;                        // output columns per tile
+constexpr int W_NSTAGE = 4;                    // 4 x 48 KB of copies in flight
+constexpr int WA_BYTES = TM * ATOM * 2;        // 16 KB: A, 128 rows x one atom
+constexpr int WB_BYTES = WN * ATOM * 2;        // 32 KB: X, 256 rows x one atom
+constexpr int W_STAGE = WA_BYTES + WB_BYTES;
+constexpr int W_CHUNK = 1024 / ATOM;           // stages per exact 1024-deep chunk
+constexpr int W_LVL = 256;                     // tensor-memory column of the INT32 level sums
+constexpr int W_COLS = WN / 2;                 // columns per epilogue thread
+constexpr uint32_t IDESC_W = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(WN >> 3) << 17) |
+                             ((uint32_t)(TM >> 4) << 24);
+
+__device__ __forceinline__ void umma_bf16_w(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "l"(da), "l"(db), "r"(IDESC_W), "r"(accumulate));
 }
 
-// Is this CTA the first of its wave to read its A rows (own_a) or its X
-// columns (own_b)?  Waves are runs of gridDim.x consecutive launch indices.
-__device__ void operand_owners(int pid, int wave_start, int tiles, bool lower, int bm, int bn, bool& own_a,
-                               bool& own_b) {
-    own_a = own_b = true;
-    for (int q = wave_start; q < pid && (own_a || own_b); ++q) {
-        int m, nn;
-        block_of(q, tiles, tiles, lower, m, nn);
-        if (m == bm) own_a = false;
-        if (nn == bn) own_b = false;
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
+        "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(taddr),
+        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]),
+        "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]), "r"(r[16]),
+        "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]), "r"(r[24]),
+        "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31])
+        : "memory");
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
+// Tile (bm, bn) of launch index pid: 128-row block bm, 256-column block bn.
+// lower: only tiles holding an entry on or below the diagonal, bn <= bm / 2
+// (rows 2r and 2r + 1 hold r + 1 tiles each; r (r + 1) tiles come first).
+__device__ __forceinline__ void block_of_wide(int pid, int tb_m, int tb_n, bool lower, int& bm, int& bn) {
+    if (!lower) {
+        block_of(pid, tb_m, tb_n, false, bm, bn);
+        return;
     }
+    int r = (int)((sqrt(4.0 * pid + 1.0) - 1.0) / 2.0);
+    while ((r + 1) * (r + 2) <= pid) ++r;
+    while (r * (r + 1) > pid) --r;
+    const int off = pid - r * (r + 1);
+    bm = 2 * r + off / (r + 1);
+    bn = off % (r + 1);
 }
 
-// The persistent form of the slice GEMM: one CTA per SM (a cooperative
-// launch, so every CTA is resident), each taking output tile w * G + c of
-// the grouped raster in wave w (G CTAs, c its index).  The tensor memory,
-// the barriers and the shared-memory ring are set up once; the ring and the
-// two accumulators run on across tiles.
-//
-// Why: with one CTA per tile, CTAs drift apart over the waves and the slice
-// rows that concurrent CTAs stream no longer fit in L2; about a fifth of the
-// sectors then come from DRAM, and since every 32 KB stage holds hundreds of
-// sectors, almost every stage waits for DRAM.  Here the TMA producers meet at
-// a barrier between waves, so the CTAs of a wave stream the same slice rows at
-// about the same time, and the first CTA of a wave that reads a block of A's
-// (or X's) slice rows prefetches it into L2 `prefetch` stages ahead of use,
-// so that the other CTAs of the wave, and itself, find it there.
 __global__ void __launch_bounds__(NTHREADS, 1)
-    ozaki_tc_persistent(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                        const __grid_constant__ TcParams p) {
+    ozaki_tc_wide(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                  const __grid_constant__ TcParams p) {
     unsigned char* smem = dynamic_smem();  // 1024-byte aligned (swizzled operand tiles)
-    __shared__ __align__(8) uint64_t full[NSTAGE], empty[NSTAGE], accf[2], acce[2], fin;
+    __shared__ __align__(8) uint64_t full[W_NSTAGE], empty[W_NSTAGE], accf, acce, fin;
     __shared__ uint32_t tmem_slot;
     __shared__ volatile int s_abort;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int G = (int)gridDim.x, cta = (int)blockIdx.x;
-    const int total = p.lower ? p.tiles * (p.tiles + 1) / 2 : p.tiles * p.tiles;
-    const int nwaves = (total + G - 1) / G;
-    const int kstages = (int)(p.npad / TK);            // stages per slice pair
-    const int chunks_per_pair = (kstages + CHUNK_STAGES - 1) / CHUNK_STAGES;
-    const int stages_per_tile = p.npairs * kstages;
-    const int chunks_per_tile = p.npairs * chunks_per_pair;
+    const int tb_m = (int)(p.npad / TM), tb_n = (int)(p.npad / WN);
+    int tile_m, tile_n;
+    block_of_wide((int)blockIdx.x, tb_m, tb_n, p.lower != 0, tile_m, tile_n);
+    const int64_t m0 = (int64_t)tile_m * TM, n0 = (int64_t)tile_n * WN;
+    const int kstages = (int)(p.npad / ATOM);  // stages per slice pair
+    const int chunks_per_pair = (kstages + W_CHUNK - 1) / W_CHUNK;
+    const int total_stages = p.npairs * kstages;
+    const int total_chunks = p.npairs * chunks_per_pair;
+    const int zpl = (int)(p.npad / ATOM);  // atom planes per slice plane
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < NSTAGE; ++s) {
+        for (int s = 0; s < W_NSTAGE; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
-        for (int b = 0; b < 2; ++b) {
-            mbar_init(&accf[b], 1);
-            mbar_init(&acce[b], EPI_WARPS);
-        }
+        mbar_init(&accf, 1);
+        mbar_init(&acce, EPI_WARPS);
         mbar_init(&fin, 1);
         s_abort = 0;
         fence_proxy_async_shared();
@@ -466,186 +494,109 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const uint32_t tmem = tmem_slot;
 
     if (warp == 0) {
-        if (lane == 0) {  // ---- TMA producer
+        if (lane == 0) {  // ---- TMA producer: one atom of A (128 rows) and of X (256 rows) per stage
             int it = 0;
-            bool stop = false;
-            for (int w = 0; w < nwaves && !stop; ++w) {
-                const int pid = w * G + cta;
-                if (pid < total) {
-                    int bm, bn;
-                    block_of(pid, p.tiles, p.tiles, p.lower != 0, bm, bn);
-                    const int m0 = bm * TM, n0 = bn * TN;
-                    bool own_a = false, own_b = false;
-                    if (p.prefetch > 0) operand_owners(pid, w * G, p.tiles, p.lower != 0, bm, bn, own_a, own_b);
-                    auto prefetch = [&](int q) {
-                        const int pair = q / kstages, kt = q - pair * kstages;
-                        if (own_a) tma_prefetch_2d(&tmA, kt * TK, (int)(p.ps[pair] * p.npad) + m0);
-                        if (own_b) tma_prefetch_2d(&tmB, kt * TK, (int)(p.pt[pair] * p.npad) + n0);
-                    };
-                    for (int q = 0; q < p.prefetch && q < stages_per_tile && (own_a || own_b); ++q) prefetch(q);
-                    for (int q = 0; q < stages_per_tile; ++q, ++it) {
-                        const int s = it % NSTAGE;
-                        if (!wait_bar(&empty[s], ((it / NSTAGE) & 1) ^ 1, &s_abort, p)) {
-                            stop = true;
-                            break;
-                        }
-                        const int pair = q / kstages, kt = q - pair * kstages;
-                        unsigned char* st = smem + s * STAGE_BYTES;
-                        mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
-                        tma_load_2d(st, &tmA, kt * TK, (int)(p.ps[pair] * p.npad) + m0, &full[s]);
-                        tma_load_2d(st + A_BYTES, &tmB, kt * TK, (int)(p.pt[pair] * p.npad) + n0, &full[s]);
-                        if ((own_a || own_b) && q + p.prefetch < stages_per_tile) prefetch(q + p.prefetch);
-                    }
-                }
-                if (!stop && w + 1 < nwaves) {  // wave barrier (every CTA has a tile in a wave before the last)
-                    atomicAdd(p.wave, 1);
-                    const int target = G * (w + 1);
-                    const uint64_t t0 = globaltimer_ns();
-                    while (ld_acquire_gpu(p.wave) < target) {
-                        if (ld_relaxed_gpu(p.err) != 0) {
-                            s_abort = 1;
-                            stop = true;
-                            break;
-                        }
-                        if ((long long)(globaltimer_ns() - t0) > p.timeout_ns) {
-                            s_abort = 1;
-                            atomicCAS(p.err, 0, SPDINV_ERR_TIMEOUT);
-                            stop = true;
-                            break;
-                        }
-                        __nanosleep(64);
-                    }
-                }
+            for (; it < total_stages; ++it) {
+                const int s = it % W_NSTAGE;
+                if (!wait_bar(&empty[s], ((it / W_NSTAGE) & 1) ^ 1, &s_abort, p)) break;
+                const int pair = it / kstages, kt = it - pair * kstages;
+                unsigned char* st = smem + s * W_STAGE;
+                mbar_arrive_expect_tx(&full[s], W_STAGE);
+                tma_load_3d(st, &tmA, (int)m0, p.ps[pair] * zpl + kt, &full[s]);
+                tma_load_3d(st + WA_BYTES, &tmB, (int)n0, p.pt[pair] * zpl + kt, &full[s]);
             }
-            if (s_abort)  // let the copies already issued land before the CTA leaves
-                for (int k = it - NSTAGE > 0 ? it - NSTAGE : 0; k < it; ++k)
-                    drain_bar(&full[k % NSTAGE], (k / NSTAGE) & 1, 200000000LL);
+            if (s_abort)
+                for (int k = it - W_NSTAGE > 0 ? it - W_NSTAGE : 0; k < it; ++k)
+                    drain_bar(&full[k % W_NSTAGE], (k / W_NSTAGE) & 1, 200000000LL);
         }
     } else if (warp == 1) {
-        if (lane == 0) {  // ---- MMA issuer
-            int it = 0, cc = 0;
-            bool ok = true;
-            for (int w = 0; w < nwaves && ok; ++w) {
-                if (w * G + cta >= total) break;
-                for (int c = 0; c < chunks_per_tile && ok; ++c, ++cc) {
-                    if (s_abort) {
-                        ok = false;
-                        break;
-                    }
-                    const int b = cc & 1;
-                    if (!wait_bar(&acce[b], ((cc >> 1) & 1) ^ 1, &s_abort, p)) {
+        if (lane == 0) {  // ---- MMA issuer: one chunk at a time into the single accumulator
+            int it = 0;
+            for (int c = 0; c < total_chunks && !s_abort; ++c) {
+                if (!wait_bar(&acce, (c & 1) ^ 1, &s_abort, p)) break;  // the epilogue drained chunk c - 1
+                tc_fence_after();
+                const int q0 = (c % chunks_per_pair) * W_CHUNK;
+                const int nq = min(W_CHUNK, kstages - q0);
+                bool ok = true;
+                for (int q = 0; q < nq; ++q, ++it) {
+                    const int s = it % W_NSTAGE;
+                    if (!wait_bar(&full[s], (it / W_NSTAGE) & 1, &s_abort, p)) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t d = tmem + (uint32_t)(b * TN);
-                    const int q0 = (c % chunks_per_pair) * CHUNK_STAGES;
-                    const int nq = min(CHUNK_STAGES, kstages - q0);
-                    for (int q = 0; q < nq; ++q, ++it) {
-                        const int s = it % NSTAGE;
-                        if (!wait_bar(&full[s], (it / NSTAGE) & 1, &s_abort, p)) {
-                            ok = false;
-                            break;
-                        }
-                        tc_fence_after();
-                        const uint32_t sa = smem_u32(smem + s * STAGE_BYTES);
-                        const uint64_t da = sdesc_sw128(sa), db = sdesc_sw128(sa + A_BYTES);
+                    const uint32_t sa = smem_u32(smem + s * W_STAGE);
+                    const uint64_t da = sdesc_sw128(sa), db = sdesc_sw128(sa + WA_BYTES);
 #pragma unroll
-                        for (int k = 0; k < TK / 16; ++k) umma_bf16(d, da + 2 * k, db + 2 * k, (q | k) != 0);
-                        umma_commit(&empty[s]);
-                    }
-                    if (!ok) break;
-                    umma_commit(&accf[b]);
+                    for (int k = 0; k < ATOM / 16; ++k) umma_bf16_w(tmem, da + 2 * k, db + 2 * k, (q | k) != 0);
+                    umma_commit(&empty[s]);
                 }
+                if (!ok) break;
+                umma_commit(&accf);
             }
-            umma_commit(&fin);  // every MMA issued above has completed when this arrives
+            umma_commit(&fin);
             drain_bar(&fin, 0, 2000000000LL);
         }
-    } else {  // ---- epilogue: warps 2..9, half of an accumulator row per thread
+    } else {  // ---- epilogue: warps 2..9, half of a row (128 columns) per thread
         const int quarter = warp & 3;
         const int half = (warp - 2) >> 2;
         const int row = quarter * 32 + lane;
+        const int64_t i = m0 + row;
+        const int ei = (i < p.n) ? p.e[i] : 0;
         const uint32_t trow = tmem + ((uint32_t)(quarter * 32) << 16);
-        const uint32_t tlvl = trow + (uint32_t)(LVL_COL + half * 2 * EPI_COLS);
-        int acc[EPI_COLS];
-#pragma unroll
-        for (int j = 0; j < EPI_COLS; ++j) acc[j] = 0;
-        int cc = 0;
-        bool ok = true;
-        for (int w = 0; w < nwaves && ok; ++w) {
-            const int pid = w * G + cta;
-            if (pid >= total) break;
-            int bm, bn;
-            block_of(pid, p.tiles, p.tiles, p.lower != 0, bm, bn);
-            const int64_t m0 = (int64_t)bm * TM, n0 = (int64_t)bn * TN;
-            const int64_t i = m0 + row;
-            const int ei = (i < p.n) ? p.e[i] : 0;
-            bool first_flush = true, level_start = true;
-            int pair = 0, cin = 0;
-            for (int c = 0; c < chunks_per_tile; ++c, ++cc) {
-                const int b = cc & 1;
-                if (!wait_bar(&accf[b], (cc >> 1) & 1, &s_abort, p)) {
-                    ok = false;
-                    break;
-                }
-                tc_fence_after();
-                {
-                    uint32_t r0[32], r1[32];
-                    tmem_ld32_async(trow + (uint32_t)(b * TN + half * EPI_COLS), r0);
-                    tmem_ld32_async(trow + (uint32_t)(b * TN + half * EPI_COLS + 32), r1);
-                    tmem_wait_ld();
-#pragma unroll
-                    for (int u = 0; u < 32; ++u) {
-                        acc[u] += __float2int_rn(__uint_as_float(r0[u]));
-                        acc[32 + u] += __float2int_rn(__uint_as_float(r1[u]));
-                    }
-                }
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&acce[b]);
-                if (++cin < chunks_per_pair) continue;
-                cin = 0;
-                const int lv = p.ps[pair] + p.pt[pair];
-                ++pair;
-                const bool level_end = !(pair < p.npairs && p.ps[pair] + p.pt[pair] == lv);
-#pragma unroll
-                for (int g = 0; g < EPI_COLS / 8; ++g) {
-                    uint32_t r[16];
-                    if (!level_start) tmem_ld16(tlvl + (uint32_t)(g * 16), r);
-#pragma unroll
-                    for (int u = 0; u < 8; ++u) {
-                        long long v = level_start ? 0ll
-                                                  : (long long)(((unsigned long long)r[2 * u + 1] << 32) | r[2 * u]);
-                        v += (long long)acc[g * 8 + u];
-                        acc[g * 8 + u] = 0;
-                        r[2 * u] = (uint32_t)(unsigned long long)v;
-                        r[2 * u + 1] = (uint32_t)((unsigned long long)v >> 32);
-                    }
-                    tmem_st16(tlvl + (uint32_t)(g * 16), r);
-                }
-                level_start = level_end;
-                if (!level_end) continue;
-                const double ri = pow2(ei - 8 * (lv + 2));
+        const uint32_t tacc = trow + (uint32_t)(half * W_COLS);          // this thread's FP32 accumulator
+        const uint32_t tsum = trow + (uint32_t)(W_LVL + half * W_COLS);  // and INT32 level sums
+        bool first_flush = true, fresh = true;  // fresh: the level sums hold nothing yet
+        int pair = 0, cin = 0, since_flush = 0;
+        for (int c = 0; c < total_chunks; ++c) {
+            if (!wait_bar(&accf, c & 1, &s_abort, p)) break;
+            tc_fence_after();
 #pragma unroll 1
-                for (int g = 0; g < EPI_COLS / 16; ++g) {
-                    uint32_t r[32];
-                    tmem_ld32(tlvl + (uint32_t)(g * 32), r);
-                    if (i >= p.n) continue;
+            for (int g = 0; g < W_COLS / 32; ++g) {  // sums += int(chunk), exact: chunk entries are integers <= 2^24
+                uint32_t r[32], l[32];
+                tmem_ld32_async(tacc + (uint32_t)(g * 32), r);
+                if (!fresh) tmem_ld32_async(tsum + (uint32_t)(g * 32), l);
+                tmem_wait_ld();
 #pragma unroll
-                    for (int u = 0; u < 16; ++u) {
-                        const long long v = (long long)(((unsigned long long)r[2 * u + 1] << 32) | r[2 * u]);
-                        const int64_t jj = n0 + half * EPI_COLS + g * 16 + u;
-                        if (jj < p.n) {
-                            double* dst = &p.R[i + jj * p.n];
-                            const double base =
-                                first_flush ? (p.base ? p.base[i + jj * p.n] : (p.identity && i == jj ? 1.0 : 0.0))
-                                            : *dst;
-                            *dst = fma(p.sign * (double)v, ri * pow2(p.f[jj]), base);
-                        }
+                for (int u = 0; u < 32; ++u)
+                    l[u] = (uint32_t)(__float2int_rn(__uint_as_float(r[u])) + (fresh ? 0 : (int)l[u]));
+                tmem_st32(tsum + (uint32_t)(g * 32), l);
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acce);
+            fresh = false;
+            ++since_flush;
+            const int lv = p.ps[pair] + p.pt[pair];
+            bool flush = since_flush >= 127;  // INT32 headroom: 127 chunks of at most 2^24
+            if (++cin == chunks_per_pair) {
+                cin = 0;
+                ++pair;
+                flush = flush || !(pair < p.npairs && p.ps[pair] + p.pt[pair] == lv);  // end of a level
+            }
+            if (!flush) continue;
+            // R = base + sign 2^{e_i + f_j - 8(lv+2)} * sum (exact scale, one FMA per entry)
+            const double ri = pow2(ei - 8 * (lv + 2));
+#pragma unroll 1
+            for (int g = 0; g < W_COLS / 32; ++g) {
+                uint32_t l[32];
+                tmem_ld32(tsum + (uint32_t)(g * 32), l);
+                if (i >= p.n) continue;
+#pragma unroll
+                for (int u = 0; u < 32; ++u) {
+                    const int64_t jj = n0 + half * W_COLS + g * 32 + u;
+                    if (jj < p.n) {
+                        double* dst = &p.R[i + jj * p.n];
+                        const double base =
+                            first_flush ? (p.base ? p.base[i + jj * p.n] : (p.identity && i == jj ? 1.0 : 0.0))
+                                        : *dst;
+                        *dst = fma(p.sign * (double)(int)l[u], ri * pow2(p.f[jj]), base);
                     }
                 }
-                first_flush = false;
             }
+            first_flush = false;
+            fresh = true;
+            since_flush = 0;
         }
     }
     tc_fence_before();
@@ -669,46 +620,36 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
-// 2D map over S slice planes stacked as (S*npad) rows of npad bf16, box 64
-// (K, one 128-byte swizzle row) x rows.
-bool make_map(CUtensorMap* m, const void* base, int64_t npad, int S, int rows) {
+// 3-D map over S atom-major slice planes (residual_ozaki.cu): x = entry of
+// an atom (64, one 128-byte swizzle row), y = row (npad), z = atom plane
+// (S * npad / 64, plane s's atoms from s * npad / 64); box 64 x rows x atoms.
+bool make_map(CUtensorMap* m, const void* base, int64_t npad, int S, int rows, int atoms) {
     auto fn = encode_fn();
     if (!fn) return false;
-    cuuint64_t dims[2] = {(cuuint64_t)npad, (cuuint64_t)(S * npad)};
-    cuuint64_t strides[1] = {(cuuint64_t)(npad * 2)};
-    cuuint32_t box[2] = {(cuuint32_t)TK, (cuuint32_t)rows};
-    cuuint32_t estr[2] = {1u, 1u};
-    return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+    cuuint64_t dims[3] = {(cuuint64_t)ATOM, (cuuint64_t)npad, (cuuint64_t)(S * (npad / ATOM))};
+    cuuint64_t strides[2] = {(cuuint64_t)(ATOM * 2), (cuuint64_t)(npad * ATOM * 2)};
+    cuuint32_t box[3] = {(cuuint32_t)ATOM, (cuuint32_t)rows, (cuuint32_t)atoms};
+    cuuint32_t estr[3] = {1u, 1u, 1u};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box, estr,
               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 }  // namespace
 
-// SPDINV_SLICE_GEMM=legacy: one CTA per output tile (the first form of this
-// kernel, kept for comparison); SPDINV_SLICE_PREFETCH=<stages>: the owners'
-// L2 prefetch distance of the persistent form (default 0 = off: at n = 4096
-// and 16384 every distance from 8 to 32 measured 15-18 % slower).
-static bool slice_gemm_legacy() {
-    static const bool v = [] {
-        const char* env = std::getenv("SPDINV_SLICE_GEMM");
-        return env && std::strcmp(env, "legacy") == 0;
-    }();
-    return v;
-}
-static int slice_prefetch() {
+// Output tile width of the slice GEMM: 256 (the wide form, default) or 128;
+// SPDINV_SLICE_TILE=128|256 in the environment chooses.
+static int slice_tile() {
     static const int v = [] {
-        const char* env = std::getenv("SPDINV_SLICE_PREFETCH");
-        const int d = env ? std::atoi(env) : 0;
-        return d < 0 ? 0 : (d > 256 ? 256 : d);
+        const char* env = std::getenv("SPDINV_SLICE_TILE");
+        return (env && std::atoi(env) == 128) ? 128 : 256;
     }();
     return v;
 }
 
 cudaError_t ozaki_products_tc(int64_t n, int64_t npad, const void* Asl, int SA, const void* Xsl, int SB,
                               const int* ps, const int* pt, int npairs, const int* e, const int* f, double* R,
-                              const double* base, bool identity, double sign, bool lower, int* err, int* sync,
-                              cudaStream_t s) {
+                              const double* base, bool identity, double sign, bool lower, int* err, cudaStream_t s) {
     if (npad % 256 != 0 || npairs < 1 || npairs > 64) return cudaErrorInvalidValue;  // whole 256-deep chunks
     for (int q = 0; q < npairs; ++q)  // every pair must address planes that the maps cover
         if (ps[q] < 0 || ps[q] >= SA || pt[q] < 0 || pt[q] >= SB) return cudaErrorInvalidValue;
@@ -730,54 +671,32 @@ cudaError_t ozaki_products_tc(int64_t n, int64_t npad, const void* Asl, int SA, 
     p.tiles = (int)(npad / TM);
     p.err = err;
     p.timeout_ns = 20LL * 1000000000LL;
-    p.wave = sync;
-    p.prefetch = slice_prefetch();
     CUtensorMap ma, mb;
-    if (!make_map(&ma, Asl, npad, SA, TM) || !make_map(&mb, Xsl, npad, SB, TN)) return cudaErrorInvalidValue;
-    const int sm = NSTAGE * STAGE_BYTES;
-    const int total = lower ? p.tiles * (p.tiles + 1) / 2 : p.tiles * p.tiles;
-    const double work = 2.0 * TM * TN * (double)npad * (double)npairs * (double)total;
     cudaError_t rc;
     void* tok = nullptr;
-    if (!slice_gemm_legacy() && sync != nullptr) {
-        rc = cudaFuncSetAttribute(ozaki_tc_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    if (slice_tile() == 256) {  // 128 x 256 output tiles
+        if (!make_map(&ma, Asl, npad, SA, TM, 1) || !make_map(&mb, Xsl, npad, SB, WN, 1)) return cudaErrorInvalidValue;
+        const int sm = W_NSTAGE * W_STAGE;
+        rc = cudaFuncSetAttribute(ozaki_tc_wide, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
         if (rc != cudaSuccess) return rc;
-        int dev = 0, sms = 0, occ = 0;
-        rc = cudaGetDevice(&dev);
-        if (rc == cudaSuccess) rc = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (rc == cudaSuccess)
-            rc = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ozaki_tc_persistent, NTHREADS, sm);
-        if (rc != cudaSuccess) return rc;
-        if (occ < 1) return cudaErrorInvalidConfiguration;
-        const int grid = total < sms ? total : sms;  // one CTA per SM: every CTA resident
-        rc = cudaMemsetAsync(sync, 0, sizeof(int), s);
-        if (rc != cudaSuccess) return rc;
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3((unsigned)grid);
-        cfg.blockDim = dim3(NTHREADS);
-        cfg.dynamicSmemBytes = (size_t)sm;
-        cfg.stream = s;
-        cudaLaunchAttribute attr[1];
-        attr[0].id = cudaLaunchAttributeCooperative;  // the wave barrier needs all CTAs resident
-        attr[0].val.cooperative = 1;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
+        const int tb_m = (int)(npad / TM), tb_n = (int)(npad / WN);
+        const int grid = lower ? (tb_m / 2) * (tb_m / 2 + 1) : tb_m * tb_n;
         timing_begin(SPDINV_TIMED_SLICE_GEMM, s, &tok);
-        rc = cudaLaunchKernelEx(&cfg, ozaki_tc_persistent, ma, mb, p);
-        if (rc == cudaSuccess) {
-            timing_end(SPDINV_TIMED_SLICE_GEMM, s, tok, work);
-            return cudaSuccess;
-        }
-        if (rc != cudaErrorCooperativeLaunchTooLarge) return rc;
-        (void)cudaGetLastError();  // not resident together (a shared GPU): one CTA per tile instead
-        timing_end(SPDINV_TIMED_SLICE_GEMM, s, tok, 0.0);
+        ozaki_tc_wide<<<(unsigned)grid, NTHREADS, sm, s>>>(ma, mb, p);
+        rc = cudaGetLastError();
+        timing_end(SPDINV_TIMED_SLICE_GEMM, s, tok, 2.0 * TM * WN * (double)npad * (double)npairs * (double)grid);
+        return rc;
     }
+    if (!make_map(&ma, Asl, npad, SA, TM, ATOMS) || !make_map(&mb, Xsl, npad, SB, TN, ATOMS))
+        return cudaErrorInvalidValue;
+    const int sm = NSTAGE * STAGE_BYTES;
     rc = cudaFuncSetAttribute(ozaki_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     if (rc != cudaSuccess) return rc;
+    const int grid = lower ? p.tiles * (p.tiles + 1) / 2 : p.tiles * p.tiles;
     timing_begin(SPDINV_TIMED_SLICE_GEMM, s, &tok);
-    ozaki_tc_kernel<<<(unsigned)total, NTHREADS, sm, s>>>(ma, mb, p);
+    ozaki_tc_kernel<<<(unsigned)grid, NTHREADS, sm, s>>>(ma, mb, p);
     rc = cudaGetLastError();
-    timing_end(SPDINV_TIMED_SLICE_GEMM, s, tok, work);
+    timing_end(SPDINV_TIMED_SLICE_GEMM, s, tok, 2.0 * TM * TN * (double)npad * (double)npairs * (double)grid);
     return rc;
 }
 

@@ -123,10 +123,10 @@ __device__ __forceinline__ void tile_mma(Acc<B>& acc, const double* P, const dou
     }
 }
 
-// Zero the strictly upper part of a b x b tile.
-template <int B>
+// Zero the strictly upper part of a b x b tile (NT threads).
+template <int B, int NT = kThreads>
 __device__ __forceinline__ void tile_zero_upper(double* T) {
-    for (int idx = threadIdx.x; idx < B * B; idx += kThreads) {
+    for (int idx = threadIdx.x; idx < B * B; idx += NT) {
         const int r = idx % B, c = idx / B;
         if (r < c) T[idx] = 0.0;
     }
@@ -136,9 +136,10 @@ __device__ __forceinline__ void tile_zero_upper(double* T) {
 // (right-looking column sweep).  Returns 0, or c+1 for the first local column
 // c whose pivot is not > 0 (or is NaN); the tile is then partly updated.
 // Must be called by all threads; the return value is uniform.
-template <int B>
+template <int B, int NT = kThreads>
 __device__ int tile_potrf(double* T, int* s_fail) {
-    constexpr int RS = kThreads / B;  // threads per row (2 for b=64, 4 for b=32)
+    constexpr int RS = NT / B;  // threads per row (2 for b=64, 4 for b=32 with 128 threads)
+    static_assert(RS >= 1 && NT % B == 0, "whole rows per thread group");
     const int r = threadIdx.x % B, cs = threadIdx.x / B;
     if (threadIdx.x == 0) *s_fail = 0;
     cta_sync();
@@ -165,10 +166,11 @@ __device__ int tile_potrf(double* T, int* s_fail) {
 // Inverse of a lower-triangular, non-singular b x b tile, in place
 // (column sweep from the last column, as in LAPACK's unblocked trti2):
 //   X_jj = 1/L_jj,  X_ij = -(sum_{k=j+1..i} X_ik L_kj) X_jj   (i > j).
-// tmp: b doubles of shared scratch.  The strictly upper part is not touched.
-template <int B>
+// tmp: NT doubles of shared scratch.  The strictly upper part is not touched.
+template <int B, int NT = kThreads>
 __device__ void tile_trtri(double* T, double* tmp) {
-    constexpr int RS = kThreads / B;
+    constexpr int RS = NT / B;
+    static_assert(RS >= 1 && NT % B == 0, "whole rows per thread group");
     const int r = threadIdx.x % B, cs = threadIdx.x / B;
     cta_sync();
     for (int j = B - 1; j >= 0; --j) {

@@ -261,7 +261,8 @@ def spd_inverse(A):
 
 
 TRACE_DTYPE = [("task", "<u4"), ("sm", "<u4"), ("ticket", "<u4"), ("cta", "<u4"), ("t_start_ns", "<u8"),
-               ("t_end_ns", "<u8")]
+               ("t_end_ns", "<u8"), ("t_wait_ns", "<u8"), ("reserved", "<u8")]
+TRACE_RECORD_BYTES = 48
 
 
 def traced_potri_(A, capacity=None, **kw):
@@ -275,7 +276,7 @@ def traced_potri_(A, capacity=None, **kw):
         st, tasks, _ = L.spdinv_plan_tasks(max(n, 1), tile, 0)
         _check(st, "spdinv_plan_tasks")
         capacity = max(len(tasks), 1) + 4096  # room for a split variant's segments
-    buf = torch.zeros(capacity * 32, dtype=torch.uint8, device=A.device)
+    buf = torch.zeros(capacity * TRACE_RECORD_BYTES, dtype=torch.uint8, device=A.device)
     _check(L.spdinv_set_trace(buf.data_ptr(), capacity), "spdinv_set_trace")
     try:
         info = potri_(A, **kw)

@@ -333,3 +333,42 @@ def test_poisoned_stores_are_never_read_unwritten(T, gpu, n):
         assert np.max(np.abs(d - np.diag(ref)) / np.abs(np.diag(ref))) <= 1e-10
     finally:
         L.spdinv_set_debug_flags(old)
+
+
+@pytest.mark.parametrize("n", [1, 100, 128, 129, 300, 513, 1000])
+def test_potri_tile128_vs_oracle(T, gpu, n):
+    """Tile 128 (256-thread CTAs, operands streamed in 32-deep slabs through
+    2-D tensor maps) against the oracle, at the FP64 gates."""
+    A, _, _ = si.spectral_spd(n, 1e4, seed=si.SEED_BASE + 3 * n)
+    dA = to_dev(A, gpu, lda=n + 1)
+    upper = np.triu(A, 1)
+    info = T.potri_(dA, tile=128)
+    _sync()
+    assert int(info.item()) == 0
+    got = dA.cpu().numpy()
+    assert np.array_equal(np.triu(got, 1), upper)
+    X = full_from_lower(np.tril(got))
+    M, _ = oracle.potri(A)
+    assert oracle.rel_frobenius(X, oracle.symmetrize_lower(M)) <= 1e-10
+    assert oracle.lapack_ratio(A, X) <= 10
+
+
+@pytest.mark.parametrize("n", [5, 300, 1000])
+def test_potri_tile128_integer_bitwise_and_info(T, gpu, n):
+    A, s = si.bidiag_integer_spd(n, seed=n + 91)
+    dA = to_dev(A, gpu)
+    assert int(T.potri_(dA, tile=128).item()) == 0
+    assert np.array_equal(lower_np(dA), np.tril(cf.bidiag_inverse(s)))
+    B, _, _ = si.spectral_spd(n, 1e2, seed=n)
+    B[n // 2, n // 2] = -1.0
+    _, oinfo = oracle.potri(B)
+    assert int(T.potri_(to_dev(B, gpu), tile=128).item()) == oinfo > 0
+
+
+def test_potri_tile128_only_for_the_whole_inversion(T, gpu):
+    import torch
+    from paper_1002_4057_gb300 import _lib as L
+    o = L.spdinv_opts(128, 0, 0, 0, 0.0, -1, 0, 0, L.SPDINV_VARIANT_UUU, 0)
+    dA = to_dev(np.eye(256), gpu)
+    assert L.spdinv_potri_ex(256, dA.data_ptr(), 256, o, None, torch.cuda.current_stream().cuda_stream) == \
+        L.SPDINV_ERR_UNSUPPORTED

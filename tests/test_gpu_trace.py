@@ -43,6 +43,7 @@ def test_trace_records_every_task_in_dependency_order(gpu, n, b):
     assert np.array_equal(rec["task"], np.array(tasks, dtype=np.uint32))
     assert np.array_equal(rec["ticket"], np.arange(len(tasks)))
     assert np.all(rec["t_end_ns"] >= rec["t_start_ns"]) and np.all(rec["t_start_ns"] > 0)
+    assert np.all(rec["t_wait_ns"] <= rec["t_end_ns"] - rec["t_start_ns"])
     t = (n + b - 1) // b
     end = {}
     for r in rec:
@@ -57,7 +58,7 @@ def test_trace_buffer_too_small_is_refused(gpu):
     from paper_1002_4057_gb300 import _lib as L
     n = 256
     dA = to_dev(np.eye(n), gpu)
-    buf = torch.zeros(32 * 4, dtype=torch.uint8, device=gpu)
+    buf = torch.zeros(48 * 4, dtype=torch.uint8, device=gpu)
     assert L.spdinv_set_trace(buf.data_ptr(), 4) == L.SPDINV_OK
     try:
         st = L.spdinv_potri(n, dA.data_ptr(), n, None, torch.cuda.current_stream().cuda_stream)
