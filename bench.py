@@ -28,7 +28,6 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "POTRI Gflop/s (n^3/inv) & % tensor peak; mixed vs FP64 speedup at 1e-10 err"
-TRAFFIC_N16384_B32 = 793344264192 + 3259657472  # DRAM bytes read + written, one launch (ncu)
 BF16_NOMINAL_TFLOPS = 2250.0
 # precision of the mixed-precision records: SPDINV_PREC_MIXED_TF32X3, the bulk
 # tile updates as 3xTF32 tensor-core products (more accurate than FP32 FMA on
@@ -367,13 +366,13 @@ def mixed_record(n, A_main, Q, lam_main, cond_main, ms64, stream, dev, peaks, re
             "speedup_vs_fp64_at_1e-10": round(ms64 / t, 3) if err <= 1e-10 else None,
             "speedup_vs_fp64": round(ms64 / t, 3),
             "slice_gemm_roofline": {
-                "bound": "tensor", "kernel": "ozaki_tc_kernel (tcgen05 kind::f16, BF16 slices, FP32 accumulator)",
+                "bound": "tensor", "kernel": "ozaki_tc_wide (tcgen05 kind::f16, BF16 slices, 128 x 256 FP32 accumulator in TMEM)",
                 "launches_per_inversion": glaunch / reps, "ms_per_inversion": round(gms / reps, 2),
                 "achieved": round(ach, 2) if ach else None, "peak": bf16, "unit": "TFLOP/s",
                 "frac": round(ach / bf16, 4) if ach else None,
                 "frac_of_sustained": round(ach / bf16_sus, 4) if (ach and bf16_sus) else None,
                 "peak_note": "bf16_tflops (%s, burst); the sustained figure is %s" % (src, bf16_sus),
-                "work": "2 * 128 * 128 * K flops per launched output tile and slice pair (K: order padded to 256)"},
+                "work": "2 * 128 * 256 * K flops per launched 128 x 256 output tile and slice pair (K: order padded to 256)"},
             "fp32_dag": {"kernel": "potri_mixed_persistent<64> (bulk updates 3xTF32 on mma.sync)",
                          "ms_per_inversion": round(dms / reps, 2),
                          "achieved_tflops": round(dag_rate, 3) if dag_rate else None,
@@ -1046,18 +1045,23 @@ def main():
                      "did not run: --no-extra or rank > 0)" % src)
         peak_src = "derived from bf16_tflops (%s)" % src
     frac = achieved_tf / peak_tf
+    # the tile products run on the FP64 FMA pipe (not the tensor pipe): the peak is
+    # that pipe's rate, measured by the probe above (2 FP64 FMAs per clock per SM,
+    # 152 SMs, 2 flops each: 1.259 TFLOP/s at 2070 MHz from the unit counts)
     roofline = {
-        "bound": "tensor", "achieved": round(achieved_tf, 4), "peak": round(peak_tf, 4), "unit": "TFLOP/s",
+        "bound": "alu", "achieved": round(achieved_tf, 4), "peak": round(peak_tf, 4), "unit": "TFLOP/s",
         "frac": round(frac, 4), "peak_source": peak_src,
-        # dram__bytes_read.sum + dram__bytes_write.sum of one timed launch of this kernel at
-        # n = 16384, tile 32 (an ncu capture of this command with --profile-timed); other
-        # sizes and tiles were not captured at full size
-        "traffic": TRAFFIC_N16384_B32 if (n, b) == (16384, 32) else None,
+        "peak_from_units": round(152 * 2 * 2 * (clocks.get("sm_mhz") or 2070.0) * 1e6 / 1e12, 4),
+        # no DRAM capture of this build at this size: a multi-pass counter capture of a
+        # seconds-long launch is above the safe capture size, and the traffic does not
+        # grow in proportion to n (the working set fits L2 up to n ~ 4096), so a small
+        # capture cannot be scaled to this launch
+        "traffic": None,
         "traffic_unit": "bytes per launch",
-        "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one timed launch of this "
-                           "kernel at this configuration, profiles/potri_fp64_persistent_n16384_b32_dram.md "
-                           "(not measured in this run)") if (n, b) == (16384, 32) else None,
-        "kernel": "potri_fp64_persistent<%d> (FP64 DMMA m8n8k4)" % b,
+        "traffic_note": ("not captured for this build at this size; at n = 4096 one launch moves 306 MB "
+                         "(profiles/potri_fp64_persistent_n4096_b32_full.md); the chain tasks' tile reads, "
+                         "about t^3 tiles of 8 b^2 bytes, bound it from above at larger n"),
+        "kernel": "potri_fp64_persistent<%d> (FP64 FMA register blocks)" % b,
         "peak_note": peak_note,
         "executed_flops_note": "the kernel executes about n^3 (1 + 5/t) flops (full-tile SYRK chains, "
                                "warp-granular triangular skipping); achieved counts n^3",
