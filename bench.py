@@ -45,7 +45,7 @@ def parse():
     ap.add_argument("--n", type=int, default=16384)
     ap.add_argument("--tile", type=int, default=32)
     ap.add_argument("--ctas-per-sm", type=int, default=0)
-    ap.add_argument("--plan-order", default="bottom_level", choices=["bottom_level", "alap"],
+    ap.add_argument("--plan-order", default="alap", choices=["bottom_level", "alap"],
                     help="ticket order of the persistent kernel's plans (spdinv_set_plan_order)")
     ap.add_argument("--cond", type=float, default=1e4)
     ap.add_argument("--e2e-steps", type=int, default=3)
@@ -853,9 +853,9 @@ def main():
     args = parse()
     PROFILE_TIMED = args.profile_timed
     rank, world, local = dist_env()
-    if args.plan_order != "bottom_level" and args.impl != "reference":
+    if args.impl != "reference":
         from paper_1002_4057_gb300 import _lib as L
-        L.spdinv_set_plan_order(L.SPDINV_PLAN_ALAP)
+        L.spdinv_set_plan_order(L.SPDINV_PLAN_ALAP if args.plan_order == "alap" else L.SPDINV_PLAN_BOTTOM_LEVEL)
     if args.impl == "reference":
         run_reference(args, rank, world)
         return

@@ -448,13 +448,16 @@ spdinv_status spdinv_plan_check(int t, int steps, int64_t out[3]) {
     if (t < 1 || t > 16383) return SPDINV_ERR_N;
     if (steps < 0 || steps > 4) return SPDINV_ERR_UNSUPPORTED;
     if (!out) return SPDINV_ERR_NULL;
-    const ExecPlan a = build_exec_plan(t, steps, false), b = build_exec_plan(t, steps, true);
-    int64_t diff = 0;
-    for (size_t m = 0; m < a.order.size() && m < b.order.size(); ++m) diff += a.order[m] != b.order[m];
-    out[0] = (int64_t)a.order.size();
-    out[1] = diff + (int64_t)(a.order.size() > b.order.size() ? a.order.size() - b.order.size()
-                                                               : b.order.size() - a.order.size());
-    out[2] = (a.crit != b.crit || a.work != b.work) ? 1 : 0;
+    out[1] = out[2] = 0;
+    for (int order : {(int)ORDER_BOTTOM_LEVEL, (int)ORDER_ALAP}) {
+        const ExecPlan a = build_exec_plan(t, steps, false, order), b = build_exec_plan(t, steps, true, order);
+        int64_t diff = 0;
+        for (size_t m = 0; m < a.order.size() && m < b.order.size(); ++m) diff += a.order[m] != b.order[m];
+        out[0] = (int64_t)a.order.size();
+        out[1] += diff + (int64_t)(a.order.size() > b.order.size() ? a.order.size() - b.order.size()
+                                                                    : b.order.size() - a.order.size());
+        if (a.crit != b.crit || a.work != b.work) out[2] = 1;
+    }
     return SPDINV_OK;
 }
 

@@ -227,6 +227,178 @@ struct TaskIndex {
     int32_t& at(uint32_t kind, int i, int j) { return id[((size_t)kind * t + i) * t + j]; }
 };
 
+// ALAP ticket order (ORDER_ALAP) by the same three passes as the element walk
+// in build_exec_plan's exhaustive path -- earliest finish forward, latest
+// finish backward, keys forward -- with the same operations in the same
+// order, so the same doubles and the same order.  Each pass walks a task's
+// chain over rows and columns of the L and X task grids; the grids are kept
+// both row-major and column-major so that every walk is sequential in memory.
+void alap_order_grid(int t, const std::vector<uint32_t>& seq, bool s1, bool s2, bool s2diag,
+                     std::vector<uint32_t>& perm) {
+    const size_t N = seq.size(), T = (size_t)t;
+    const bool hasL = s1, hasX = s2, hasD = s1 || s2diag;
+    std::vector<double> Lr(T * T), Lc(T * T), Xr(T * T), Xc(T * T), D(T);
+    auto rm = [T](int i, int j) { return (size_t)i * T + (size_t)j; };  // row-major (i, j)
+    auto cm = [T](int i, int j) { return (size_t)j * T + (size_t)i; };  // column-major (i, j)
+    // One forward pass.  step(v, p) folds a producer's value into v; elem(v)
+    // ends an element of cost c; store keeps a task's value for its readers.
+    auto forward = [&](std::vector<double>& val, auto&& init, auto&& fold, auto&& end_elem) {
+        std::fill(D.begin(), D.end(), 0.0);
+        for (size_t r = 0; r < N; ++r) {
+            const uint32_t e = seq[r];
+            const int i = (int)task_i(e), j = (int)task_j(e);
+            double v = init(r);
+            switch (task_kind(e)) {
+                case K_S1_DIAG:
+                    for (int k = 0; k < j; ++k) {
+                        if (hasL) v = fold(v, Lr[rm(j, k)]);
+                        v = end_elem(v, 1.0);
+                    }
+                    v = end_elem(v, 0.7);
+                    if (hasD) D[j] = v;
+                    break;
+                case K_S1_OFF:
+                    for (int k = 0; k < j; ++k) {
+                        if (hasL) v = fold(fold(v, Lr[rm(i, k)]), Lr[rm(j, k)]);
+                        v = end_elem(v, 1.0);
+                    }
+                    if (hasD) v = fold(v, D[j]);
+                    v = end_elem(v, 1.0);
+                    Lr[rm(i, j)] = Lc[cm(i, j)] = v;
+                    break;
+                case K_S2_DIAG:
+                    v = end_elem(v, 0.4);
+                    if (!s1) D[j] = v;
+                    break;
+                case K_S2_OFF:
+                    if (hasD) v = fold(v, D[i]);
+                    if (hasL) v = fold(v, Lr[rm(i, j)]);
+                    v = end_elem(v, 1.0);
+                    for (int k = i - 1; k > j; --k) {
+                        v = fold(v, Xr[rm(i, k)]);
+                        if (hasL) v = fold(v, Lc[cm(k, j)]);
+                        v = end_elem(v, 1.0);
+                    }
+                    if (hasD) v = fold(v, D[j]);
+                    v = end_elem(v, 1.0);
+                    Xr[rm(i, j)] = Xc[cm(i, j)] = v;
+                    break;
+                case K_S3_DIAG:
+                    if (hasD) v = fold(v, D[i]);
+                    v = end_elem(v, 1.0);
+                    for (int k = i + 1; k < t; ++k) {
+                        if (hasX) v = fold(v, Xc[cm(k, i)]);
+                        v = end_elem(v, 1.0);
+                    }
+                    break;
+                default:  // K_S3_OFF
+                    if (hasD) v = fold(v, D[i]);
+                    if (hasX) v = fold(v, Xr[rm(i, j)]);
+                    v = end_elem(v, 1.0);
+                    for (int k = i + 1; k < t; ++k) {
+                        if (hasX) v = fold(fold(v, Xc[cm(k, i)]), Xc[cm(k, j)]);
+                        v = end_elem(v, 1.0);
+                    }
+                    break;
+            }
+            val[r] = v;
+        }
+    };
+    auto vmax = [](double a, double b) { return std::max(a, b); };
+    // Earliest finish with unlimited CTAs (seq is topological).
+    std::vector<double> fin(N);
+    forward(
+        fin, [](size_t) { return 0.0; }, vmax, [](double v, double c) { return v + c; });
+    double span = 0.0;
+    for (size_t r = 0; r < N; ++r) span = std::max(span, fin[r]);
+    // Latest finish that keeps the span: the grids now hold, per produced
+    // tile, the least latest start among the elements that read it (row walks
+    // into the row-major copy, column walks into the column-major one).
+    std::fill(Lr.begin(), Lr.end(), span);
+    std::fill(Lc.begin(), Lc.end(), span);
+    std::fill(Xr.begin(), Xr.end(), span);
+    std::fill(Xc.begin(), Xc.end(), span);
+    std::fill(D.begin(), D.end(), span);
+    std::vector<double> late(N, span);
+    auto lower = [](double& a, double v) { a = std::min(a, v); };
+    for (size_t r = N; r-- > 0;) {
+        const uint32_t e = seq[r];
+        const int i = (int)task_i(e), j = (int)task_j(e);
+        double tail = span;
+        switch (task_kind(e)) {
+            case K_S1_DIAG:
+                if (hasD) tail = D[j];
+                late[r] = tail;
+                tail -= 0.7;
+                for (int k = j - 1; k >= 0; --k) {
+                    tail -= 1.0;
+                    if (hasL) lower(Lr[rm(j, k)], tail);
+                }
+                break;
+            case K_S1_OFF:
+                tail = std::min(Lr[rm(i, j)], Lc[cm(i, j)]);
+                late[r] = tail;
+                tail -= 1.0;
+                if (hasD) lower(D[j], tail);
+                for (int k = j - 1; k >= 0; --k) {
+                    tail -= 1.0;
+                    if (hasL) {
+                        lower(Lr[rm(i, k)], tail);
+                        lower(Lr[rm(j, k)], tail);
+                    }
+                }
+                break;
+            case K_S2_DIAG:
+                if (!s1) tail = D[j];
+                late[r] = tail;
+                break;
+            case K_S2_OFF:
+                tail = std::min(Xr[rm(i, j)], Xc[cm(i, j)]);
+                late[r] = tail;
+                tail -= 1.0;
+                if (hasD) lower(D[j], tail);
+                for (int k = j + 1; k < i; ++k) {
+                    tail -= 1.0;
+                    lower(Xr[rm(i, k)], tail);
+                    if (hasL) lower(Lc[cm(k, j)], tail);
+                }
+                tail -= 1.0;
+                if (hasD) lower(D[i], tail);
+                if (hasL) lower(Lr[rm(i, j)], tail);
+                break;
+            case K_S3_DIAG:
+                late[r] = tail;
+                for (int k = t - 1; k > i; --k) {
+                    tail -= 1.0;
+                    if (hasX) lower(Xc[cm(k, i)], tail);
+                }
+                tail -= 1.0;
+                if (hasD) lower(D[i], tail);
+                break;
+            default:  // K_S3_OFF
+                late[r] = tail;
+                for (int k = t - 1; k > i; --k) {
+                    tail -= 1.0;
+                    if (hasX) {
+                        lower(Xc[cm(k, i)], tail);
+                        lower(Xc[cm(k, j)], tail);
+                    }
+                }
+                tail -= 1.0;
+                if (hasD) lower(D[i], tail);
+                if (hasX) lower(Xr[rm(i, j)], tail);
+                break;
+        }
+    }
+    // Keys raised to the producers' keys keep the sorted order topological
+    // (ties go to the earlier task of Algorithm 1's order).
+    std::vector<double> key(N);
+    forward(
+        key, [&](size_t r) { return late[r]; }, vmax, [](double v, double) { return v; });
+    std::iota(perm.begin(), perm.end(), 0u);
+    std::stable_sort(perm.begin(), perm.end(), [&](uint32_t a, uint32_t b) { return key[a] < key[b]; });
+}
+
 }  // namespace
 
 ExecPlan build_exec_plan(int t, int steps, bool exhaustive, int order) {
@@ -404,7 +576,9 @@ ExecPlan build_exec_plan(int t, int steps, bool exhaustive, int order) {
     p.crit = N ? bl[perm[0]] : 0.0;
     p.work = work;
 
-    if (order == ORDER_ALAP && N) {
+    if (order == ORDER_ALAP && N && !exhaustive) {
+        alap_order_grid(t, seq, s1, s2, s2diag, perm);
+    } else if (order == ORDER_ALAP && N) {
         // Each task's chain elements in the kernel's order: up to two producer
         // tasks (-1: ready at launch) and a cost; the costs add up to cost().
         struct Elem {
@@ -643,8 +817,9 @@ namespace {
 std::atomic<int>& plan_order_setting() {
     static std::atomic<int> order{[] {
         const char* env = std::getenv("SPDINV_PLAN_ORDER");
-        if (env && (std::strcmp(env, "alap") == 0 || std::strcmp(env, "1") == 0)) return (int)ORDER_ALAP;
-        return (int)ORDER_BOTTOM_LEVEL;
+        if (env && (std::strcmp(env, "bottom_level") == 0 || std::strcmp(env, "0") == 0))
+            return (int)ORDER_BOTTOM_LEVEL;
+        return (int)ORDER_ALAP;
     }()};
     return order;
 }

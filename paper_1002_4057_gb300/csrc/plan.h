@@ -75,16 +75,19 @@ struct ExecPlan {
 // Ticket order of a plan (both are topological, so any grid is free of
 // deadlock, and the result does not depend on the order: every output tile
 // keeps its own accumulation order).
-//   ORDER_BOTTOM_LEVEL  decreasing task-level bottom level (the default);
+//   ORDER_BOTTOM_LEVEL  decreasing task-level bottom level;
 //   ORDER_ALAP          increasing latest finish time of each task in the
 //                       element-pipelined schedule on unlimited CTAs (each
 //                       chain element starts when its own inputs are final),
 //                       raised to the largest key among the task's producers
-//                       so that the order stays topological.  O(t^3).
+//                       so that the order stays topological.  O(t^3)
+//                       chain elements, walked along rows and columns of
+//                       the task grids (exhaustive: producer by producer).
 enum PlanOrder { ORDER_BOTTOM_LEVEL = 0, ORDER_ALAP = 1 };
 
-// The order the library plans with: ORDER_BOTTOM_LEVEL unless
-// SPDINV_PLAN_ORDER=alap (or 1) in the environment or spdinv_set_plan_order.
+// The order the library plans with: ORDER_ALAP unless
+// SPDINV_PLAN_ORDER=bottom_level (or 0) in the environment or
+// spdinv_set_plan_order says otherwise.
 int current_plan_order();
 int set_plan_order(int order);  // returns the previous one
 

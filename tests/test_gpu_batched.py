@@ -30,7 +30,14 @@ def _check(hs, ds, tol):
     return worst
 
 
-@pytest.mark.parametrize("dtype_name,tol", [("float64", 1e-10), ("float32", 2e-4)])
+# FP32: the inputs are the FP64 matrices rounded to FP32 (cond <= ~41 for
+# B B^T/n + 0.1 I), so the error against the FP64 oracle is of order
+# cond * 2^-24 * sqrt(n); the worst measured over these tests on a GB300 is
+# 1.42e-6, and the tolerance is about 4x that.
+F32_TOL = 6e-6
+
+
+@pytest.mark.parametrize("dtype_name,tol", [("float64", 1e-10), ("float32", F32_TOL)])
 def test_batched_uneven_vs_oracle(gpu, dtype_name, tol):
     import torch
     from paper_1002_4057_gb300 import torch_api as T
@@ -149,7 +156,7 @@ def test_sharded_batch_matches_whole_batch(gpu, dtype_name, tol):
         a = full_from_lower(np.tril(got[k].double().cpu().numpy()))
         b = full_from_lower(np.tril(whole[k].double().cpu().numpy()))
         assert oracle.rel_frobenius(a, b) <= tol, (k, sizes[k])
-    _check(hs, got, 1e-10 if dtype == torch.float64 else 2e-4)
+    _check(hs, got, 1e-10 if dtype == torch.float64 else F32_TOL)
 
 @pytest.mark.slow
 def test_batched_config_4096_sampled(gpu):
@@ -160,7 +167,7 @@ def test_batched_config_4096_sampled(gpu):
     from paper_1002_4057_gb300 import torch_api as T
     sizes = si.batch_sizes(4096, 16, 256, seed=si.SEED_BASE + 3)
     hs = si.wishart_batch(sizes, 0.1, si.SEED_BASE + 3)
-    for dtype, tol, ptol in ((torch.float64, 1e-10, 1e-11), (torch.float32, 2e-4, 1e-3)):
+    for dtype, tol, ptol in ((torch.float64, 1e-10, 1e-11), (torch.float32, F32_TOL, 1e-3)):
         ds = [to_dev(A, gpu).to(dtype) for A in hs]
         info = T.potri_batched_(ds)
         torch.cuda.synchronize()

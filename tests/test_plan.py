@@ -312,3 +312,22 @@ def test_plan_order_setter():
     finally:
         L.spdinv_set_plan_order(old)
 
+
+
+@pytest.mark.parametrize("env,expected", [(None, 1), ("bottom_level", 0), ("0", 0), ("alap", 1)])
+def test_plan_order_default_and_environment(env, expected):
+    """The ALAP order is the default; SPDINV_PLAN_ORDER=bottom_level (or 0)
+    selects the bottom-level order for the whole process."""
+    import os
+    import subprocess
+    import sys
+    e = dict(os.environ)
+    e.pop("SPDINV_PLAN_ORDER", None)
+    if env is not None:
+        e["SPDINV_PLAN_ORDER"] = env
+    code = ("from paper_1002_4057_gb300 import _lib as L; "
+            "print(L.spdinv_set_plan_order(L.SPDINV_PLAN_BOTTOM_LEVEL))")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-c", code], cwd=root, env=e, capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, r.stderr
+    assert int(r.stdout.strip().splitlines()[-1]) == expected
