@@ -126,6 +126,105 @@ __device__ __forceinline__ bool fetch(PCtx& c, const int* f0, const int* f1, con
     return mbar_wait_bounded(c);
 }
 
+// Double-buffered update chains.  Two sets of tile buffers, each with its own
+// mbarrier; element e of a chain lands in set e & 1.  While element e is
+// multiplied, the copy of element e + 1 is already in flight when its input
+// flags were raised by the time element e started (thread 0 checks them once,
+// without waiting); otherwise thread 0 waits for them (bounded) after element
+// e, as the single-buffered fetch does.  Every issued copy is waited exactly
+// once, also on the abort path, so no copy lands after the CTA has left.
+struct Chain2 {
+    unsigned char* base;  // set s, operand o at base + (2 s + o) * stride
+    uint32_t stride;      // bytes per tile buffer
+    uint64_t* bar;        // [2] mbarriers
+    uint32_t phase;       // bit s: the parity set s waits for next
+    int* s_state;         // shared [3]: [0] thread 0's verdict, [1..2] copy issued into set 0 / 1
+    __device__ __forceinline__ void* buf(int s, int o) const { return base + (2 * s + o) * stride; }
+};
+
+struct ChainElem {
+    const int* f0;
+    const int* f1;
+    const void* g0;
+    const void* g1;
+};
+
+// Thread 0: copy element x into set s (flags already final).
+__device__ __forceinline__ void chain_issue(Chain2& ch, int s, const ChainElem& x, uint32_t bytes) {
+    fence_proxy_async_global();
+    fence_proxy_async_shared();
+    mbar_arrive_expect_tx(&ch.bar[s], (x.g0 ? bytes : 0u) + (x.g1 ? bytes : 0u));
+    if (x.g0) bulk_g2s(ch.buf(s, 0), x.g0, bytes, &ch.bar[s]);
+    if (x.g1) bulk_g2s(ch.buf(s, 1), x.g1, bytes, &ch.bar[s]);
+}
+
+// All threads: wait (bounded) for the copy into set s.
+__device__ __forceinline__ bool chain_wait(Chain2& ch, int s, int* ctrl) {
+    const uint64_t t0 = globaltimer_ns();
+    while (!mbar_try_wait(&ch.bar[s], (ch.phase >> s) & 1u)) {
+        if ((long long)(globaltimer_ns() - t0) > 2000000000LL) {
+            if (threadIdx.x == 0) raise_error(ctrl, SPDINV_ERR_TIMEOUT);
+            return false;
+        }
+    }
+    ch.phase ^= 1u << s;
+    return true;
+}
+
+// Runs a chain of m >= 1 elements: elem(e) names element e's flags and
+// tiles, mul(e, Ta, Tb) consumes it from shared memory (all threads).  The
+// buffers of both sets may be written by generic stores before the call
+// (each thread fences them here).  false = stop (abort or timeout), with no
+// copy in flight.
+template <class Elem, class Mul>
+__device__ __forceinline__ bool run_chain(Chain2& ch, PCtx& c, int m, uint32_t bytes, Elem&& elem, Mul&& mul) {
+    fence_proxy_async_shared();
+    cta_sync();
+    if (threadIdx.x == 0) {
+        const ChainElem x = elem(0);
+        const uint64_t w0 = c.wait_ns ? globaltimer_ns() : 0;
+        const bool ok = wait_flag(x.f0, c.ctrl, c.timeout_ns) && wait_flag(x.f1, c.ctrl, c.timeout_ns);
+        if (c.wait_ns) *c.wait_ns += globaltimer_ns() - w0;
+        if (ok) chain_issue(ch, 0, x, bytes);
+        ch.s_state[0] = ok ? 0 : 1;
+        ch.s_state[1] = ok ? 1 : 0;
+        ch.s_state[2] = 0;
+    }
+    cta_sync();
+    if (ch.s_state[0] != 0) return false;
+    for (int e = 0; e < m; ++e) {
+        const int s = e & 1;
+        bool prefetched = false;  // thread 0 only
+        if (threadIdx.x == 0 && e + 1 < m) {  // prefetch e + 1 if its inputs are final
+            const ChainElem x = elem(e + 1);
+            prefetched = (x.f0 == nullptr || ld_acquire_gpu(x.f0) != 0) &&
+                         (x.f1 == nullptr || ld_acquire_gpu(x.f1) != 0);
+            if (prefetched) chain_issue(ch, s ^ 1, x, bytes);
+            ch.s_state[1 + (s ^ 1)] = prefetched ? 1 : 0;
+        }
+        if (!chain_wait(ch, s, c.ctrl)) {  // (2 s on one copy: the error is raised)
+            if (prefetched) chain_wait(ch, s ^ 1, c.ctrl);  // drain the prefetch, bounded
+            return false;
+        }
+        mul(e, ch.buf(s, 0), ch.buf(s, 1));
+        fence_proxy_async_shared();  // this thread's reads of set s before the next copy into it
+        cta_sync();
+        if (e + 1 < m && ch.s_state[1 + (s ^ 1)] == 0) {
+            if (threadIdx.x == 0) {
+                const ChainElem x = elem(e + 1);
+                const uint64_t w0 = c.wait_ns ? globaltimer_ns() : 0;
+                const bool ok = wait_flag(x.f0, c.ctrl, c.timeout_ns) && wait_flag(x.f1, c.ctrl, c.timeout_ns);
+                if (c.wait_ns) *c.wait_ns += globaltimer_ns() - w0;
+                if (ok) chain_issue(ch, s ^ 1, x, bytes);
+                ch.s_state[0] = ok ? 0 : 1;
+            }
+            cta_sync();
+            if (ch.s_state[0] != 0) return false;  // nothing in flight: e + 1 was not issued
+        }
+    }
+    return true;
+}
+
 // All threads: make the CTA's global writes visible -- to the generic proxy
 // and to the async proxy of the consumers' bulk copies -- then raise the flag.
 __device__ __forceinline__ void publish(PCtx& c, int* flag, int ticket) {

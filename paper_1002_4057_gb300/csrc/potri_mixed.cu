@@ -57,11 +57,6 @@ __host__ __device__ constexpr int padded_tile() {
 }
 
 template <int B>
-__device__ __forceinline__ bool fetch32(PCtx& c, const int* f0, const int* f1, const float* g0, const float* g1) {
-    return fetch(c, f0, f1, g0, g1, (uint32_t)(padded_tile<B>() * sizeof(float)));
-}
-
-template <int B>
 __device__ __forceinline__ const float* tB(const KParamsMixed& p, int i, int j) {
     return p.Bw + ((int64_t)i * (i - 1) / 2 + j) * (int64_t)padded_tile<B>();
 }
@@ -123,38 +118,67 @@ __device__ void store_X(const KParamsMixed& p, int ti, int tj, const float* T) {
 // ACC: the bulk tile products' accumulator, which selects their arithmetic --
 // Acc32<B> FP32 FMA on the CUDA cores, AccTC<B, SplitTF32> three TF32 MMAs
 // (3xTF32), AccTC<B, SplitBF16> three BF16 MMAs (BF16x3).
+//
+// Shared memory: two sets of two tile buffers for the double-buffered update
+// chains (run_chain); the FP64 diagonal tile of the Step-1 diagonal task and
+// its scratch reuse the second set once that task's chain is done.
+template <int B>
+__host__ __device__ constexpr int mixed_tile_bytes() {
+    return round_up128(padded_tile<B>() * (int)sizeof(float));
+}
+template <int B>
+__host__ __device__ constexpr int mixed_smem_bytes() {
+    return 2 * mixed_tile_bytes<B>() + (2 * mixed_tile_bytes<B>() > (B * B + kThreads) * (int)sizeof(double)
+                                            ? 2 * mixed_tile_bytes<B>()
+                                            : (B * B + kThreads) * (int)sizeof(double));
+}
+
 template <int B, class ACC>
 __global__ void __launch_bounds__(kThreads) potri_mixed_persistent(const KParamsMixed prm) {
     unsigned char* const smem_raw = dynamic_smem();
-    __shared__ __align__(8) uint64_t bar;
-    __shared__ int s_task, s_flag, s_fail;
+    __shared__ __align__(8) uint64_t bars[2];
+    __shared__ int s_task, s_fail, s_state[3];
     constexpr int LD = B + 1;
+    constexpr uint32_t kBytes = (uint32_t)(padded_tile<B>() * sizeof(float));
     const KParamsMixed& p = prm;
-    constexpr int kT = round_up128(padded_tile<B>() * (int)sizeof(float));
-    float* const T0 = reinterpret_cast<float*>(smem_raw);  // bulk-copy targets first
+    constexpr int kT = mixed_tile_bytes<B>();
+    float* const T0 = reinterpret_cast<float*>(smem_raw);  // set 0: T0, T1; set 1: T2, T3
     float* const T1 = reinterpret_cast<float*>(smem_raw + kT);
-    double* const Td = reinterpret_cast<double*>(smem_raw + 2 * kT);  // FP64 diagonal tile, stride B
+    float* const T2 = reinterpret_cast<float*>(smem_raw + 2 * kT);
+    float* const T3 = reinterpret_cast<float*>(smem_raw + 3 * kT);
+    double* const Td = reinterpret_cast<double*>(smem_raw + 2 * kT);  // FP64 diagonal tile, stride B (set 1)
     double* const tmpd = Td + B * B;                                   // kThreads doubles
     PCtx c;
     c.T0 = T0;
     c.T1 = T1;
-    c.bar = &bar;
-    c.s_flag = &s_flag;
+    c.bar = nullptr;
+    c.s_flag = nullptr;
     c.phase = 0;
     c.ctrl = p.ctrl;
     c.timeout_ns = p.timeout_ns;
     c.drop_task = p.drop_task;
     c.wait_ns = nullptr;
+    Chain2 ch;
+    ch.base = smem_raw;
+    ch.stride = (uint32_t)kT;
+    ch.bar = bars;
+    ch.phase = 0;
+    ch.s_state = s_state;
     if (threadIdx.x == 0) {
-        mbar_init(&bar, 1);
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
         fence_proxy_async_shared();
     }
     cta_sync();
-    if (!layout_ok(T0, T1, p.Bw, p.Cw, p.Dw, p.ctrl)) return;
+    if (!layout_ok(T0, T2, p.Bw, p.Cw, p.Dw, p.ctrl)) return;
+    if (!layout_ok(T1, T3, p.Bw, p.Cw, p.Dw, p.ctrl)) return;
     const int t = p.t;
     int* const fL = p.flags;
     int* const fX = p.flags + (int64_t)t * t;
     int* const fD = p.flags + 2 * (int64_t)t * t;
+    auto el = [](const int* f0, const int* f1, const float* g0, const float* g1) {
+        return ChainElem{f0, f1, g0, g1};
+    };
 
     for (;;) {
         const int ticket = next_ticket(p.ctrl, p.ntasks, &s_task);
@@ -167,10 +191,13 @@ __global__ void __launch_bounds__(kThreads) potri_mixed_persistent(const KParams
             load_A32<B>(p, j, j, T0, true);
             cta_sync();
             acc_load<B>(acc, T0);
-            for (int k = 0; k < j; ++k) {  // SYRK chain (FP32)
-                if (!fetch32<B>(c, &fL[j * t + k], nullptr, tB<B>(p, j, k), nullptr)) return;
-                tile_mma<B, false, true, true, FULL, FULL>(acc, T0, T0);
-            }
+            if (j > 0 &&
+                !run_chain(ch, c, j, kBytes, [&](int k) { return el(&fL[j * t + k], nullptr, tB<B>(p, j, k), nullptr); },
+                           [&](int, const void* Ta, const void*) {  // SYRK chain (FP32)
+                               const float* A = static_cast<const float*>(Ta);
+                               tile_mma<B, false, true, true, FULL, FULL>(acc, A, A);
+                           }))
+                return;
             cta_sync();
             acc_store<B>(acc, T0);
             cta_sync();
@@ -196,58 +223,97 @@ __global__ void __launch_bounds__(kThreads) potri_mixed_persistent(const KParams
             load_A32<B>(p, i, j, T0, false);
             cta_sync();
             acc_load<B>(acc, T0);
-            for (int k = 0; k < j; ++k) {
-                if (!fetch32<B>(c, &fL[i * t + k], &fL[j * t + k], tB<B>(p, i, k), tB<B>(p, j, k))) return;
-                tile_mma<B, false, true, true, FULL, FULL>(acc, T0, T1);
-            }
-            if (!fetch32<B>(c, &fD[j], nullptr, nullptr, tD<B>(p, j))) return;
-            acc_store<B>(acc, T0);
-            cta_sync();
-            acc_zero<B>(acc);
-            tile_mma<B, false, true, false, FULL, LOWER>(acc, T0, T1);
+            // GEMM chain k < j, then the TRSM as a product with X_jj^T
+            if (!run_chain(
+                    ch, c, j + 1, kBytes,
+                    [&](int k) {
+                        return k < j ? el(&fL[i * t + k], &fL[j * t + k], tB<B>(p, i, k), tB<B>(p, j, k))
+                                     : el(&fD[j], nullptr, nullptr, tD<B>(p, j));
+                    },
+                    [&](int k, const void* Ta, const void* Tb) {
+                        float* P = static_cast<float*>(const_cast<void*>(Ta));
+                        const float* Q = static_cast<const float*>(Tb);
+                        if (k < j) {
+                            tile_mma<B, false, true, true, FULL, FULL>(acc, P, Q);
+                        } else {
+                            acc_store<B>(acc, P);  // P's slot received no copy for this element
+                            cta_sync();
+                            acc_zero<B>(acc);
+                            tile_mma<B, false, true, false, FULL, LOWER>(acc, P, Q);
+                        }
+                    }))
+                return;
             cta_sync();
             acc_store<B>(acc, T0);
             cta_sync();
             store_ws32<B>(const_cast<float*>(tB<B>(p, i, j)), T0);
             publish(c, &fL[i * t + j], ticket);
         } else if (kind == K_S2_OFF) {
-            if (!fetch32<B>(c, &fD[i], &fL[i * t + j], tD<B>(p, i), tB<B>(p, i, j))) return;
             acc_zero<B>(acc);
-            tile_mma<B, false, false, false, LOWER, FULL>(acc, T0, T1);
-            for (int k = i - 1; k > j; --k) {
-                if (!fetch32<B>(c, &fX[i * t + k], &fL[k * t + j], tC<B>(p, i, k), tB<B>(p, k, j))) return;
-                tile_mma<B, false, false, false, FULL, FULL>(acc, T0, T1);
-            }
-            if (!fetch32<B>(c, &fD[j], nullptr, nullptr, tD<B>(p, j))) return;
-            acc_store<B>(acc, T0);
-            cta_sync();
-            acc_zero<B>(acc);
-            tile_mma<B, false, false, true, FULL, LOWER>(acc, T0, T1);
+            const int m = i - j + 1;  // TRMM by X_ii, GEMMs k = i-1 .. j+1, TRMM by -X_jj
+            if (!run_chain(
+                    ch, c, m, kBytes,
+                    [&](int q) {
+                        if (q == 0) return el(&fD[i], &fL[i * t + j], tD<B>(p, i), tB<B>(p, i, j));
+                        if (q == m - 1) return el(&fD[j], nullptr, nullptr, tD<B>(p, j));
+                        const int k = i - q;
+                        return el(&fX[i * t + k], &fL[k * t + j], tC<B>(p, i, k), tB<B>(p, k, j));
+                    },
+                    [&](int q, const void* Ta, const void* Tb) {
+                        float* P = static_cast<float*>(const_cast<void*>(Ta));
+                        const float* Q = static_cast<const float*>(Tb);
+                        if (q == 0) {
+                            tile_mma<B, false, false, false, LOWER, FULL>(acc, P, Q);
+                        } else if (q < m - 1) {
+                            tile_mma<B, false, false, false, FULL, FULL>(acc, P, Q);
+                        }
+                        if (q == m - 1) {
+                            acc_store<B>(acc, P);  // P's slot received no copy for this element
+                            cta_sync();
+                            acc_zero<B>(acc);
+                            tile_mma<B, false, false, true, FULL, LOWER>(acc, P, Q);
+                        }
+                    }))
+                return;
             cta_sync();
             acc_store<B>(acc, T0);
             cta_sync();
             store_ws32<B>(const_cast<float*>(tC<B>(p, i, j)), T0);
             publish(c, &fX[i * t + j], ticket);
         } else if (kind == K_S3_OFF) {
-            if (!fetch32<B>(c, &fD[i], &fX[i * t + j], tD<B>(p, i), tC<B>(p, i, j))) return;
             acc_zero<B>(acc);
-            tile_mma<B, true, false, false, LOWER, FULL>(acc, T0, T1);
-            for (int k = i + 1; k < t; ++k) {
-                if (!fetch32<B>(c, &fX[k * t + i], &fX[k * t + j], tC<B>(p, k, i), tC<B>(p, k, j))) return;
-                tile_mma<B, true, false, false, FULL, FULL>(acc, T0, T1);
-            }
+            if (!run_chain(
+                    ch, c, t - i, kBytes,
+                    [&](int q) {
+                        if (q == 0) return el(&fD[i], &fX[i * t + j], tD<B>(p, i), tC<B>(p, i, j));
+                        const int k = i + q;
+                        return el(&fX[k * t + i], &fX[k * t + j], tC<B>(p, k, i), tC<B>(p, k, j));
+                    },
+                    [&](int q, const void* Ta, const void* Tb) {
+                        const float* P = static_cast<const float*>(Ta);
+                        const float* Q = static_cast<const float*>(Tb);
+                        if (q == 0) tile_mma<B, true, false, false, LOWER, FULL>(acc, P, Q);
+                        else tile_mma<B, true, false, false, FULL, FULL>(acc, P, Q);
+                    }))
+                return;
             cta_sync();
             acc_store<B>(acc, T0);
             cta_sync();
             store_X<B>(p, i, j, T0);
         } else if (kind == K_S3_DIAG) {
-            if (!fetch32<B>(c, &fD[i], nullptr, tD<B>(p, i), nullptr)) return;
             acc_zero<B>(acc);
-            tile_mma<B, true, false, false, LOWER, LOWER>(acc, T0, T0);
-            for (int k = i + 1; k < t; ++k) {
-                if (!fetch32<B>(c, &fX[k * t + i], nullptr, tC<B>(p, k, i), nullptr)) return;
-                tile_mma<B, true, false, false, FULL, FULL>(acc, T0, T0);
-            }
+            if (!run_chain(
+                    ch, c, t - i, kBytes,
+                    [&](int q) {
+                        if (q == 0) return el(&fD[i], nullptr, tD<B>(p, i), nullptr);
+                        return el(&fX[(i + q) * t + i], nullptr, tC<B>(p, i + q, i), nullptr);
+                    },
+                    [&](int q, const void* Ta, const void*) {
+                        const float* P = static_cast<const float*>(Ta);
+                        if (q == 0) tile_mma<B, true, false, false, LOWER, LOWER>(acc, P, P);
+                        else tile_mma<B, true, false, false, FULL, FULL>(acc, P, P);
+                    }))
+                return;
             cta_sync();
             acc_store<B>(acc, T0);
             cta_sync();
@@ -354,7 +420,7 @@ __global__ void finalize_info_mixed(const int* ctrl, int* d_info) {
 
 template <int B>
 int mixed_smem() {
-    return 2 * round_up128(padded_tile<B>() * (int)sizeof(float)) + (B * B + kThreads) * (int)sizeof(double);
+    return mixed_smem_bytes<B>();
 }
 
 template <int B, class ACC>

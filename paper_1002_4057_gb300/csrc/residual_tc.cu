@@ -107,6 +107,17 @@ __device__ __forceinline__ double pow2(int x) { return __longlong_as_double((lon
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
+// After tmem_wait_ld: marks the 32 registers of an earlier tmem load as
+// written here, so that no use of them is scheduled above the wait.
+__device__ __forceinline__ void reg_fence32(uint32_t (&r)[32]) {
+    asm volatile(""
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                   "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]),
+                   "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]),
+                   "+r"(r[29]), "+r"(r[30]), "+r"(r[31]));
+}
+
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
@@ -118,6 +129,7 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
         : "r"(taddr)
         : "memory");
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    reg_fence32(r);
 }
 
 // The same load without its wait: several loads in flight, then one wait.
@@ -134,6 +146,7 @@ __device__ __forceinline__ void tmem_ld32_async(uint32_t taddr, uint32_t (&r)[32
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
+
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
@@ -142,6 +155,10 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
         : "r"(taddr)
         : "memory");
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    asm volatile(""
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                   "+r"(r[15]));
 }
 
 __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16]) {
@@ -551,20 +568,31 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         for (int c = 0; c < total_chunks; ++c) {
             if (!wait_bar(&accf, c & 1, &s_abort, p)) break;
             tc_fence_after();
-#pragma unroll 1
-            for (int g = 0; g < W_COLS / 32; ++g) {  // sums += int(chunk), exact: chunk entries are integers <= 2^24
-                uint32_t r[32], l[32];
-                tmem_ld32_async(tacc + (uint32_t)(g * 32), r);
-                if (!fresh) tmem_ld32_async(tsum + (uint32_t)(g * 32), l);
-                tmem_wait_ld();
+            // The whole chunk (128 values per thread) into registers, then the
+            // accumulator goes back to the MMA warp at once: the next chunk's
+            // products overlap the level-sum update below.
+            uint32_t r[W_COLS / 32][32];
 #pragma unroll
-                for (int u = 0; u < 32; ++u)
-                    l[u] = (uint32_t)(__float2int_rn(__uint_as_float(r[u])) + (fresh ? 0 : (int)l[u]));
-                tmem_st32(tsum + (uint32_t)(g * 32), l);
-            }
+            for (int g = 0; g < W_COLS / 32; ++g) tmem_ld32_async(tacc + (uint32_t)(g * 32), r[g]);
+            tmem_wait_ld();
+#pragma unroll
+            for (int g = 0; g < W_COLS / 32; ++g) reg_fence32(r[g]);
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&acce);
+#pragma unroll
+            for (int g = 0; g < W_COLS / 32; ++g) {  // sums += int(chunk), exact: chunk entries are integers <= 2^24
+                uint32_t l[32];
+                if (!fresh) {
+                    tmem_ld32(tsum + (uint32_t)(g * 32), l);
+#pragma unroll
+                    for (int u = 0; u < 32; ++u) l[u] = (uint32_t)(__float2int_rn(__uint_as_float(r[g][u])) + (int)l[u]);
+                } else {
+#pragma unroll
+                    for (int u = 0; u < 32; ++u) l[u] = (uint32_t)__float2int_rn(__uint_as_float(r[g][u]));
+                }
+                tmem_st32(tsum + (uint32_t)(g * 32), l);
+            }
             fresh = false;
             ++since_flush;
             const int lv = p.ps[pair] + p.pt[pair];

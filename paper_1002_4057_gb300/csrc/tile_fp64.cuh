@@ -167,22 +167,26 @@ __device__ int tile_potrf(double* T, int* s_fail) {
 // (column sweep from the last column, as in LAPACK's unblocked trti2):
 //   X_jj = 1/L_jj,  X_ij = -(sum_{k=j+1..i} X_ik L_kj) X_jj   (i > j).
 // tmp: NT doubles of shared scratch.  The strictly upper part is not touched.
+// The b reciprocals are formed once, in parallel, into tmp[0 .. b-1] (the
+// partial sums use tmp[b ..]): an FP64 division is a sequence of FP64-pipe
+// instructions, and this chip's FP64 pipe issues two FMAs per clock per SM.
 template <int B, int NT = kThreads>
 __device__ void tile_trtri(double* T, double* tmp) {
     constexpr int RS = NT / B;
     static_assert(RS >= 1 && NT % B == 0, "whole rows per thread group");
     const int r = threadIdx.x % B, cs = threadIdx.x / B;
     cta_sync();
+    if (threadIdx.x < B) tmp[threadIdx.x] = 1.0 / T[threadIdx.x * B + threadIdx.x];
+    cta_sync();
     for (int j = B - 1; j >= 0; --j) {
-        const double xjj = 1.0 / T[j * B + j];
+        const double xjj = tmp[j];
         // rows i > j: partial sums over k split among the RS threads of a row
         double s = 0.0;
         if (r > j)
             for (int k = j + 1 + cs; k <= r; k += RS) s += T[k * B + r] * T[j * B + k];
-        // combine the RS partial sums (RS consecutive... rows share lanes across warps)
-        if (RS > 1) {
-            tmp[cs * B + r] = s;
-        }
+        // combine the RS partial sums: thread group cs > 0 leaves its sum in
+        // tmp[cs * b + r] (tmp[0 .. b-1] holds the reciprocals)
+        if (RS > 1 && cs > 0) tmp[cs * B + r] = s;
         cta_sync();
         if (cs == 0 && r > j) {
             double tot = s;

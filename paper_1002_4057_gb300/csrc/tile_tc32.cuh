@@ -114,7 +114,7 @@ __device__ __forceinline__ void split_bf16x2(float x0, float x1, uint32_t& hi, u
 }
 
 __device__ __forceinline__ void mma_tf32(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
-    asm volatile(
+    asm(
         "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
         "{%0,%1,%2,%3};"
         : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
@@ -122,7 +122,7 @@ __device__ __forceinline__ void mma_tf32(float (&c)[4], const uint32_t (&a)[4], 
 }
 
 __device__ __forceinline__ void mma_bf16x(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
-    asm volatile(
+    asm(
         "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
         "{%0,%1,%2,%3};"
         : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
@@ -182,14 +182,20 @@ __device__ __forceinline__ void tile_mma(AccTC<B, S>& acc, const float* P, const
                 split_tf32(opQ(k0 + q, n), bh[ni][0], bl[ni][0]);
                 split_tf32(opQ(k0 + q + 4, n), bh[ni][1], bl[ni][1]);
             }
+            // each term over all (mi, ni) blocks before the next: the three
+            // MMAs into one accumulator depend on each other, the blocks not
 #pragma unroll
             for (int mi = 0; mi < MI; ++mi)
 #pragma unroll
-                for (int ni = 0; ni < NI; ++ni) {
-                    mma_tf32(part[mi][ni], al[mi], bh[ni][0], bh[ni][1]);
-                    mma_tf32(part[mi][ni], ah[mi], bl[ni][0], bl[ni][1]);
-                    mma_tf32(part[mi][ni], ah[mi], bh[ni][0], bh[ni][1]);
-                }
+                for (int ni = 0; ni < NI; ++ni) mma_tf32(part[mi][ni], al[mi], bh[ni][0], bh[ni][1]);
+#pragma unroll
+            for (int mi = 0; mi < MI; ++mi)
+#pragma unroll
+                for (int ni = 0; ni < NI; ++ni) mma_tf32(part[mi][ni], ah[mi], bl[ni][0], bl[ni][1]);
+#pragma unroll
+            for (int mi = 0; mi < MI; ++mi)
+#pragma unroll
+                for (int ni = 0; ni < NI; ++ni) mma_tf32(part[mi][ni], ah[mi], bh[ni][0], bh[ni][1]);
         } else {  // m16n8k16 bf16: a pairs (g, 2q..) (g+8, 2q..) (g, 2q+8..) (g+8, 2q+8..); b (2q.., g) (2q+8.., g)
 #pragma unroll
             for (int mi = 0; mi < MI; ++mi) {
@@ -208,11 +214,15 @@ __device__ __forceinline__ void tile_mma(AccTC<B, S>& acc, const float* P, const
 #pragma unroll
             for (int mi = 0; mi < MI; ++mi)
 #pragma unroll
-                for (int ni = 0; ni < NI; ++ni) {
-                    mma_bf16x(part[mi][ni], al[mi], bh[ni][0], bh[ni][1]);
-                    mma_bf16x(part[mi][ni], ah[mi], bl[ni][0], bl[ni][1]);
-                    mma_bf16x(part[mi][ni], ah[mi], bh[ni][0], bh[ni][1]);
-                }
+                for (int ni = 0; ni < NI; ++ni) mma_bf16x(part[mi][ni], al[mi], bh[ni][0], bh[ni][1]);
+#pragma unroll
+            for (int mi = 0; mi < MI; ++mi)
+#pragma unroll
+                for (int ni = 0; ni < NI; ++ni) mma_bf16x(part[mi][ni], ah[mi], bl[ni][0], bl[ni][1]);
+#pragma unroll
+            for (int mi = 0; mi < MI; ++mi)
+#pragma unroll
+                for (int ni = 0; ni < NI; ++ni) mma_bf16x(part[mi][ni], ah[mi], bh[ni][0], bh[ni][1]);
         }
     }
 #pragma unroll
