@@ -97,8 +97,8 @@ typedef enum {
 
 /* Options for spdinv_potri_ex.  Zero-initialise and set what you need. */
 typedef struct {
-    int tile;            /* tile order b, 32 or 64; 0 = automatic (FP64: 32 up to n = 16384,
-                            64 above; mixed precision: 64) */
+    int tile;            /* tile order b, 32, 64 or (FP64 potri only) 128; 0 = automatic (FP64: 32
+                            up to n = 16384, 64 above; mixed precision: 32 up to n = 8192, 64 above) */
     int ctas_per_sm;     /* resident CTAs per SM of the persistent kernel; 0 = automatic */
     int precision;       /* spdinv_precision */
     int refine_steps;    /* mixed precision only: residual corrections X <- X + X(I - A X); 0 = none */

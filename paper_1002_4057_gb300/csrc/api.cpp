@@ -184,11 +184,11 @@ double wait_timeout_s(const spdinv_opts* o) {
     return 60.0;
 }
 
-// Tile 32 measured faster than 64 at n = 4096, 8192 and 16384 (6 resident
-// CTAs per SM instead of 3, and fewer wasted flops in the diagonal tiles).
-// Above n = 16384 the default is the tile measured there: 64 runs at the
-// FP64 rate at n = 32768 (1084 Gflop/s), and it halves t for the first call's
-// plan build (0.04 s at t = 512, 0.2 s at t = 1024).
+// Tile 32 measured faster than 64 at n = 4096, 8192 and 16384 (1241 against
+// 1200 Gflop/s at 16384: more tasks to overlap the dependency waits, and fewer
+// wasted flops in the diagonal tiles).  Above n = 16384 the default is 64: it
+// runs at the FP64 rate at n = 32768, and it halves t for the first call's
+// plan build (the ALAP order takes about 1 s at t = 512, 8 s at t = 1024).
 // SPDINV_TILE=32|64 in the environment overrides it.
 static int default_tile(int64_t n) {
     static const int forced = [] {

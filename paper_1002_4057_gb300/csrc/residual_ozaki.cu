@@ -110,18 +110,36 @@ __global__ void exponents_kernel(int64_t n, const unsigned long long* maxbits, i
     }
 }
 
-// The S balanced base-256 digits of u = v 2^-e in (-1/2, 1/2): each step
-// takes a = round(256 u) in [-128, 128] and keeps the remainder, again in
-// [-1/2, 1/2].  Every operation is exact (scaling by powers of two and
-// subtracting the integer part of a double).
+// The S balanced base-256 digits of u = v 2^-e in (-1/2, 1/2), in integer
+// arithmetic: W = u 2^(8S), rounded to the nearest integer (half away from
+// zero), is formed from v's exponent and 53-bit significand by one shift; its
+// digits are then peeled from the least significant end, each the residue of
+// W mod 256 taken in [-128, 127], and the top digit is what remains, in
+// [-128, 128] because |W| <= 2^(8S-1).  The digits sum to W 2^(-8S), within
+// 2^-(8S+1) of u, and each is an exact BF16 integer.  (Digit by digit in FP64
+// -- a = rint(256 u), u -= a -- gives a split with the same bounds, but costs
+// some 25 FP64 instructions per entry, and the FP64 pipe is this chip's
+// slowest.)  A NaN or Inf entry gives NaN digits.
 __device__ __forceinline__ void cut(double v, int e, int S, __nv_bfloat16* out, int64_t stride) {
-    double u = scalbn(v, -e);
-    for (int s = 0; s < S; ++s) {
-        u *= 256.0;
-        const double a = rint(u);
-        u -= a;
-        out[s * stride] = __float2bfloat16_rn((float)a);
+    const long long bits = __double_as_longlong(v);
+    const int E = (int)((bits >> 52) & 0x7ff);
+    if (E == 0x7ff) {
+        for (int s = 0; s < S; ++s) out[s * stride] = __float2bfloat16_rn(__int_as_float(0x7fc00000));
+        return;
     }
+    const long long M = (bits & 0xFFFFFFFFFFFFFLL) | (E ? (1LL << 52) : 0LL);  // |v| = M 2^(max(E,1) - 1075)
+    const int sh = (E ? E : 1) - 1075 + 8 * S - e;                              // |W| = M 2^sh
+    long long W;
+    if (M == 0 || sh < -60) W = 0;         // below half a unit of the last digit
+    else if (sh >= 0) W = M << sh;         // < 2^(8S-1) <= 2^55: no overflow
+    else W = (M + (1LL << (-sh - 1))) >> -sh;
+    if (bits < 0) W = -W;
+    for (int s = S - 1; s > 0; --s) {
+        const long long a = ((W + 128) & 255) - 128;  // W mod 256 in [-128, 127]
+        out[s * stride] = __float2bfloat16_rn((float)a);
+        W = (W - a) >> 8;                              // exact: W - a is a multiple of 256
+    }
+    out[0] = __float2bfloat16_rn((float)W);
 }
 
 // Slices of A, K-major: Asl[s][i][k] = slice s of A(i,k) 2^-e_i (npad x npad,

@@ -133,26 +133,34 @@ __device__ __forceinline__ void tile_zero_upper(double* T) {
 }
 
 // Unblocked Cholesky of the lower triangle of a b x b tile, in place
-// (right-looking column sweep).  Returns 0, or c+1 for the first local column
-// c whose pivot is not > 0 (or is NaN); the tile is then partly updated.
+// (right-looking column sweep; each column is scaled by the reciprocal of its
+// pivot, one FP64 division per column instead of one per element).  Returns
+// 0, or c+1 for the first local column c whose pivot is not > 0 (or is NaN);
+// the tile is then partly updated.
 // Must be called by all threads; the return value is uniform.
 template <int B, int NT = kThreads>
 __device__ int tile_potrf(double* T, int* s_fail) {
     constexpr int RS = NT / B;  // threads per row (2 for b=64, 4 for b=32 with 128 threads)
     static_assert(RS >= 1 && NT % B == 0, "whole rows per thread group");
+    __shared__ double s_inv;  // 1 / L_cc of the current column
     const int r = threadIdx.x % B, cs = threadIdx.x / B;
     if (threadIdx.x == 0) *s_fail = 0;
     cta_sync();
     for (int c = 0; c < B; ++c) {
         if (threadIdx.x == 0) {
             const double d = T[c * B + c];
-            if (d > 0.0) T[c * B + c] = sqrt(d);
-            else *s_fail = c + 1;
+            if (d > 0.0) {
+                const double l = sqrt(d);
+                T[c * B + c] = l;
+                s_inv = 1.0 / l;  // one division per column; the column is scaled by products
+            } else {
+                *s_fail = c + 1;
+            }
         }
         cta_sync();
         if (*s_fail) return *s_fail;
-        const double l = T[c * B + c];
-        if (cs == 0 && r > c) T[c * B + r] = T[c * B + r] / l;
+        const double inv = s_inv;
+        if (cs == 0 && r > c) T[c * B + r] = T[c * B + r] * inv;
         cta_sync();
         if (r > c) {
             const double lr = T[c * B + r];

@@ -218,11 +218,15 @@ def test_workspace_size_mixed_and_residual_layout(lib):
     256 * (8 + 16) bytes of scales and 1024 bytes of pad."""
     mixed = L.SPDINV_PREC_MIXED_FP32
     base = 256 + 2 * 16640 + 33280
-    o = L.spdinv_opts(0, 0, mixed, 0, 0.0, -1, 0, 0)
+    o = L.spdinv_opts(64, 0, mixed, 0, 0.0, -1, 0, 0)
     assert _ws(100, L.SPDINV_ROUTINE_POTRI, o) == base + 80128
-    o = L.spdinv_opts(0, 0, mixed, 1, 0.0, -1, 0, 3)
+    o = L.spdinv_opts(64, 0, mixed, 1, 0.0, -1, 0, 3)
     planes = 23 * 65536 * 2 + 256 * 24 + 1024
     assert _ws(100, L.SPDINV_ROUTINE_POTRI, o) == base + 3 * 80128 + planes
+    # the automatic tile is 32 up to n = 8192 and 64 above
+    for n, b in ((100, 32), (8192, 32), (8193, 64)):
+        assert _ws(n, L.SPDINV_ROUTINE_POTRI, L.spdinv_opts(0, 0, mixed, 0, 0.0, -1, 0, 0)) == \
+            _ws(n, L.SPDINV_ROUTINE_POTRI, L.spdinv_opts(b, 0, mixed, 0, 0.0, -1, 0, 0))
     # the residual alone: 256 bytes of status words, plus 2 x 7 slice planes,
     # 256 ints and 256 64-bit maxima per side and 1024 bytes of pad when emulated
     r = L.SPDINV_ROUTINE_INVERSE_RESIDUAL
