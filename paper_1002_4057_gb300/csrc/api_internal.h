@@ -83,6 +83,9 @@ spdinv_status log_status(const char* fn, const char* size_name, int64_t size, sp
 // d_diag: STEPS_DIAG only, receives diag(A^{-1}).
 spdinv_status run_fp64(int64_t n, double* dA, int64_t lda, int steps, const spdinv_opts* o, int* d_info,
                        cudaStream_t stream, double* d_diag = nullptr);
+// FP32 backward on the tensor cores (backward_tc.cu); arguments already checked.
+spdinv_status backward_f32_tc(int batch, int64_t n, const float* dX, int64_t ldx, int64_t sx, const float* dG,
+                              int64_t ldg, int64_t sg, float* dGrad, int64_t ldr, int64_t sr, cudaStream_t stream);
 spdinv_status run_mixed(int64_t n, double* dA, int64_t lda, const spdinv_opts* o, int* d_info,
                         cudaStream_t stream);
 

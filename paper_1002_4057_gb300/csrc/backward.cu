@@ -7,7 +7,8 @@
 //   phase 1:  grad = -Y X, lower tiles only, each written to (i, j) and,
 //             transposed, to (j, i); the diagonal tiles are averaged with
 //             their transpose, so grad is exactly symmetric.
-// FP64 uses the tensor-core MMA tile products, FP32 the CUDA-core ones.
+// This file runs FP64: the tile products are FP64 FMAs on register blocks.
+// FP32 runs on the tensor cores as 3xTF32 products (backward_tc.cu).
 #include <cuda_runtime.h>
 
 #include <map>
@@ -181,6 +182,8 @@ spdinv_status run_backward(int batch, int64_t n, const T* dX, int64_t ldx, int64
     if (batch == 0 || n == 0) return SPDINV_OK;
     if (!dX || !dG || !dGrad) return SPDINV_ERR_NULL;
     if (batch > 65535) return SPDINV_ERR_N;
+    if constexpr (sizeof(T) == 4)  // FP32: 3xTF32 products on the tensor cores (backward_tc.cu)
+        return backward_f32_tc(batch, n, dX, ldx, sx, dG, ldg, sg, dGrad, ldr, sr, stream);
     const int64_t t = (n + BB - 1) / BB;
     if (t * (t + 1) / 2 > 2147483647LL || t * t > 2147483647LL) return SPDINV_ERR_N;
     int dev = 0;
