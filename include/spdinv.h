@@ -343,7 +343,11 @@ SPDINV_API spdinv_status spdinv_potri_backward(int batch, int64_t n, const doubl
                                     double* dGrad, int64_t ldgrad, int64_t stride_grad,
                                     cudaStream_t stream);
 
-/* FP32 twin of spdinv_potri_backward. */
+/* FP32 twin of spdinv_potri_backward, on the tensor cores: each product is a
+ * sum of three TF32 products of split operands (3xTF32: x = hi + lo, hi the
+ * TF32 rounding of x), FP32 accumulation; close to FP32 accuracy.  The
+ * library workspace holds 6 batch npad^2 floats, npad = n rounded up to 128
+ * (hi and lo planes of X, sym(G) and Y). */
 SPDINV_API spdinv_status spdinv_spotri_backward(int batch, int64_t n, const float* dX, int64_t ldx, int64_t stride_x,
                                      const float* dG, int64_t ldg, int64_t stride_g,
                                      float* dGrad, int64_t ldgrad, int64_t stride_grad,

@@ -16,7 +16,6 @@
 
 #include "../../include/spdinv.h"
 #include "api_internal.h"
-#include "tile_f32.cuh"
 #include "tile_fp64.cuh"
 
 namespace spdinv {
@@ -30,11 +29,6 @@ template <>
 struct BwdTile<double> {
     using Acc = spdinv::Acc<BB>;
     static constexpr int LD = BB;
-};
-template <>
-struct BwdTile<float> {
-    using Acc = Acc32<BB>;
-    static constexpr int LD = BB + 1;
 };
 
 template <typename T>
@@ -122,10 +116,7 @@ __global__ void __launch_bounds__(kThreads) backward_kernel(const BwdParams<T> p
             load_tile<T>(X, p.n, p.ldx, kt, tj, S1);
         }
         cta_sync();
-        if constexpr (sizeof(T) == 4)
-            tile_mma<BB, false, false, PHASE == 1, FULL, FULL, true>(acc, S0, S1);  // packed FP32 FMA
-        else
-            tile_mma<BB, false, false, PHASE == 1, FULL, FULL>(acc, S0, S1);
+        tile_mma<BB, false, false, PHASE == 1, FULL, FULL>(acc, S0, S1);
     }
     cta_sync();
     acc_store<BB>(acc, S0);
@@ -173,17 +164,27 @@ BwdState& bwd_state(int dev) {
     return *s;
 }
 
-template <typename T>
-spdinv_status run_backward(int batch, int64_t n, const T* dX, int64_t ldx, int64_t sx, const T* dG, int64_t ldg,
-                           int64_t sg, T* dGrad, int64_t ldr, int64_t sr, cudaStream_t stream) {
+// Argument checks of both precisions: SPDINV_OK with *run = false when there
+// is nothing to do.
+spdinv_status backward_args(int batch, int64_t n, const void* dX, int64_t ldx, const void* dG, int64_t ldg,
+                            const void* dGrad, int64_t ldr, bool* run) {
+    *run = false;
     if (batch < 0 || n < 0) return SPDINV_ERR_N;
     const int64_t mn = n > 1 ? n : 1;
     if (ldx < mn || ldg < mn || ldr < mn) return SPDINV_ERR_LDA;
     if (batch == 0 || n == 0) return SPDINV_OK;
     if (!dX || !dG || !dGrad) return SPDINV_ERR_NULL;
     if (batch > 65535) return SPDINV_ERR_N;
-    if constexpr (sizeof(T) == 4)  // FP32: 3xTF32 products on the tensor cores (backward_tc.cu)
-        return backward_f32_tc(batch, n, dX, ldx, sx, dG, ldg, sg, dGrad, ldr, sr, stream);
+    *run = true;
+    return SPDINV_OK;
+}
+
+template <typename T>
+spdinv_status run_backward(int batch, int64_t n, const T* dX, int64_t ldx, int64_t sx, const T* dG, int64_t ldg,
+                           int64_t sg, T* dGrad, int64_t ldr, int64_t sr, cudaStream_t stream) {
+    bool run = false;
+    const spdinv_status a = backward_args(batch, n, dX, ldx, dG, ldg, dGrad, ldr, &run);
+    if (!run) return a;
     const int64_t t = (n + BB - 1) / BB;
     if (t * (t + 1) / 2 > 2147483647LL || t * t > 2147483647LL) return SPDINV_ERR_N;
     int dev = 0;
@@ -240,7 +241,10 @@ SPDINV_API spdinv_status spdinv_potri_backward(int batch, int64_t n, const doubl
 SPDINV_API spdinv_status spdinv_spotri_backward(int batch, int64_t n, const float* dX, int64_t ldx, int64_t sx,
                                                 const float* dG, int64_t ldg, int64_t sg, float* dGrad,
                                                 int64_t ldr, int64_t sr, cudaStream_t stream) {
-    return log_status("spdinv_spotri_backward", "n", n, run_backward<float>(batch, n, dX, ldx, sx, dG, ldg, sg, dGrad, ldr, sr, stream));
+    bool run = false;
+    spdinv_status st = backward_args(batch, n, dX, ldx, dG, ldg, dGrad, ldr, &run);
+    if (run) st = backward_f32_tc(batch, n, dX, ldx, sx, dG, ldg, sg, dGrad, ldr, sr, stream);
+    return log_status("spdinv_spotri_backward", "n", n, st);
 }
 
 }  // extern "C"
