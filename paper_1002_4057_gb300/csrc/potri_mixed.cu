@@ -30,6 +30,7 @@
 #include "persist.cuh"
 #include "tile_f32.cuh"
 #include "tile_tc32.cuh"
+#include "tile_diag32.cuh"
 #include "tile_fp64.cuh"
 
 namespace spdinv {
@@ -200,23 +201,36 @@ __global__ void __launch_bounds__(kThreads) potri_mixed_persistent(const KParams
                 return;
             cta_sync();
             acc_store<B>(acc, T0);
-            cta_sync();
-            for (int idx = threadIdx.x; idx < B * B; idx += kThreads) {  // to FP64
-                const int r = idx % B, cc = idx / B;
-                Td[idx] = r >= cc ? (double)T0[cc * LD + r] : 0.0;
+            if constexpr (B == 32) {  // warp-level FP32 sweeps in registers (tile_diag32.cuh)
+                const int fail = diag_potrf32_f32<LD>(T0, &s_fail);
+                if (fail) {
+                    if (threadIdx.x == 0) record_info(p.ctrl, j * B + fail);
+                    return;
+                }
+                for (int idx = threadIdx.x; idx < padded_tile<B>(); idx += kThreads) {  // upper part, pad row
+                    const int r = idx % LD, cc = idx / LD;
+                    if (r < cc || r == B) T0[idx] = 0.f;
+                }
+                diag_trtri32_f32<LD>(T0);
+            } else {  // FP64 block-wide sweeps
+                cta_sync();
+                for (int idx = threadIdx.x; idx < B * B; idx += kThreads) {  // to FP64
+                    const int r = idx % B, cc = idx / B;
+                    Td[idx] = r >= cc ? (double)T0[cc * LD + r] : 0.0;
+                }
+                const int fail = tile_potrf<B>(Td, &s_fail);
+                if (fail) {
+                    if (threadIdx.x == 0) record_info(p.ctrl, j * B + fail);
+                    return;
+                }
+                tile_zero_upper<B>(Td);
+                tile_trtri<B>(Td, tmpd);
+                for (int idx = threadIdx.x; idx < padded_tile<B>(); idx += kThreads) {
+                    const int r = idx % LD, cc = idx / LD;
+                    T0[idx] = (r < B && r >= cc) ? (float)Td[cc * B + r] : 0.f;
+                }
+                cta_sync();
             }
-            const int fail = tile_potrf<B>(Td, &s_fail);  // POTRF in FP64
-            if (fail) {
-                if (threadIdx.x == 0) record_info(p.ctrl, j * B + fail);
-                return;
-            }
-            tile_zero_upper<B>(Td);
-            tile_trtri<B>(Td, tmpd);  // TRTRI in FP64
-            for (int idx = threadIdx.x; idx < padded_tile<B>(); idx += kThreads) {
-                const int r = idx % LD, cc = idx / LD;
-                T0[idx] = (r < B && r >= cc) ? (float)Td[cc * B + r] : 0.f;
-            }
-            cta_sync();
             store_ws32<B>(const_cast<float*>(tD<B>(p, j)), T0);
             publish(c, &fD[j], ticket);
         } else if (kind == K_S1_OFF) {
