@@ -1,7 +1,9 @@
 // Mixed-precision inversion (an added form): the tile DAG of Algorithm 1
 // (Sec. 2) with renaming and pipelining (Sec. 3) runs with its bulk updates
-// (GEMM, SYRK, TRMM) in FP32 while every diagonal-tile POTRF and TRTRI runs in
-// native FP64; then `refine_steps` residual corrections of order p bring the
+// (GEMM, SYRK, TRMM) at FP32 accuracy (FP32 FMA, or three TF32 or BF16
+// tensor-core products of split operands) and its diagonal-tile POTRF and
+// TRTRI in FP32 (warp-level register sweeps for 32-tiles, block-wide sweeps
+// for 64-tiles); then `refine_steps` residual corrections of order p bring the
 // result back to FP64 accuracy:
 //      R = I - A X         (FP64-accurate; A read from its lower triangle)
 //      X <- X + X R + X R^2 + ... + X R^{p-1}
@@ -121,17 +123,15 @@ __device__ void store_X(const KParamsMixed& p, int ti, int tj, const float* T) {
 // (3xTF32), AccTC<B, SplitBF16> three BF16 MMAs (BF16x3).
 //
 // Shared memory: two sets of two tile buffers for the double-buffered update
-// chains (run_chain); the FP64 diagonal tile of the Step-1 diagonal task and
-// its scratch reuse the second set once that task's chain is done.
+// chains (run_chain); the TRTRI scratch of the Step-1 diagonal task reuses
+// the second set once that task's chain is done.
 template <int B>
 __host__ __device__ constexpr int mixed_tile_bytes() {
     return round_up128(padded_tile<B>() * (int)sizeof(float));
 }
 template <int B>
 __host__ __device__ constexpr int mixed_smem_bytes() {
-    return 2 * mixed_tile_bytes<B>() + (2 * mixed_tile_bytes<B>() > (B * B + kThreads) * (int)sizeof(double)
-                                            ? 2 * mixed_tile_bytes<B>()
-                                            : (B * B + kThreads) * (int)sizeof(double));
+    return 4 * mixed_tile_bytes<B>();
 }
 
 template <int B, class ACC>
@@ -147,8 +147,7 @@ __global__ void __launch_bounds__(kThreads) potri_mixed_persistent(const KParams
     float* const T1 = reinterpret_cast<float*>(smem_raw + kT);
     float* const T2 = reinterpret_cast<float*>(smem_raw + 2 * kT);
     float* const T3 = reinterpret_cast<float*>(smem_raw + 3 * kT);
-    double* const Td = reinterpret_cast<double*>(smem_raw + 2 * kT);  // FP64 diagonal tile, stride B (set 1)
-    double* const tmpd = Td + B * B;                                   // kThreads doubles
+    float* const tmpf = reinterpret_cast<float*>(smem_raw + 2 * kT);  // TRTRI scratch, kThreads floats (set 1)
     PCtx c;
     c.T0 = T0;
     c.T1 = T1;
@@ -212,23 +211,17 @@ __global__ void __launch_bounds__(kThreads) potri_mixed_persistent(const KParams
                     if (r < cc || r == B) T0[idx] = 0.f;
                 }
                 diag_trtri32_f32<LD>(T0);
-            } else {  // FP64 block-wide sweeps
-                cta_sync();
-                for (int idx = threadIdx.x; idx < B * B; idx += kThreads) {  // to FP64
-                    const int r = idx % B, cc = idx / B;
-                    Td[idx] = r >= cc ? (double)T0[cc * LD + r] : 0.0;
-                }
-                const int fail = tile_potrf<B>(Td, &s_fail);
+            } else {  // FP32 block-wide column sweeps (tile_f32.cuh)
+                const int fail = tile_potrf<B>(T0, &s_fail);
                 if (fail) {
                     if (threadIdx.x == 0) record_info(p.ctrl, j * B + fail);
                     return;
                 }
-                tile_zero_upper<B>(Td);
-                tile_trtri<B>(Td, tmpd);
-                for (int idx = threadIdx.x; idx < padded_tile<B>(); idx += kThreads) {
+                for (int idx = threadIdx.x; idx < padded_tile<B>(); idx += kThreads) {  // upper part, pad row
                     const int r = idx % LD, cc = idx / LD;
-                    T0[idx] = (r < B && r >= cc) ? (float)Td[cc * B + r] : 0.f;
+                    if (r < cc || r == B) T0[idx] = 0.f;
                 }
+                tile_trtri<B>(T0, tmpf);
                 cta_sync();
             }
             store_ws32<B>(const_cast<float*>(tD<B>(p, j)), T0);
