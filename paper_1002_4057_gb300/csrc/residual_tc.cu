@@ -455,19 +455,41 @@ __device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32
 }
 
 // Tile (bm, bn) of launch index pid: 128-row block bm, 256-column block bn.
-// lower: only tiles holding an entry on or below the diagonal, bn <= bm / 2
-// (rows 2r and 2r + 1 hold r + 1 tiles each; r (r + 1) tiles come first).
+// lower: only tiles holding an entry on or below the diagonal, bn <= bm / 2,
+// in the same grouped raster as the full grid (GROUP row blocks swept column
+// by column), so the CTAs resident at one time share the column blocks of X's
+// slices in L2.  In the group of rows [first, first + gm), column bn holds the
+// rows max(first, 2 bn) .. first + gm - 1.  (tb_m is even: npad is a multiple
+// of 256.)
+__device__ __forceinline__ int lower_group_tiles(int first, int gm) {
+    const int h = (first + gm - 1) / 2, f2 = first / 2;  // last column; last full column
+    int cnt = (min(f2, h) + 1) * gm;
+    if (h > f2) cnt += (h - f2) * (first + gm) - (h * (h + 1) - f2 * (f2 + 1));
+    return cnt;
+}
 __device__ __forceinline__ void block_of_wide(int pid, int tb_m, int tb_n, bool lower, int& bm, int& bn) {
     if (!lower) {
         block_of(pid, tb_m, tb_n, false, bm, bn);
         return;
     }
-    int r = (int)((sqrt(4.0 * pid + 1.0) - 1.0) / 2.0);
-    while ((r + 1) * (r + 2) <= pid) ++r;
-    while (r * (r + 1) > pid) --r;
-    const int off = pid - r * (r + 1);
-    bm = 2 * r + off / (r + 1);
-    bn = off % (r + 1);
+    constexpr int GROUP = 16;
+    int first = 0, gm = min(tb_m, GROUP);
+    for (;;) {
+        gm = min(tb_m - first, GROUP);
+        const int cnt = lower_group_tiles(first, gm);
+        if (pid < cnt || first + gm >= tb_m) break;
+        pid -= cnt;
+        first += gm;
+    }
+    for (bn = 0; bn <= (first + gm - 1) / 2; ++bn) {
+        const int lo = max(first, 2 * bn), c = first + gm - lo;
+        if (pid < c) {
+            bm = lo + pid;
+            return;
+        }
+        pid -= c;
+    }
+    bm = tb_m;  // past the last tile (the launch has exactly as many CTAs as tiles)
 }
 
 __global__ void __launch_bounds__(NTHREADS, 1)
@@ -481,6 +503,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const int tb_m = (int)(p.npad / TM), tb_n = (int)(p.npad / WN);
     int tile_m, tile_n;
     block_of_wide((int)blockIdx.x, tb_m, tb_n, p.lower != 0, tile_m, tile_n);
+    if (tile_m >= tb_m) return;
     const int64_t m0 = (int64_t)tile_m * TM, n0 = (int64_t)tile_n * WN;
     const int kstages = (int)(p.npad / ATOM);  // stages per slice pair
     const int chunks_per_pair = (kstages + W_CHUNK - 1) / W_CHUNK;
