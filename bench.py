@@ -428,7 +428,7 @@ def run_mixed_study(args, dev, stream):
     mw = 3 if n <= 16384 else 1
     schedules = {1e2: ((0, 2), (1, 2), (2, 2), (1, 3), (1, 4)),
                  1e4: ((0, 2), (1, 2), (2, 2), (1, 3), (1, 4), (1, 5)),
-                 1e6: ((0, 2), (1, 4), (2, 2), (3, 2), (4, 2), (2, 3), (2, 4))}
+                 1e6: ((0, 2), (1, 4), (1, 5), (1, 6), (1, 7), (2, 2), (3, 2), (2, 3), (2, 4))}
     for cond in [float(c) for c in args.conds.split(",")]:
         A, Q, lam = si.spectral_spd(n, cond, seed=si.SEED_BASE + 2, device=dev)
         # the exact inverse of the generated A, Q diag(1/lam) Q^T, on the sampled columns
