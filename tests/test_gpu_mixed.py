@@ -54,12 +54,15 @@ def test_mixed_integer_case_exact(gpu):
         assert np.array_equal(lower_np(dA), np.tril(cf.bidiag_inverse(s)))
 
 
-@pytest.mark.parametrize("n", [1, 64, 129, 256, 513, 1000])
+@pytest.mark.parametrize("n", [1, 64, 129, 256, 513, 1000, 2300])
 def test_mixed_one_step_of_higher_order(gpu, n):
     """One correction of order p: R = I - A X, then X + X R + ... + X R^{p-1}
     with the terms formed as symmetric lower-tile products.  Order 3 at cond
     1e2 and order 4 at cond 1e4 reach the 1e-10 gate in one step; a higher
-    order is never worse than order 2 with the same single residual."""
+    order is never worse than order 2 with the same single residual.
+    n = 2300 pads to 18 blocks of 128 rows: the slice products' grouped tile
+    orders (8 row blocks per group for R, 16 for the lower-tile terms) end in
+    a partial group."""
     from paper_1002_4057_gb300 import torch_api as T
     for cond, order in ((1e2, 3), (1e4, 4)):
         A, _, _ = si.spectral_spd(n, cond, seed=si.SEED_BASE + 5 + n)
@@ -139,11 +142,13 @@ def test_mixed_full_size_sampled(gpu):
         torch.cuda.empty_cache()
 
 
-@pytest.mark.parametrize("n", [1, 31, 127, 128, 129, 300, 1030])
+@pytest.mark.parametrize("n", [1, 31, 127, 128, 129, 300, 1030, 2300])
 @pytest.mark.parametrize("residual", [0, 1, 2])
 def test_inverse_residual_vs_fp64(gpu, n, residual):
     """R = I - A X against the FP64 CPU product, for an X near A^{-1} (the
-    case the correction meets): |R - R_ref| <= 1e-13 |A| |X| elementwise-max."""
+    case the correction meets): |R - R_ref| <= 1e-13 |A| |X| elementwise-max.
+    n = 1030 and 2300 pad to 10 and 18 blocks of 128 rows, so the tile order
+    of the emulated product (groups of 8 row blocks) ends in a partial group."""
     import torch
     from paper_1002_4057_gb300 import _lib as L
     A, _, _ = si.spectral_spd(n, 1e3, seed=900 + n)
