@@ -396,7 +396,7 @@ def mixed_record(n, A_main, Q, lam_main, cond_main, ms64, stream, dev, peaks, re
                          "achieved_tflops": round(dag_rate, 3) if dag_rate else None,
                          "note": "n^3 per factorisation; the bulk products run as three TF32 mma.sync "
                                  "products (TF32 mma.sync measures about 304 TFLOP/s on this GPU, so about 101 "
-                                 "FP32-equivalent), the diagonal POTRF/TRTRI in FP64",
+                                 "FP32-equivalent), the diagonal POTRF/TRTRI in FP32 (block-wide sweeps at tile 64)",
                          "ffma_peak_tflops": ffma},
         })
         del W
@@ -427,7 +427,7 @@ def run_mixed_study(args, dev, stream):
     # one FP64 inversion takes ~33 s at n = 32768: fewer untimed runs there
     mw = 3 if n <= 16384 else 1
     schedules = {1e2: ((0, 2), (1, 2), (2, 2), (1, 3), (1, 4)),
-                 1e4: ((0, 2), (1, 2), (2, 2), (1, 3), (1, 4), (1, 5)),
+                 1e4: ((0, 2), (1, 2), (2, 2), (1, 3), (1, 4), (1, 5), (0, 2, 1), (1, 3, 1)),
                  1e6: ((0, 2), (1, 4), (1, 5), (1, 6), (1, 7), (2, 2), (3, 2), (2, 3), (2, 4))}
     for cond in [float(c) for c in args.conds.split(",")]:
         A, Q, lam = si.spectral_spd(n, cond, seed=si.SEED_BASE + 2, device=dev)
@@ -450,14 +450,18 @@ def run_mixed_study(args, dev, stream):
         ms64 = timed_steps(fp64, 1, 1, stream, mw)
         e64 = err_of(W)
         rec = {"cond": cond, "fp64_ms": round(ms64, 1), "fp64_err": e64, "mixed": []}
-        for k, order in schedules[cond]:
+        for sch in schedules[cond]:
+            k, order = sch[0], sch[1]
+            d64 = sch[2] if len(sch) > 2 else 0  # 1: the DAG's diagonal POTRF/TRTRI in FP64
+
             def mixed():
                 W.copy_(A)
-                T.potri_(W, info=info, precision=MIXED_PREC, refine_steps=k, refine_order=order)
+                T.potri_(W, info=info, precision=MIXED_PREC, refine_steps=k, refine_order=order, diag_fp64=d64)
             ms = timed_steps(mixed, 1, 1, stream, mw)
             assert int(info.item()) == 0
             e = err_of(W)
-            rec["mixed"].append({"steps": k, "order": order if k else None, "ms": round(ms, 1), "err": e,
+            rec["mixed"].append({"steps": k, "order": order if k else None, "diag_fp64": bool(d64),
+                                 "ms": round(ms, 1), "err": e,
                                  "gflops": round(flops / (ms * 1e-3) / 1e9, 1),
                                  "speedup_vs_fp64": round(ms64 / ms, 3)})
         out.append(rec)
@@ -466,7 +470,7 @@ def run_mixed_study(args, dev, stream):
         torch.cuda.empty_cache()
     best = []
     for rec in out:
-        ok = sorted((m for m in rec["mixed"] if m["err"] <= 1e-10), key=lambda m: m["ms"])
+        ok = sorted((m for m in rec["mixed"] if m["err"] <= 1e-10 and not m["diag_fp64"]), key=lambda m: m["ms"])
         best.append({"cond": rec["cond"], "steps_for_1e-10": ok[0]["steps"] if ok else None,
                      "order": ok[0]["order"] if ok else None, "err": ok[0]["err"] if ok else None,
                      "speedup_vs_fp64_at_1e-10": ok[0]["speedup_vs_fp64"] if ok else None})

@@ -86,7 +86,7 @@ typedef enum {
 typedef enum {
     SPDINV_PREC_FP64 = 0,         /* every operation in native FP64 (FMA on the FP64 pipe) */
     SPDINV_PREC_MIXED_FP32 = 1,   /* bulk updates FP32 (FMA on the CUDA cores); diagonal POTRF/TRTRI
-                                     and the residual FP64 */
+                                     FP32 (FP64 with spdinv_opts.diag_fp64); the residual FP64 */
     SPDINV_PREC_MIXED_BF16X3 = 2, /* as MIXED_FP32, the bulk updates on the BF16 tensor cores as three
                                      products of two-term BF16 splits (hi hi + hi lo + lo hi, FP32
                                      accumulation): about 2^-16 relative per product */
@@ -122,6 +122,13 @@ typedef struct {
                             The result is the same up to rounding (the integer test case:
                             bit for bit); the variants differ in memory and critical path. */
     int split_segment;   /* SPDINV_VARIANT_SPLIT3: chain segment length in tiles (0 = 16) */
+    int diag_fp64;       /* mixed precision only: precision of the FP32 tile DAG's diagonal-tile
+                            POTRF and TRTRI.  0 (default): FP32 (warp-level register sweeps for
+                            32-tiles, block-wide sweeps for 64-tiles); 1: native FP64 (the tile
+                            converted to FP64, block-wide sweeps, X_jj rounded back to FP32 for
+                            the bulk products).  Any other value: SPDINV_ERR_UNSUPPORTED.  The
+                            corrected result's accuracy is the same either way; FP64 sweeps
+                            lengthen the DAG's critical path. */
 } spdinv_opts;
 
 /* Execution variants (spdinv_opts.variant), for the study of Sec. 3 on the GPU:
@@ -181,7 +188,8 @@ SPDINV_API spdinv_status spdinv_potri(int64_t n, double* dA, int64_t lda, int* d
 /* spdinv_potri with options (tile size, residency, precision, correction
  * steps and order, wait limit).  opts may be NULL (= all defaults).
  * Mixed precision (opts->precision == SPDINV_PREC_MIXED_FP32, tile 32 or 64):
- * the tile DAG runs with FP32 bulk updates and FP64 diagonal POTRF/TRTRI,
+ * the tile DAG runs with FP32 bulk updates and FP32 diagonal POTRF/TRTRI
+ * (FP64 with opts->diag_fp64),
  * then refine_steps times R = I - A X (FP64-accurate; A read from its lower
  * triangle, intact until the end) and X <- X + X R + ... + X R^{p-1} (p =
  * refine_order; sums in FP64); the lower triangle of A then holds X in FP64.

@@ -77,7 +77,8 @@ STATUS_NAMES = {0: "SPDINV_OK", -1: "SPDINV_ERR_N", -2: "SPDINV_ERR_LDA", -3: "S
 class spdinv_opts(ctypes.Structure):
     _fields_ = [("tile", c_int), ("ctas_per_sm", c_int), ("precision", c_int), ("refine_steps", c_int),
                 ("wait_timeout_s", c_double), ("fault_drop_task", c_int), ("residual", c_int),
-                ("refine_order", c_int), ("variant", c_int), ("split_segment", c_int)]
+                ("refine_order", c_int), ("variant", c_int), ("split_segment", c_int),
+                ("diag_fp64", c_int)]
 
 
 # name -> (restype, argtypes); every symbol declared in include/spdinv.h

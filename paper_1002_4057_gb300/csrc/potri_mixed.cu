@@ -3,7 +3,7 @@
 // (GEMM, SYRK, TRMM) at FP32 accuracy (FP32 FMA, or three TF32 or BF16
 // tensor-core products of split operands) and its diagonal-tile POTRF and
 // TRTRI in FP32 (warp-level register sweeps for 32-tiles, block-wide sweeps
-// for 64-tiles); then `refine_steps` residual corrections of order p bring the
+// for 64-tiles) or, with spdinv_opts.diag_fp64, in native FP64; then `refine_steps` residual corrections of order p bring the
 // result back to FP64 accuracy:
 //      R = I - A X         (FP64-accurate; A read from its lower triangle)
 //      X <- X + X R + X R^2 + ... + X R^{p-1}
@@ -123,18 +123,25 @@ __device__ void store_X(const KParamsMixed& p, int ti, int tj, const float* T) {
 // (3xTF32), AccTC<B, SplitBF16> three BF16 MMAs (BF16x3).
 //
 // Shared memory: two sets of two tile buffers for the double-buffered update
-// chains (run_chain); the TRTRI scratch of the Step-1 diagonal task reuses
-// the second set once that task's chain is done.
+// chains (run_chain); the Step-1 diagonal task's scratch (the FP32 TRTRI's, or
+// the FP64 copy of the tile and its TRTRI scratch) reuses the second set once
+// that task's chain is done, and extends past it where the FP64 copy needs.
 template <int B>
 __host__ __device__ constexpr int mixed_tile_bytes() {
     return round_up128(padded_tile<B>() * (int)sizeof(float));
 }
 template <int B>
+__host__ __device__ constexpr int mixed_diag64_bytes() {
+    return (B * B + kThreads) * (int)sizeof(double);
+}
+template <int B, bool DIAG64>
 __host__ __device__ constexpr int mixed_smem_bytes() {
-    return 4 * mixed_tile_bytes<B>();
+    return 2 * mixed_tile_bytes<B>() + (DIAG64 && mixed_diag64_bytes<B>() > 2 * mixed_tile_bytes<B>()
+                                            ? mixed_diag64_bytes<B>()
+                                            : 2 * mixed_tile_bytes<B>());
 }
 
-template <int B, class ACC>
+template <int B, class ACC, bool DIAG64>
 __global__ void __launch_bounds__(kThreads) potri_mixed_persistent(const KParamsMixed prm) {
     unsigned char* const smem_raw = dynamic_smem();
     __shared__ __align__(8) uint64_t bars[2];
@@ -148,6 +155,8 @@ __global__ void __launch_bounds__(kThreads) potri_mixed_persistent(const KParams
     float* const T2 = reinterpret_cast<float*>(smem_raw + 2 * kT);
     float* const T3 = reinterpret_cast<float*>(smem_raw + 3 * kT);
     float* const tmpf = reinterpret_cast<float*>(smem_raw + 2 * kT);  // TRTRI scratch, kThreads floats (set 1)
+    double* const Td = reinterpret_cast<double*>(smem_raw + 2 * kT);  // FP64 diagonal tile, stride B (set 1 on)
+    double* const tmpd = Td + B * B;                                   // its TRTRI scratch, kThreads doubles
     PCtx c;
     c.T0 = T0;
     c.T1 = T1;
@@ -200,7 +209,25 @@ __global__ void __launch_bounds__(kThreads) potri_mixed_persistent(const KParams
                 return;
             cta_sync();
             acc_store<B>(acc, T0);
-            if constexpr (B == 32) {  // warp-level FP32 sweeps in registers (tile_diag32.cuh)
+            if constexpr (DIAG64) {  // FP64 block-wide sweeps (tile_fp64.cuh) on an FP64 copy of the tile
+                cta_sync();
+                for (int idx = threadIdx.x; idx < B * B; idx += kThreads) {
+                    const int r = idx % B, cc = idx / B;
+                    Td[idx] = r >= cc ? (double)T0[cc * LD + r] : 0.0;
+                }
+                const int fail = tile_potrf<B>(Td, &s_fail);
+                if (fail) {
+                    if (threadIdx.x == 0) record_info(p.ctrl, j * B + fail);
+                    return;
+                }
+                tile_zero_upper<B>(Td);
+                tile_trtri<B>(Td, tmpd);
+                for (int idx = threadIdx.x; idx < padded_tile<B>(); idx += kThreads) {  // X_jj back to FP32
+                    const int r = idx % LD, cc = idx / LD;
+                    T0[idx] = (r < B && r >= cc) ? (float)Td[cc * B + r] : 0.f;
+                }
+                cta_sync();
+            } else if constexpr (B == 32) {  // warp-level FP32 sweeps in registers (tile_diag32.cuh)
                 const int fail = diag_potrf32_f32<LD>(T0, &s_fail);
                 if (fail) {
                     if (threadIdx.x == 0) record_info(p.ctrl, j * B + fail);
@@ -425,15 +452,10 @@ __global__ void finalize_info_mixed(const int* ctrl, int* d_info) {
     if (threadIdx.x == 0 && blockIdx.x == 0) *d_info = ctrl[2] != 0 ? ctrl[2] : ctrl[3];
 }
 
-template <int B>
-int mixed_smem() {
-    return mixed_smem_bytes<B>();
-}
-
-template <int B, class ACC>
-cudaError_t launch_mixed_dag(const KParamsMixed& p, int ctas_per_sm, int num_sms, cudaStream_t s) {
-    auto kern = potri_mixed_persistent<B, ACC>;
-    const int sm = mixed_smem<B>();
+template <int B, class ACC, bool DIAG64>
+cudaError_t launch_mixed_dag_t(const KParamsMixed& p, int ctas_per_sm, int num_sms, cudaStream_t s) {
+    auto kern = potri_mixed_persistent<B, ACC, DIAG64>;
+    const int sm = mixed_smem_bytes<B, DIAG64>();
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     if (e != cudaSuccess) return e;
     int occ = 0;
@@ -446,6 +468,12 @@ cudaError_t launch_mixed_dag(const KParamsMixed& p, int ctas_per_sm, int num_sms
     if (grid > p.ntasks) grid = p.ntasks;
     kern<<<grid, kThreads, sm, s>>>(p);
     return cudaGetLastError();
+}
+
+template <int B, class ACC>
+cudaError_t launch_mixed_dag(const KParamsMixed& p, bool diag64, int ctas_per_sm, int num_sms, cudaStream_t s) {
+    return diag64 ? launch_mixed_dag_t<B, ACC, true>(p, ctas_per_sm, num_sms, s)
+                  : launch_mixed_dag_t<B, ACC, false>(p, ctas_per_sm, num_sms, s);
 }
 
 }  // namespace
@@ -462,9 +490,11 @@ spdinv_status mixed_layout(int64_t n, const spdinv_opts* o, MixedLayout* out) {
                o->precision != SPDINV_PREC_MIXED_TF32X3))
         return SPDINV_ERR_UNSUPPORTED;
     if (o->variant != 0) return SPDINV_ERR_UNSUPPORTED;  // the execution variants are FP64 only
-    // default tile: 32 up to n = 8192 (the FP64 diagonal tiles on the critical
-    // path cost 8x less; 9.2 against 13.0 ms at n = 4096), 64 above (110 against
-    // 155 ms at n = 16384)
+    if (o->diag_fp64 != 0 && o->diag_fp64 != 1) return SPDINV_ERR_UNSUPPORTED;
+    // default tile: 32 up to n = 8192, 64 above.  The diagonal tasks lie on the
+    // critical path, and a 32-tile's sweeps cost 8x less (measured with FP64
+    // sweeps: 9.2 against 13.0 ms at n = 4096); at n = 16384 the 64-tile DAG
+    // has the shorter run (110 against 155 ms, FP64 sweeps).
     const int b = o->tile > 0 ? o->tile : (n <= 8192 ? 32 : 64);
     if (b != 32 && b != 64) return SPDINV_ERR_UNSUPPORTED;
     if (o->refine_steps < 0 || o->refine_steps > 16) return SPDINV_ERR_UNSUPPORTED;
@@ -565,16 +595,16 @@ spdinv_status run_mixed(int64_t n, double* dA, int64_t lda, const spdinv_opts* o
     timing_begin(SPDINV_TIMED_MIXED_DAG, stream, &tok);
     switch (o->precision) {
         case SPDINV_PREC_MIXED_TF32X3:
-            e = b == 64 ? launch_mixed_dag<64, AccTC<64, SplitTF32>>(p, o->ctas_per_sm, ds.num_sms, stream)
-                        : launch_mixed_dag<32, AccTC<32, SplitTF32>>(p, o->ctas_per_sm, ds.num_sms, stream);
+            e = b == 64 ? launch_mixed_dag<64, AccTC<64, SplitTF32>>(p, o->diag_fp64 != 0, o->ctas_per_sm, ds.num_sms, stream)
+                        : launch_mixed_dag<32, AccTC<32, SplitTF32>>(p, o->diag_fp64 != 0, o->ctas_per_sm, ds.num_sms, stream);
             break;
         case SPDINV_PREC_MIXED_BF16X3:
-            e = b == 64 ? launch_mixed_dag<64, AccTC<64, SplitBF16>>(p, o->ctas_per_sm, ds.num_sms, stream)
-                        : launch_mixed_dag<32, AccTC<32, SplitBF16>>(p, o->ctas_per_sm, ds.num_sms, stream);
+            e = b == 64 ? launch_mixed_dag<64, AccTC<64, SplitBF16>>(p, o->diag_fp64 != 0, o->ctas_per_sm, ds.num_sms, stream)
+                        : launch_mixed_dag<32, AccTC<32, SplitBF16>>(p, o->diag_fp64 != 0, o->ctas_per_sm, ds.num_sms, stream);
             break;
         default:
-            e = b == 64 ? launch_mixed_dag<64, Acc32<64>>(p, o->ctas_per_sm, ds.num_sms, stream)
-                        : launch_mixed_dag<32, Acc32<32>>(p, o->ctas_per_sm, ds.num_sms, stream);
+            e = b == 64 ? launch_mixed_dag<64, Acc32<64>>(p, o->diag_fp64 != 0, o->ctas_per_sm, ds.num_sms, stream)
+                        : launch_mixed_dag<32, Acc32<32>>(p, o->diag_fp64 != 0, o->ctas_per_sm, ds.num_sms, stream);
     }
     if (e != cudaSuccess) return cuda_fail(e);
     timing_end(SPDINV_TIMED_MIXED_DAG, stream, tok, (double)n * (double)n * (double)n);

@@ -69,17 +69,19 @@ def lauum_(A, stream=None):
 
 
 def potri_(A, info=None, stream=None, tile=0, ctas_per_sm=0, precision=0, refine_steps=0,
-           wait_timeout_s=0.0, fault_drop_task=-1, residual=0, refine_order=0, variant=0, split_segment=0):
+           wait_timeout_s=0.0, fault_drop_task=-1, residual=0, refine_order=0, variant=0, split_segment=0,
+           diag_fp64=0):
     """In place: lower triangle of A <- lower triangle of A^{-1} (Steps 1-3).
     Mixed precision (precision=1): refine_steps corrections of order
-    refine_order (0 = 2).  variant: an execution variant of the FP64 plan
+    refine_order (0 = 2); diag_fp64=1 runs the DAG's diagonal POTRF/TRTRI in
+    FP64.  variant: an execution variant of the FP64 plan
     (SPDINV_VARIANT_*; split_segment for SPDINV_VARIANT_SPLIT3)."""
     n, lda = _lda(A, torch.float64)
     info = _info_buf(A.device) if info is None else info
     if (tile or ctas_per_sm or precision or refine_steps or wait_timeout_s or fault_drop_task >= 0 or residual
-            or refine_order or variant or split_segment):
+            or refine_order or variant or split_segment or diag_fp64):
         o = L.spdinv_opts(tile, ctas_per_sm, precision, refine_steps, float(wait_timeout_s), fault_drop_task,
-                          residual, refine_order, variant, split_segment)
+                          residual, refine_order, variant, split_segment, diag_fp64)
         st = L.spdinv_potri_ex(n, A.data_ptr(), lda, o, info.data_ptr(), _stream(stream))
         _check(st, "spdinv_potri_ex")
     else:

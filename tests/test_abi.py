@@ -94,6 +94,8 @@ def test_potri_ex_option_errors(lib):
         L.spdinv_opts(64, 0, mixed, 1, 0.0, -1, -1, 0),
         L.spdinv_opts(64, 0, 4, 1, 0.0, -1, 0, 0),       # unknown precision
         L.spdinv_opts(64, 0, 7, 1, 0.0, -1, 0, 0),
+        L.spdinv_opts(64, 0, mixed, 1, 0.0, -1, 0, 0, 0, 0, 2),   # diagonal precision
+        L.spdinv_opts(64, 0, mixed, 1, 0.0, -1, 0, 0, 0, 0, -1),
     ]
     for o in bad:
         assert L.spdinv_potri_ex(100, FAKE, 100, o, None, None) == L.SPDINV_ERR_UNSUPPORTED

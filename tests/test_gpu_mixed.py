@@ -94,6 +94,42 @@ def test_mixed_two_steps_order3_cond1e6(gpu):
     assert err <= max(1e-10, 2 * e64)
 
 
+@pytest.mark.parametrize("n", [1, 64, 513, 1000])
+@pytest.mark.parametrize("tile", [32, 64])
+@pytest.mark.parametrize("prec", [MIXED, 3])
+def test_mixed_fp64_diagonal_tiles(gpu, n, tile, prec):
+    """diag_fp64: the DAG's diagonal POTRF/TRTRI in native FP64 (the tile
+    converted to FP64 and X_jj rounded back to FP32).  The unrefined result
+    is FP32-accurate, one correction of order 4 at cond 1e4 reaches the 1e-10
+    gate, and the integer case stays exact."""
+    from paper_1002_4057_gb300 import torch_api as T
+    A, _, _ = si.spectral_spd(n, 1e4, seed=si.SEED_BASE + 7 + n)
+    M, _ = oracle.potri(A)
+    ref = oracle.symmetrize_lower(M)
+    errs = []
+    for steps, order in ((0, 0), (1, 4)):
+        dA = to_dev(A, gpu)
+        info = T.potri_(dA, precision=prec, refine_steps=steps, refine_order=order, tile=tile, diag_fp64=1)
+        assert int(info.item()) == 0
+        errs.append(oracle.rel_frobenius(full_from_lower(lower_np(dA)), ref))
+    print("n=%d tile=%d prec=%d FP64 diagonal tiles: errors %s" % (n, tile, prec, ["%.2e" % e for e in errs]))
+    assert errs[0] <= 1e-3 and errs[1] <= 1e-10
+    Ai, s_ = si.bidiag_integer_spd(max(n, 2), seed=11)
+    dA = to_dev(Ai, gpu)
+    info = T.potri_(dA, precision=prec, tile=tile, diag_fp64=1)
+    assert int(info.item()) == 0
+    assert np.array_equal(lower_np(dA), np.tril(cf.bidiag_inverse(s_)))
+
+
+def test_mixed_fp64_diagonal_info(gpu):
+    from paper_1002_4057_gb300 import torch_api as T
+    d = np.ones(300)
+    d[150] = -2.0
+    dA = to_dev(np.diag(d), gpu)
+    info = T.potri_(dA, precision=MIXED, refine_steps=1, diag_fp64=1)
+    assert int(info.item()) == 151
+
+
 def test_mixed_info(gpu):
     from paper_1002_4057_gb300 import torch_api as T
     d = np.ones(300)
