@@ -434,6 +434,21 @@ SPDINV_API spdinv_status spdinv_dag_task_counts(int t, int64_t out[12]);
  * = 1 if the critical path or the total work differ. */
 SPDINV_API spdinv_status spdinv_plan_check(int t, int steps, int64_t out[3]);
 
+/* Launch order of the emulated residual's slice GEMM (host only; no GPU): one
+ * CTA per output tile of R = I - A X (lower = 0) or of a symmetric correction
+ * term X R^m (lower = 1: only the tiles holding an entry on or below the
+ * diagonal), for the order-n product padded to npad = n rounded up to 256.
+ * wide = 1: 128 x 256 output tiles (the default kernel); 0: 128 x 128
+ * (SPDINV_SLICE_TILE=128).  Launch index pid computes the tile of 128-row
+ * block bm[pid] and column block bn[pid] (256 or 128 columns), in a grouped
+ * raster that keeps the CTAs resident at one time on shared operand blocks;
+ * the replay calls the kernels' own index functions.  *count = number of
+ * launched tiles; bm and bn (both NULL to query the count, else both of
+ * *count entries, caller-owned) receive the order.  Errors: n outside
+ * 1 .. 2^20 (SPDINV_ERR_N); count NULL, or only one of bm, bn NULL
+ * (SPDINV_ERR_NULL). */
+SPDINV_API spdinv_status spdinv_slice_tile_order(int64_t n, int lower, int wide, int* bm, int* bn, int* count);
+
 /* The execution plan the persistent kernel runs for an order-n matrix with
  * tile b: the chain tasks (one per output tile and step; each holds its
  * whole commutative update chain, Sec. 3 "loop reversal") in the order CTAs

@@ -101,6 +101,7 @@ SIGNATURES = {
     "spdinv_batch_shard": (c_int, [c_int, P, c_int, P, P]),
     "spdinv_plan_emulate": (c_int, [c_int, c_int, c_int, ctypes.c_uint64, c_int, c_int, c_double, c_int, P]),
     "spdinv_plan_check": (c_int, [c_int, c_int, P]),
+    "spdinv_slice_tile_order": (c_int, [c_int64, c_int, c_int, P, P, P]),
     "spdinv_plan_emulate_variant": (c_int, [c_int, c_int, c_int, c_int, ctypes.c_uint64, c_int, c_double, c_int, P]),
     "spdinv_workspace_size": (c_int, [c_int64, c_int, ctypes.POINTER(spdinv_opts), P]),
     "spdinv_set_workspace": (c_int, [P, ctypes.c_size_t]),
@@ -217,6 +218,19 @@ def spdinv_plan_check(t, steps):
     out = (ctypes.c_int64 * 3)()
     st = _call("spdinv_plan_check", int(t), int(steps), ctypes.addressof(out))
     return st, list(out)
+
+
+def spdinv_slice_tile_order(n, lower, wide=1):
+    """(status, bm list, bn list) of the slice GEMM's launch order for order n."""
+    cnt = ctypes.c_int(0)
+    st = _call("spdinv_slice_tile_order", int(n), int(lower), int(wide), None, None, ctypes.addressof(cnt))
+    if st != 0:
+        return st, [], []
+    bm = (ctypes.c_int * max(cnt.value, 1))()
+    bn = (ctypes.c_int * max(cnt.value, 1))()
+    st = _call("spdinv_slice_tile_order", int(n), int(lower), int(wide), ctypes.addressof(bm),
+               ctypes.addressof(bn), ctypes.addressof(cnt))
+    return st, list(bm)[:cnt.value], list(bn)[:cnt.value]
 
 
 def spdinv_plan_simulate(t, steps, workers):

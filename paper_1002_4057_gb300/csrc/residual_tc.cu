@@ -198,25 +198,28 @@ __device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity, volatil
 // resident at one time share both operands' slices in L2.  With `lower`
 // only the tiles with bm >= bn (tb_m == tb_n): in the group of rows
 // [first, first + gm), column c holds the rows r >= c.
+__host__ __device__ constexpr int imin(int a, int b) { return a < b ? a : b; }
+__host__ __device__ constexpr int imax(int a, int b) { return a > b ? a : b; }
+
 template <int GROUP>
-__device__ __forceinline__ void block_of(int pid, int tb_m, int tb_n, bool lower, int& bm, int& bn) {
+__host__ __device__ __forceinline__ void block_of(int pid, int tb_m, int tb_n, bool lower, int& bm, int& bn) {
     if (!lower) {
         const int per_group = GROUP * tb_n;
         const int first = (pid / per_group) * GROUP;
-        const int gm = min(tb_m - first, GROUP);
+        const int gm = imin(tb_m - first, GROUP);
         bm = first + (pid % per_group) % gm;
         bn = (pid % per_group) / gm;
         return;
     }
     int first = 0;
     for (;;) {
-        const int gm = min(tb_m - first, GROUP);
+        const int gm = imin(tb_m - first, GROUP);
         const int cnt = first * gm + gm * (gm + 1) / 2;
         if (pid < cnt || first + gm >= tb_m) break;
         pid -= cnt;
         first += gm;
     }
-    const int gm = min(tb_m - first, GROUP);
+    const int gm = imin(tb_m - first, GROUP);
     if (pid < first * gm) {
         bn = pid / gm;
         bm = first + pid % gm;
@@ -462,28 +465,28 @@ __device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32
 // one time share the column blocks of X's slices in L2.  In the group of rows [first, first + gm), column bn holds the
 // rows max(first, 2 bn) .. first + gm - 1.  (tb_m is even: npad is a multiple
 // of 256.)
-__device__ __forceinline__ int lower_group_tiles(int first, int gm) {
+__host__ __device__ __forceinline__ int lower_group_tiles(int first, int gm) {
     const int h = (first + gm - 1) / 2, f2 = first / 2;  // last column; last full column
-    int cnt = (min(f2, h) + 1) * gm;
+    int cnt = (imin(f2, h) + 1) * gm;
     if (h > f2) cnt += (h - f2) * (first + gm) - (h * (h + 1) - f2 * (f2 + 1));
     return cnt;
 }
-__device__ __forceinline__ void block_of_wide(int pid, int tb_m, int tb_n, bool lower, int& bm, int& bn) {
+__host__ __device__ __forceinline__ void block_of_wide(int pid, int tb_m, int tb_n, bool lower, int& bm, int& bn) {
     if (!lower) {
         block_of<8>(pid, tb_m, tb_n, false, bm, bn);
         return;
     }
     constexpr int GROUP = 16;
-    int first = 0, gm = min(tb_m, GROUP);
+    int first = 0, gm = imin(tb_m, GROUP);
     for (;;) {
-        gm = min(tb_m - first, GROUP);
+        gm = imin(tb_m - first, GROUP);
         const int cnt = lower_group_tiles(first, gm);
         if (pid < cnt || first + gm >= tb_m) break;
         pid -= cnt;
         first += gm;
     }
     for (bn = 0; bn <= (first + gm - 1) / 2; ++bn) {
-        const int lo = max(first, 2 * bn), c = first + gm - lo;
+        const int lo = imax(first, 2 * bn), c = first + gm - lo;
         if (pid < c) {
             bm = lo + pid;
             return;
@@ -691,6 +694,15 @@ bool make_map(CUtensorMap* m, const void* base, int64_t npad, int S, int rows, i
 
 // Output tile width of the slice GEMM: 256 (the wide form, default) or 128;
 // SPDINV_SLICE_TILE=128|256 in the environment chooses.
+// Launch size of the slice GEMM for padded order npad: one CTA per output
+// tile, 128 x 256 tiles (wide) or 128 x 128; lower: the tiles holding an entry
+// on or below the diagonal.
+int slice_grid(int64_t npad, bool lower, bool wide) {
+    const int tb_m = (int)(npad / TM);
+    if (wide) return lower ? (tb_m / 2) * (tb_m / 2 + 1) : tb_m * (int)(npad / WN);
+    return lower ? tb_m * (tb_m + 1) / 2 : tb_m * tb_m;
+}
+
 static int slice_tile() {
     static const int v = [] {
         const char* env = std::getenv("SPDINV_SLICE_TILE");
@@ -731,8 +743,7 @@ cudaError_t ozaki_products_tc(int64_t n, int64_t npad, const void* Asl, int SA, 
         const int sm = W_NSTAGE * W_STAGE;
         rc = cudaFuncSetAttribute(ozaki_tc_wide, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
         if (rc != cudaSuccess) return rc;
-        const int tb_m = (int)(npad / TM), tb_n = (int)(npad / WN);
-        const int grid = lower ? (tb_m / 2) * (tb_m / 2 + 1) : tb_m * tb_n;
+        const int grid = slice_grid(npad, lower, true);
         timing_begin(SPDINV_TIMED_SLICE_GEMM, s, &tok);
         ozaki_tc_wide<<<(unsigned)grid, NTHREADS, sm, s>>>(ma, mb, p);
         rc = cudaGetLastError();
@@ -744,7 +755,7 @@ cudaError_t ozaki_products_tc(int64_t n, int64_t npad, const void* Asl, int SA, 
     const int sm = NSTAGE * STAGE_BYTES;
     rc = cudaFuncSetAttribute(ozaki_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     if (rc != cudaSuccess) return rc;
-    const int grid = lower ? p.tiles * (p.tiles + 1) / 2 : p.tiles * p.tiles;
+    const int grid = slice_grid(npad, lower, false);
     timing_begin(SPDINV_TIMED_SLICE_GEMM, s, &tok);
     ozaki_tc_kernel<<<(unsigned)grid, NTHREADS, sm, s>>>(ma, mb, p);
     rc = cudaGetLastError();
@@ -752,4 +763,26 @@ cudaError_t ozaki_products_tc(int64_t n, int64_t npad, const void* Asl, int SA, 
     return rc;
 }
 
+// Host replay of the slice GEMM's launch order: the output tile (bm, bn) that
+// launch index pid takes, from the same functions the kernels call.
+int slice_tile_order(int64_t n, bool lower, bool wide, int* bm, int* bn) {
+    const int64_t npad = (n + 255) / 256 * 256;
+    const int tb_m = (int)(npad / TM);
+    const int grid = slice_grid(npad, lower, wide);
+    if (bm && bn)
+        for (int pid = 0; pid < grid; ++pid) {
+            if (wide) block_of_wide(pid, tb_m, (int)(npad / WN), lower, bm[pid], bn[pid]);
+            else block_of<16>(pid, tb_m, tb_m, lower, bm[pid], bn[pid]);
+        }
+    return grid;
+}
+
 }  // namespace spdinv
+
+extern "C" SPDINV_API spdinv_status spdinv_slice_tile_order(int64_t n, int lower, int wide, int* bm, int* bn,
+                                                            int* count) {
+    if (n < 1 || n > (int64_t(1) << 20)) return SPDINV_ERR_N;
+    if (!count || (bm == nullptr) != (bn == nullptr)) return SPDINV_ERR_NULL;
+    *count = spdinv::slice_tile_order(n, lower != 0, wide != 0, bm, bn);
+    return SPDINV_OK;
+}

@@ -304,3 +304,48 @@ def test_status_names_match_the_binding(lib):
     for code, name in L.STATUS_NAMES.items():
         assert L.spdinv_status_name(code) == name
     assert L.spdinv_status_name(-99) == "unknown status"
+
+
+@pytest.mark.parametrize("wide", [1, 0])
+@pytest.mark.parametrize("lower", [0, 1])
+def test_slice_gemm_tile_order_is_a_bijection(lib, lower, wide):
+    """The slice GEMM launches one CTA per output tile in a grouped raster
+    (groups of 8 row blocks for the full 128 x 256 grid, 16 for its lower
+    tiles and for the 128 x 128 grid).  Replayed on the host through the
+    kernels' own index functions, every launch index takes a distinct tile of
+    the grid (only tiles holding an entry on or below the diagonal when
+    lower), and every such tile is taken -- including grids that end in a
+    partial group."""
+    for n in (1, 255, 256, 257, 1030, 2300, 4096, 5000, 16384, 20000, 32768):
+        npad = (n + 255) // 256 * 256
+        tb_m = npad // 128
+        cols = 256 if wide else 128
+        tb_n = npad // cols
+        st, bm, bn = L.spdinv_slice_tile_order(n, lower, wide)
+        assert st == 0
+        want = {(r, c) for r in range(tb_m) for c in range(tb_n)
+                if not lower or c * cols <= r * 128 + 127}
+        assert len(bm) == len(want), (n, len(bm), len(want))
+        assert set(zip(bm, bn)) == want, n
+
+
+def test_slice_gemm_tile_order_groups(lib):
+    """The full 128 x 256 grid at n = 16384 (128 x 64 tiles) runs groups of 8
+    row blocks column by column: the first 8 launch indices are column 0 of
+    rows 0-7, and each group covers its 8 rows before the next starts."""
+    st, bm, bn = L.spdinv_slice_tile_order(16384, 0, 1)
+    assert st == 0
+    assert list(zip(bm[:9], bn[:9])) == [(r, 0) for r in range(8)] + [(0, 1)]
+    per_group = 8 * 64
+    for g in range(128 // 8):
+        assert set(bm[g * per_group:(g + 1) * per_group]) == set(range(8 * g, 8 * g + 8))
+
+
+def test_slice_gemm_tile_order_errors(lib):
+    cnt = ctypes.c_int(0)
+    assert L._call("spdinv_slice_tile_order", 0, 0, 1, None, None, ctypes.addressof(cnt)) == L.SPDINV_ERR_N
+    assert L._call("spdinv_slice_tile_order", (1 << 20) + 1, 0, 1, None, None, ctypes.addressof(cnt)) == L.SPDINV_ERR_N
+    assert L._call("spdinv_slice_tile_order", 100, 0, 1, None, None, None) == L.SPDINV_ERR_NULL
+    a = (ctypes.c_int * 4)()
+    assert L._call("spdinv_slice_tile_order", 100, 0, 1, ctypes.addressof(a), None,
+                   ctypes.addressof(cnt)) == L.SPDINV_ERR_NULL
