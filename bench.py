@@ -186,7 +186,11 @@ def cpu_baseline(n_full, cond, budget_s=12.0):
             "cpu_model": cpu_model(), "nproc": os.cpu_count(),
             "all_cores": {"n512": round(g512, 3), "n%d" % n2: round(g_all, 3)},
             "single_thread": {"n512": round(g1_512, 3), "n%d" % n1: round(g1, 3),
-                              "note": "one OpenMP thread, n=%d took %.1f s" % (n1, dt1b)}}
+                              "note": "one OpenMP thread, n=%d took %.1f s" % (n1, dt1b)},
+            "full_size_estimate": {"n": n_full, "seconds_all_cores": round(dt_all * (n_full / n2) ** 3, 1),
+                                   "seconds_one_thread": round(dt1b * (n_full / n1) ** 3, 1),
+                                   "note": "not timed (it would exceed the run's few minutes): the measured "
+                                           "n=%d and n=%d times scaled by n^3" % (n2, n1)}}
 
 
 def run_reference(args, rank, world):
