@@ -3,8 +3,7 @@
 // accesses free of bank conflicts), run by one CTA of 128 threads arranged
 // 16 x 8, each thread owning an (b/16) x (b/8) block of the output.
 // Same operations as the FP64 tile kernels (Algorithm 1, Sec. 2), in FP32
-// CUDA-core arithmetic (fused multiply-add; optionally packed two columns at
-// a time).
+// CUDA-core arithmetic (fused multiply-add).
 #pragma once
 #include "tile_fp64.cuh"
 
@@ -15,7 +14,6 @@ struct Cfg32 {
     static constexpr int LD = B + 1;
     static constexpr int RM = B / 16;  // rows per thread
     static constexpr int CN = B / 8;   // columns per thread
-    static_assert(CN % 2 == 0, "column pairs for the packed FMA");
 };
 
 template <int B>
@@ -55,11 +53,7 @@ __device__ __forceinline__ void acc_load(Acc32<B>& a, const float* T) {
 // warp skip the k-range that multiplies its zero part; the bounds are
 // uniform across the warp (a warp owns all rows and 2*CN columns), so no warp
 // diverges.  (A triangular left operand gives no warp-wide skip here.)
-// PACKED: two columns per packed FMA instruction (each component rounds as
-// fmaf, so the result is the same bit for bit).  It halves the FMA
-// instructions and measured faster in the backward's long plain products
-// (4.67 -> 4.30 ms) but slower in the tile DAGs, so it is a per-caller choice.
-template <int B, bool TA, bool TB, bool NEG, int SP, int SQ, bool PACKED = false>
+template <int B, bool TA, bool TB, bool NEG, int SP, int SQ>
 __device__ __forceinline__ void tile_mma(Acc32<B>& acc, const float* P, const float* Q) {
     constexpr int RM = Cfg32<B>::RM, CN = Cfg32<B>::CN, LD = Cfg32<B>::LD;
     const int r0 = (threadIdx.x % 16) * RM, c0 = (threadIdx.x / 16) * CN;
@@ -78,22 +72,10 @@ __device__ __forceinline__ void tile_mma(Acc32<B>& acc, const float* P, const fl
         }
 #pragma unroll
         for (int c = 0; c < CN; ++c) b[c] = TB ? Q[k * LD + c0 + c] : Q[(c0 + c) * LD + k];
-        if constexpr (PACKED) {
 #pragma unroll
-            for (int r = 0; r < RM; ++r)
+        for (int r = 0; r < RM; ++r)
 #pragma unroll
-                for (int c = 0; c < CN; c += 2) {
-                    const float2 t = __ffma2_rn(make_float2(a[r], a[r]), make_float2(b[c], b[c + 1]),
-                                                make_float2(acc.v[r][c], acc.v[r][c + 1]));
-                    acc.v[r][c] = t.x;
-                    acc.v[r][c + 1] = t.y;
-                }
-        } else {
-#pragma unroll
-            for (int r = 0; r < RM; ++r)
-#pragma unroll
-                for (int c = 0; c < CN; ++c) acc.v[r][c] = fmaf(a[r], b[c], acc.v[r][c]);
-        }
+            for (int c = 0; c < CN; ++c) acc.v[r][c] = fmaf(a[r], b[c], acc.v[r][c]);
     }
 }
 

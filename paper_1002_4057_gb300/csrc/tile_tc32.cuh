@@ -135,7 +135,7 @@ __device__ __forceinline__ void mma_bf16x(float (&c)[4], const uint32_t (&a)[4],
 // acc (+|-)= op(P) op(Q) as three split MMAs per k-step.  op(X) = X or X^T
 // (TA / TB); a lower-triangular stored operand lets each warp skip the k-steps
 // that multiply its zero part (the skipped terms are exact zeros).
-template <int B, bool TA, bool TB, bool NEG, int SP, int SQ, bool PACKED = false, class S>
+template <int B, bool TA, bool TB, bool NEG, int SP, int SQ, class S>
 __device__ __forceinline__ void tile_mma(AccTC<B, S>& acc, const float* P, const float* Q) {
     constexpr int W = AccTC<B, S>::W, MI = AccTC<B, S>::MI, NI = AccTC<B, S>::NI, LD = AccTC<B, S>::LD;
     constexpr int KS = S::K;
