@@ -2,6 +2,7 @@
  * libspdinv.so must link and answer without a GPU for everything that needs
  * none (argument checks, planner queries, the batch split).  Prints one
  * "name value" line per check; tests/test_c_abi.py compares them. */
+#include <stddef.h>
 #include <stdio.h>
 #include <stdint.h>
 
@@ -18,6 +19,7 @@ int main(void) {
     double load[2] = {0.0, 0.0};
     int64_t chk[3] = {0, 0, 0};
     spdinv_opts o = {0};
+    int tiles = 0;
     spdinv_status st;
 
     printf("version %d\n", spdinv_version());
@@ -41,5 +43,15 @@ int main(void) {
     st = spdinv_batch_shard(5, sizes, 2, owner, load);
     printf("shard %d %d %d %d %d %d %.0f %.0f\n", (int)st, owner[0], owner[1], owner[2], owner[3], owner[4],
            load[0], load[1]);
+    st = spdinv_slice_tile_order(2300, 1, 1, NULL, NULL, &tiles);
+    printf("slice_tiles %d %d\n", (int)st, tiles);
+    /* the layout of the options struct, for the binding's copy of it */
+    printf("opts_size %d\n", (int)sizeof(spdinv_opts));
+    printf("opts_offsets %d %d %d %d %d %d %d %d %d %d %d\n", (int)offsetof(spdinv_opts, tile),
+           (int)offsetof(spdinv_opts, ctas_per_sm), (int)offsetof(spdinv_opts, precision),
+           (int)offsetof(spdinv_opts, refine_steps), (int)offsetof(spdinv_opts, wait_timeout_s),
+           (int)offsetof(spdinv_opts, fault_drop_task), (int)offsetof(spdinv_opts, residual),
+           (int)offsetof(spdinv_opts, refine_order), (int)offsetof(spdinv_opts, variant),
+           (int)offsetof(spdinv_opts, split_segment), (int)offsetof(spdinv_opts, diag_fp64));
     return 0;
 }

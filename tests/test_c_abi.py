@@ -35,3 +35,11 @@ def test_plain_c_caller(tmp_path):
     # sizes 5, 9, 9, 3, 7 on two ranks, largest first: 9 -> 0, 9 -> 1, 7 -> 0
     # (tie, lower rank), 5 -> 1, 3 -> 1; loads 729 + 343 and 729 + 125 + 27
     assert got["shard"] == "0 1 0 1 1 0 1072 881"
+    # n = 2300 pads to 2304: 18 row blocks of 128, the lower 128 x 256 tiles 9 * 10
+    assert got["slice_tiles"] == "0 90"
+    # the binding's spdinv_opts has the header's layout
+    from paper_1002_4057_gb300 import _lib as L
+    import ctypes
+    assert int(got["opts_size"]) == ctypes.sizeof(L.spdinv_opts)
+    offs = [getattr(L.spdinv_opts, f).offset for f, _ in L.spdinv_opts._fields_]
+    assert [int(v) for v in got["opts_offsets"].split()] == offs
