@@ -1,28 +1,33 @@
 // The slice products of the emulated FP64 residual (residual_ozaki.cu; the
 // error-free splitting of Ozaki, Ogita, Oishi and Rump 2012) on the
 // fifth-generation tensor cores: tcgen05.mma (BF16 in, FP32 accumulator in
-// tensor memory), operands staged by TMA with 128-byte swizzle.
+// tensor memory), operands staged by TMA with 128-byte swizzle.  One CTA
+// computes one output tile of R = I - A X (or of a correction term X R^m)
+// over all slice pairs.  Two forms:
 //
-// One CTA computes a 128 x 128 tile of R = I - A X (or of a correction term
-// X R^m) over all slice pairs:
-//   warp 0    TMA producer: 64-deep K slices of A's and X's slice planes into
-//             a 6-stage shared-memory ring;
-//   warp 1    allocates all 512 tensor-memory columns and issues the MMAs
-//             from one thread into two 128-column FP32 accumulators: 16
-//             stages = one exact 1024-deep chunk per accumulator, then a
-//             commit;
-//   warps 2-9 epilogue: each thread owns half of one accumulator row (its
-//             warp's lane quarter, 64 columns).  Per chunk it reads the
-//             accumulator with tcgen05.ld, adds the exact FP32 integers into
-//             INT32 registers and releases the accumulator; per slice pair it
-//             adds those into INT64 level sums kept in tensor memory (columns
-//             256-511, lo/hi pairs); per level s + t -- all its pairs share
-//             the scale 2^{e_i + f_j - 8(s+t+2)} -- it adds the level once into
-//             R (FP64, global).  FP64 work, slow on this chip, thus happens
-//             once per level (L + 1 times per tile) instead of once per chunk
-//             or pair.
-// Every wait is bounded; on a timeout the CTA records an error, all roles
-// leave their loops, and the tensor memory is freed before exit.
+// ozaki_tc_wide (the default): a 128 x 256 tile, 320 threads, 1 CTA per SM.
+//   warp 0    TMA producer: per stage one 3-D box of an A-slice plane
+//             (128 rows x one 64-deep atom, 16 KB) and one of an X-slice
+//             plane (256 rows, 32 KB) into a 4-stage ring;
+//   warp 1    allocates the 512 tensor-memory columns and issues the MMAs
+//             (M = 128, N = 256) from one thread into one 256-column FP32
+//             accumulator, committing at the end of each exact 1024-deep
+//             chunk;
+//   warps 2-9 epilogue: per chunk each thread loads its half of an
+//             accumulator row (128 values) into registers and releases the
+//             accumulator at once, then adds the exact FP32 integers into
+//             INT32 level sums kept in tensor-memory columns 256-511; per level
+//             s + t -- all its pairs share the scale 2^{e_i + f_j - 8(s+t+2)}
+//             -- it adds the level once into R (FP64, global), so the FP64
+//             work, slow on this chip, happens once per level per tile.
+// ozaki_tc_kernel (SPDINV_SLICE_TILE=128): a 128 x 128 tile, two 64-deep atoms
+//   per stage and operand, 3 stages, two alternating 128-column accumulators
+//   and INT64 level sums; it wins only where too few 128 x 256 tiles exist to
+//   fill the GPU.
+// Both visit the tiles in a grouped raster (block_of, block_of_wide), replayed
+// on the host by spdinv_slice_tile_order.  Every wait is bounded; on a timeout
+// the CTA records an error, all roles leave their loops, and the tensor memory
+// is freed before exit.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
