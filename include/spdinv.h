@@ -559,8 +559,9 @@ SPDINV_API unsigned spdinv_set_debug_flags(unsigned flags);
 
 /* Peak microbenchmark.  Queues one kernel on `stream` that keeps one pipe
  * busy on register operands -- kind SPDINV_PROBE_DMMA: the FP64 tensor-core
- * MMA mma.sync m8n8k4 (the instruction of the FP64 tile products),
- * SPDINV_PROBE_DFMA: the FP64 fused multiply-add, SPDINV_PROBE_FFMA: the FP32
+ * MMA mma.sync m8n8k4, SPDINV_PROBE_DFMA: the FP64 fused multiply-add (the
+ * instruction of the FP64 tile products, the faster of the two on GB300),
+ * SPDINV_PROBE_FFMA: the FP32
  * fused multiply-add (the CUDA-core FP32 tile products) -- with 16
  * independent accumulators per thread, `iters` iterations, `blocks_per_sm`
  * CTAs of 128 threads per SM (1..16).  *flops receives the number of

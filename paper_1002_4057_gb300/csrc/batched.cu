@@ -13,7 +13,8 @@
 // class, capped per batch by plan tuning (one kernel holds the largest tile
 // any matrix uses, and that sets every CTA's occupancy).  Inside each chain of
 // products the next tiles are read into registers while the current product
-// runs.  FP64 uses the tensor-core MMA tile products, FP32 the CUDA-core ones.
+// runs.  FP64 uses the FP64 FMA register-block tile products (tile_fp64.cuh),
+// FP32 the CUDA-core FMA ones (tile_f32.cuh).
 // spdinv_batch_shard splits a batch across GPUs (host only).
 #include <cuda_runtime.h>
 

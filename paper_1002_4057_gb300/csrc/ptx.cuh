@@ -1,5 +1,6 @@
 // Inline-PTX helpers for sm_103a: mbarriers, bulk (TMA) copies, acquire /
-// release flags, the global timer and the FP64 tensor-core MMA.
+// release flags, the global timer and the FP64 tensor-core MMA (the peak
+// probe's comparison kernel; the FP64 tile products use the FP64 FMA).
 #pragma once
 #include <cstdint>
 
