@@ -15,9 +15,12 @@
 //     paper chose because they shorten the critical path.  Renamed stores
 //     B (L), C (L^{-1}) and D (inverted diagonal tiles) remove every
 //     write-after-read hazard, so a task depends only on the tiles it reads.
-//     Tasks are ordered by decreasing bottom level (longest weighted path to
-//     the end), which is a topological order; a CTA only ever waits for tasks
-//     taken before its own, so the persistent kernel cannot deadlock.
+//     Tasks are ordered by increasing latest finish time in the
+//     element-pipelined schedule (ORDER_ALAP, the default; alap_order_grid)
+//     or by decreasing bottom level (longest weighted path to the end;
+//     ORDER_BOTTOM_LEVEL, also the order of the execution variants).  Both
+//     are topological orders: a CTA only ever waits for tasks taken before
+//     its own, so the persistent kernel cannot deadlock.
 #include "plan.h"
 
 #include <algorithm>
