@@ -629,7 +629,9 @@ SPDINV_API const char* spdinv_last_cuda_error(void);
  * devices, all threads): a host-side counter, incremented per launch. */
 SPDINV_API uint64_t spdinv_kernel_launches(void);
 
-/* Version as major*10000 + minor*100 + patch. */
+/* Version as major*10000 + minor*100 + patch.  1.2 appended diag_fp64 to
+ * spdinv_opts (the library reads the whole struct: rebuild callers compiled
+ * against an older header) and added spdinv_slice_tile_order. */
 SPDINV_API int spdinv_version(void);
 
 #ifdef __cplusplus

@@ -489,6 +489,6 @@ const char* spdinv_last_cuda_error(void) { return g_last_cuda_error.c_str(); }
 
 uint64_t spdinv_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 
-int spdinv_version(void) { return 10100; }
+int spdinv_version(void) { return 10200; }
 
 }  // extern "C"
