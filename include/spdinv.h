@@ -53,6 +53,12 @@
  *      SPDINV_TILE=32|64  the default tile of the FP64 single-matrix calls.
  *      SPDINV_WAIT_TIMEOUT_S  the default limit of one dependency wait (60 s).
  *      SPDINV_BATCHED_TILE=16|32|64  one tile for every batched size class.
+ *      SPDINV_PLAN_ORDER=bottom_level (or 0)  the bottom-level ticket order
+ *                         instead of the default ALAP order (see
+ *                         spdinv_set_plan_order).
+ *      SPDINV_SLICE_TILE=128  the 128 x 128 slice GEMM instead of the
+ *                         default 128 x 256 one (emulated residual).
+ *      SPDINV_DEBUG       initial debug flags (spdinv_set_debug_flags).
  */
 #ifndef SPDINV_H
 #define SPDINV_H
