@@ -258,7 +258,7 @@ SPDINV_API spdinv_status spdinv_inverse_residual(int64_t n, const double* dA, in
  * spdinv_potri.
  *  - n > SPDINV_NOALLOC_MAX_N returns SPDINV_ERR_N and launches nothing.
  *  - The first call on a device (with that device current) looks up the
- *    array's device address; make that first call before any stream capture.
+ *    array's device address, a host-side query of the loaded module.
  *    A device reset (cudaDeviceReset) ends the context the address belongs
  *    to: the first call in the new context looks it up again.
  *  - Every call uses the same array, which keeps the last call's contents
